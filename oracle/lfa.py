@@ -1,0 +1,124 @@
+"""Local Fourier analysis of the SPAI smoothers (Sec. 2, Sec. 3, Table 1).
+
+TEST INFRASTRUCTURE (see the package docstring).
+
+All symbols are written in the cosine variables x_i = cos(theta_i), h = 1
+(every symbol below is invariant under the h^2 scaling of the oracle):
+
+    A~(x)  = 2 (d - sum_i x_i)                               [Eq. (3.1), 3D analogue]
+    M~(x)  = c0 + 2 c1 sum_i x_i (+ 4 c2 x_1 x_2 in 2D)       [symbols of Upsilon, T]
+    S~(x)  = 1 - A~(x) M~(x)        (omega already folded into the weights c)
+
+The high frequencies T^H = [-pi/2, 3pi/2)^d minus [-pi/2, pi/2)^d map to the
+cosine set X^H = [-1, 1]^d minus (0, 1]^d (Appendix A and the proof of
+Theorem 3.2). The smoothing factor is mu = max_{X^H} |S~| (Sec. 2); for a
+positive product A~M~ in [l0, l1] the optimum is mu_opt = (l1 - l0)/(l1 + l0)
+at omega_opt = 2/(l0 + l1) (Eqs. (2.6), (2.7)).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+from scipy.optimize import minimize
+
+
+def product_symbol(d: int, w, x) -> np.ndarray:
+    """A~ M~ at cosine points x (shape (..., d)); w = stencil weights (units h^2)."""
+    x = np.asarray(x, dtype=np.float64)
+    sx = x.sum(axis=-1)
+    a = 2.0 * (d - sx)
+    m = w[0] + 2.0 * w[1] * sx
+    if d == 2 and len(w) > 2:
+        m = m + 4.0 * w[2] * x[..., 0] * x[..., 1]
+    return a * m
+
+
+def _high_grid(d: int, k: int) -> np.ndarray:
+    """Points of X^H on a uniform cosine grid with k points per axis (+ 0)."""
+    g = np.union1d(np.linspace(-1.0, 1.0, k), [0.0])
+    mesh = np.stack(np.meshgrid(*([g] * d), indexing="ij"), axis=-1).reshape(-1, d)
+    return mesh[mesh.min(axis=1) <= 0.0]
+
+
+def _refine(d: int, w, sign: float, x0) -> float:
+    """Polish an extremum of sign*A~M~ over X^H (box [-1,1]^d, one coordinate <= 0)."""
+    best = sign * product_symbol(d, w, x0)
+    for j in range(d):  # keep coordinate j non-positive
+        bounds = [(-1.0, 1.0)] * d
+        bounds[j] = (-1.0, 0.0)
+        start = np.clip(x0, [b[0] for b in bounds], [b[1] for b in bounds])
+        res = minimize(lambda x: -sign * product_symbol(d, w, x), start, bounds=bounds,
+                       method="L-BFGS-B", options={"ftol": 1e-15, "gtol": 1e-12})
+        best = max(best, -res.fun)
+    return sign * best
+
+
+def extremes(d: int, w, k: int | None = None):
+    """(lambda_0, lambda_1) = (min, max) of A~ M~ over X^H."""
+    k = k or (1201 if d == 2 else 121)
+    pts = _high_grid(d, k)
+    vals = product_symbol(d, w, pts)
+    lo = _refine(d, w, -1.0, pts[np.argmin(vals)])
+    hi = _refine(d, w, +1.0, pts[np.argmax(vals)])
+    return min(lo, vals.min()), max(hi, vals.max())
+
+
+def optimal(d: int, w):
+    """(mu_opt, omega_opt) of Eqs. (2.6), (2.7) for the stencil weights w."""
+    l0, l1 = extremes(d, w)
+    if l0 <= 0.0:
+        raise ValueError("product symbol not positive on X^H: no convergent omega")
+    return (l1 - l0) / (l1 + l0), 2.0 / (l0 + l1)
+
+
+def smoothing_factor(d: int, wfold, k: int | None = None) -> float:
+    """mu = max_{X^H} |1 - A~ M~| for omega-folded weights."""
+    l0, l1 = extremes(d, wfold, k)
+    return max(abs(1.0 - l0), abs(1.0 - l1))
+
+
+# ---------------------------------------------------------------------------
+# Appendix A and Theorem 3.2 quantities
+# ---------------------------------------------------------------------------
+
+def f_ab(x1, x2, a, b):
+    """f_{a,b}(x1, x2) = [b + a (x1 + x2) + x1 x2] (2 - x1 - x2) (Appendix A)."""
+    return (b + a * (x1 + x2) + x1 * x2) * (2.0 - x1 - x2)
+
+
+def f_ab_extremes(a: float, b: float):
+    """(m_{a,b}, chi_{a,b}): min and max of f_{a,b} over X^H (2D)."""
+    # with 8 gamma = 1, b = 2 alpha, a = 4 beta the product A~M~ of
+    # Upsilon(alpha, beta, gamma) equals f_{a,b} (Sec. 3.1)
+    w = (b / 2.0, a / 4.0, 1.0 / 8.0)
+    return extremes(2, w)
+
+
+# ---------------------------------------------------------------------------
+# two-grid analysis (Sec. 4, Table 1)
+# ---------------------------------------------------------------------------
+
+def two_grid_factor(d: int, wfold, nu: int, n: int = 256) -> float:
+    """LFA two-grid factor rho_h(nu): the largest spectral radius of the
+    2^d x 2^d symbol S^nu K over the low frequencies theta = 2 pi k / n in
+    T^L, theta != 0, where K = I - P~ (A~_H)^{-1} R~ A~_h uses the
+    rediscretised coarse operator (H = 2h), full weighting (symbol
+    prod (1 + cos theta_i)/2 per harmonic) and linear interpolation (the same
+    symbol). The harmonics of theta are theta + pi alpha, alpha in {0,1}^d."""
+    ks = np.arange(-n // 4, n // 4)
+    theta = np.stack(np.meshgrid(*([2.0 * np.pi * ks / n] * d), indexing="ij"), -1).reshape(-1, d)
+    theta = theta[np.any(theta != 0.0, axis=1)]
+    alphas = np.array(list(itertools.product((0, 1), repeat=d)), dtype=np.float64)  # (2^d, d)
+    cos = np.cos(theta[:, None, :] + np.pi * alphas[None, :, :])  # (T, 2^d, d)
+    sx = cos.sum(axis=-1)
+    a_h = 2.0 * (d - sx)
+    m = wfold[0] + 2.0 * wfold[1] * sx
+    if d == 2 and len(wfold) > 2:
+        m = m + 4.0 * wfold[2] * cos[..., 0] * cos[..., 1]
+    s = (1.0 - a_h * m) ** nu
+    r = np.prod((1.0 + cos) / 2.0, axis=-1)  # (T, 2^d)
+    a_H = 2.0 * (d - np.cos(2.0 * theta).sum(axis=-1)) / 4.0  # H = 2h relative to h = 1
+    K = np.eye(2 ** d)[None] - r[:, :, None] * (r * a_h)[:, None, :] / a_H[:, None, None]
+    T = s[:, :, None] * K
+    return float(np.max(np.abs(np.linalg.eigvals(T))))
