@@ -437,14 +437,30 @@ static void cycle(orc_mg *g, int l)
     smooth(g, l, g->nu2);
 }
 
+/* Sum of squares with compensated (Neumaier) summation, so that the norm is
+ * accurate to a few ulps whatever the grid size; a plain running sum of n
+ * positive terms can be off by up to ~n eps relative. */
+static double sum_squares(const double *a, long np)
+{
+    double s = 0.0, comp = 0.0;
+    for (long i = 0; i < np; ++i) {
+        double x = a[i] * a[i];
+        double t = s + x;
+        if (fabs(s) >= fabs(x))
+            comp += (s - t) + x;
+        else
+            comp += (x - t) + s;
+        s = t;
+    }
+    return s + comp;
+}
+
 static double resnorm_scaled(orc_mg *g)
 {
     int n = g->N - 1;
     long np = npoints(g->d, n);
     orc_residual_scaled(g->d, n, 0, g->u[0], g->bh[0], g->rh[0]);
-    double s = 0.0;
-    for (long i = 0; i < np; ++i) s += g->rh[0][i] * g->rh[0][i];
-    return sqrt(s);
+    return sqrt(sum_squares(g->rh[0], np));
 }
 
 static void load_rhs(orc_mg *g, const double *b)

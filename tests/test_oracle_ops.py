@@ -159,3 +159,14 @@ def test_cycle_rates(d, N, name, nu1, nu2, gamma, cyc, rate):
     # the history is monotone and ends below the tolerance
     assert np.all(np.diff(res.hist) < 0)
     assert res.hist[-1] <= 1e-10 * res.hist[0]
+
+
+def test_residual_norm_is_accurately_summed():
+    """||b - A u||_2 (Eq. (4.1)) on a 1M-point grid agrees with an exactly
+    rounded sum (math.fsum) of the squared residual to 1e-14."""
+    import math
+    N = 1024
+    u, b = _rand(2, N - 1, 21), _rand(2, N - 1, 22)
+    r = b.ravel() - exact.laplacian(2, N) @ u.ravel()
+    ref = math.sqrt(math.fsum(r * r))
+    assert oracle.residual_norm(u, b) == pytest.approx(ref, rel=1e-14)
