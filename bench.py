@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the SPAI-smoothed multigrid solver on one GB300.
+
+Workload (the headline configuration): 2D Poisson, 5-point stencil, N = 8192
+(8191^2 = 67,092,481 unknowns), FP64, b ~ U[-1, 1] (numpy seed 0), zero
+initial guess, V(1,1) cycles with the M9 SPAI smoother (Theorem 3.1), full
+weighting, bilinear interpolation, 12 levels, solved to a 1e-10 relative
+residual. One step = one complete solve (about ten cycles) with b resident
+in HBM; every field (537 MB) is larger than L2, so no flush is needed.
+
+value = unknowns x V-cycles / second (DOF/s), summed over ranks; each rank
+solves its own replica of the problem (the single-problem path does not
+shard). Printed as one JSON line by rank 0.
+
+--impl reference times the FP64 CPU oracle (the checker in oracle/) on this
+machine's host cores on the same workload; each step is a bounded sample,
+one V(1,1) cycle of the full-size problem.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V(1,1)-cycles/s & DOF/s, % HBM peak; time-to-1e-10 mixed vs FP64 on GPU"
+D, N, TOL, SEED = 2, 8192, 1e-10, 0
+NU1 = NU2 = 1
+UNKNOWNS = (N - 1) ** D
+WORKLOAD = "poisson2d-N8192-fp64-V(1,1)-M9-tol1e-10"
+# FP64 operations per point of one finest-level sweep with unscaled b, in the
+# kernel's canonical formula: h^2 b (1 mul), s (3 add), rh (fma + add),
+# hp (1 add), E (2 add), C (1 add), update (3 fma) = 13.
+SWEEP_DP_OPS_PER_POINT = 13
+# algorithmic bytes per point of one sweep: read u, read b, write u' (FP64)
+SWEEP_BYTES_PER_POINT = 24
+# FP64 pipe: 2 operations (add, mul or fma) per SM per clock on this part
+FP64_OPS_PER_SM_CLK = 2
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "yes", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: one V(1,1) cycle of the
+    full-size workload per step (single-threaded C)."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from oracle import coeffs
+    from paper_2206_05543_gb300 import inputs
+
+    b = inputs.uniform(D, N, SEED)
+    u = np.zeros_like(b)
+    w = coeffs.default(D)
+    for _ in range(args.warmup):
+        oracle.cycles(b, u, w, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = oracle.cycles(b, u, w, 1)
+    dt = time.perf_counter() - t0
+    value = UNKNOWNS * args.steps / dt
+    sample = f"{args.steps} V(1,1) cycles of the full-size {WORKLOAD} problem (oracle.cycles, C, 1 thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "d": D, "N": N, "unknowns": UNKNOWNS},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def _cpu_baseline_sample():
+    """The oracle timed on a bounded sample: one V(1,1) cycle of the full
+    problem (about 10-20 s of single-threaded CPU work)."""
+    import numpy as np
+
+    import oracle
+    from oracle import coeffs
+    from paper_2206_05543_gb300 import inputs
+
+    b = inputs.uniform(D, N, SEED)
+    u = np.zeros_like(b)
+    t0 = time.perf_counter()
+    oracle.cycles(b, u, coeffs.default(D), 1)
+    dt = time.perf_counter() - t0
+    return {"value": UNKNOWNS / dt, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 V(1,1) cycle of the full-size problem in {dt:.1f} s (C oracle, 1 thread)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2206_05543_gb300 import binding, inputs, smoothers
+    from paper_2206_05543_gb300.binding import Solver
+
+    peaks = _peaks()
+    stream = torch.cuda.current_stream()
+    b_host = torch.from_numpy(inputs.uniform(D, N, SEED)).pin_memory()
+    b = b_host.to("cuda", non_blocking=False)
+    u = torch.zeros_like(b)
+    solver = Solver(D, N, smoothers.M9, nu1=NU1, nu2=NU2, precision="fp64")
+
+    def one_solve():
+        u.zero_()
+        return solver.solve(b, u, tol=TOL, max_cycles=100)
+
+    for _ in range(args.warmup):
+        info = one_solve()
+    assert info.converged, info.status
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = binding.kernel_launch_count()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cycles = 0
+    for _ in range(args.steps):
+        info = one_solve()
+        cycles += info.cycles
+    e1.record(stream)
+    barrier()
+    launches = binding.kernel_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms, cycles], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        ms, total_cycles = float(tmax[0]), float(tsum[1])
+    else:
+        total_cycles = cycles
+    value = UNKNOWNS * total_cycles / (ms * 1e-3)
+
+    # end to end through the public API: pinned host b -> device, solve,
+    # solution back to pinned host memory, every step
+    u_host = torch.empty_like(b_host).pin_memory()
+    b_dev = torch.empty_like(b)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    e2e_cycles = 0
+    for _ in range(args.steps):
+        b_dev.copy_(b_host, non_blocking=True)
+        u.zero_()
+        info = solver.solve(b_dev, u, tol=TOL, max_cycles=100)
+        e2e_cycles += info.cycles
+        u_host.copy_(u, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    clocks.stop()
+    e2e_ms = f0.elapsed_time(f1)
+    e2e_value = world * UNKNOWNS * e2e_cycles / (e2e_ms * 1e-3)
+
+    # dominant kernel: the finest-level FP64 sweep, timed alone on the stream
+    # it is launched on, same launch configuration as inside the cycle
+    out = torch.empty_like(b)
+    ur = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, b.shape)).cuda()
+    for _ in range(3):
+        binding.op_sweep(ur, b, smoothers.M9, b_unscaled=True, stream=stream, out=out)
+    reps = 20
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        binding.op_sweep(ur, b, smoothers.M9, b_unscaled=True, stream=stream, out=out)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    sweep_s = k0.elapsed_time(k1) * 1e-3 / reps
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_ops = FP64_OPS_PER_SM_CLK * sms * peaks["sm_max_mhz"] * 1e6
+    achieved_ops = SWEEP_DP_OPS_PER_POINT * UNKNOWNS / sweep_s
+    sweep_gbs = SWEEP_BYTES_PER_POINT * UNKNOWNS / sweep_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("sweep2d_fp64_n8191")
+
+    # time to 1e-10: FP64 vs FP32-in-FP64 refinement on the same 2D grid
+    mixed = Solver(D, N, smoothers.M9, nu1=NU1, nu2=NU2, precision="fp32_ir")
+    um = torch.zeros_like(b)
+    for _ in range(2):
+        um.zero_()
+        minfo = mixed.solve(b, um, tol=TOL, max_cycles=100)
+    barrier()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    um.zero_()
+    minfo = mixed.solve(b, um, tol=TOL, max_cycles=100)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mixed_ms = m0.elapsed_time(m1)
+    mixed.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "d": D, "N": N, "unknowns": UNKNOWNS, "smoother": "M9",
+                       "cycle": "V(1,1)", "levels": 12, "tol": TOL, "rhs": "U[-1,1] seed 0", "u0": "zero",
+                       "l2": "no flush: every field (537 MB) is larger than L2",
+                       "parallelism": f"replicas{world}"},
+            "vcycles_per_s": total_cycles / (ms * 1e-3) / world,
+            "cycles_per_solve": cycles / args.steps,
+            "time_to_tol_ms": ms / args.steps,
+            "mixed_fp32_ir": {"time_to_tol_ms": mixed_ms, "iterations": minfo.cycles,
+                              "relres": minfo.relres, "speedup_vs_fp64": (ms / args.steps) / mixed_ms},
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": peak_ops / 1e9,
+                         "unit": "Gop/s FP64", "frac": achieved_ops / peak_ops, "traffic": traffic,
+                         "kernel": "sweep2d_kernel<double> (finest level, n=8191)",
+                         "peak_basis": f"{FP64_OPS_PER_SM_CLK} FP64 ops/SM/clk x {sms} SMs x "
+                                       f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['source']})",
+                         "hbm_gbs": sweep_gbs, "hbm_frac": sweep_gbs / peaks["hbm_gbs"],
+                         "ms_per_launch": sweep_s * 1e3},
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": b.numel() * 8,
+                    "d2h_bytes_per_step": u.numel() * 8},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline_sample()
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

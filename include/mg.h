@@ -1,0 +1,143 @@
+/*
+ * mg.h -- C ABI of the GB300 (sm_103a) geometric-multigrid library for the
+ * Dirichlet Poisson problem with the SPAI smoothers of He, Liu and Wang,
+ * "Optimized sparse approximate inverse smoothers for solving Laplacian
+ * linear systems" (arXiv:2206.05543).
+ *
+ * Problem (Sec. 1, Eqs. (1.1)-(1.3)): A_h u_h = b_h on the interior points of
+ * (0,1)^d, d = 2 (5-point stencil) or d = 3 (7-point stencil), h = 1/N, N a
+ * power of two >= 4. Non-zero boundary data g is folded into b by the caller.
+ *
+ * Smoother (Sec. 2, Eq. (2.1)): u <- u + omega M_h (b_h - A_h u) with M_h a
+ * symmetric stencil proportional to h^2 (Sec. 3). The library takes the
+ * omega-folded, h-free weights
+ *     2D: c = (c0, c1, c2) = omega * (centre, edge, corner) / h^2
+ *     3D: c = (c0, c1)     = omega * (centre, face) / h^2
+ * e.g. M9 = Upsilon(44,10,3)/24 with omega = (309 - 12 sqrt 10)/1720
+ * (Theorem 3.1) gives c = omega*(44, 10, 3)/24; M7 = T(8/5, 2/5) with
+ * omega = 20/73 (Theorem 3.2) gives c = (16/73, 2/73). Fewer weights than
+ * the maximum leave the rest zero (Jacobi: one weight, M5: two).
+ *
+ * Cycle (Sec. 4): re-discretised coarse operators (H = 2h), full-weighting
+ * restriction, bilinear/trilinear interpolation, nu1 pre- and nu2
+ * post-smoothing sweeps, coarsest grid h0 = 1/4 solved exactly, stopping on
+ * ||b - A u_k||_2 <= tol ||b - A u_0||_2.
+ *
+ * Layout of every grid array crossing this ABI: interior points only,
+ * row-major with x fastest, (N-1)^d elements: a[y*(N-1) + x] in 2D,
+ * a[(z*(N-1) + y)*(N-1) + x] in 3D; index i is the grid point (i+1)h.
+ * Grid arrays are DEVICE pointers unless stated otherwise; the caller owns
+ * them, and they must stay valid until the work queued on the context's
+ * stream has finished.
+ *
+ * Errors: every call returns an mg_status; no exception crosses the ABI.
+ * On MG_ECUDA the CUDA error text is available from mg_last_cuda_error().
+ * All work runs on the stream given to mg_setup; calls that return numbers
+ * to the host (norms, cycle counts) synchronise that stream.
+ */
+#ifndef MG_H
+#define MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx; /* opaque; owns every coarse-level buffer */
+
+typedef enum {
+    MG_OK = 0,
+    MG_EINVAL = -1,   /* bad argument: d, N, weights, nu, null pointer ... */
+    MG_ENOMEM = -2,   /* device or pinned host allocation failed */
+    MG_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    MG_ENOCONV = -4,  /* max_cycles ran out; u and the history are still written */
+    MG_ENAN = -5,     /* the residual norm became NaN or Inf */
+    MG_ETIMEOUT = -6  /* a bounded device-side wait gave up */
+} mg_status;
+
+typedef enum {
+    MG_FP64 = 0,   /* every level and every operation in FP64 */
+    MG_FP32_IR = 1 /* FP32 cycle inside FP64 iterative refinement: the outer
+                      residual b - A u and the update u += e in FP64 */
+} mg_prec;
+
+/* ---------------------------------------------------------------------- */
+/* solver context                                                         */
+/* ---------------------------------------------------------------------- */
+
+/* Create a solver for dimension d (2 or 3) and grid N (power of two, >= 4).
+ * spai_coeffs: HOST array of ncoeffs omega-folded weights (see above;
+ * 1..3 in 2D, 1..2 in 3D). nu1, nu2 >= 0 sweeps, nu1 + nu2 >= 1.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Allocates the level hierarchy on the current device. MG_EINVAL, MG_ENOMEM
+ * or MG_ECUDA on failure (*out is then NULL). */
+mg_status mg_setup(int d, int N, const double *spai_coeffs, int ncoeffs, int nu1, int nu2,
+                   mg_prec prec, void *cuda_stream, mg_ctx **out);
+
+/* Like mg_setup, with gamma coarse-grid visits per level: 1 = V cycle,
+ * 2 = W cycle (Sec. 4 tests W(1+0) and V(1+1)). */
+mg_status mg_setup_ex(int d, int N, const double *spai_coeffs, int ncoeffs, int nu1, int nu2,
+                      int gamma, mg_prec prec, void *cuda_stream, mg_ctx **out);
+
+/* One cycle in place on u for right-hand side b (device arrays, FP64,
+ * (N-1)^d). MG_FP64: one V/W cycle. MG_FP32_IR: one refinement step (FP64
+ * residual, FP32 cycle for the correction, FP64 update). Asynchronous. */
+mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b);
+
+/* Solve from the initial guess in u until ||b - A u_k||_2 <= tol ||b - A u_0||_2
+ * or max_cycles cycles ran (Sec. 4). b, u: device FP64 arrays. cycles_out,
+ * relres_out (= ||r_k||/||r_0||): nullable HOST pointers. hist_out: nullable
+ * HOST array of max_cycles + 1 doubles receiving ||r_k||_2, k = 0..cycles.
+ * Returns MG_OK, MG_ENOCONV (u and outputs still written) or MG_ENAN.
+ * Synchronises the stream once per cycle. */
+mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
+                   double *relres_out, double *hist_out);
+
+/* ||b - A_h u||_2 (FP64) of device arrays u, b; result in *norm_out (HOST). */
+mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out);
+
+void mg_destroy(mg_ctx *ctx);
+
+/* ---------------------------------------------------------------------- */
+/* single operators on one level (each step of the cycle, for checking)    */
+/* ---------------------------------------------------------------------- */
+/* n = points per axis of the level (N_l - 1, odd, >= 3); arrays in the
+ * interior layout of that level, device pointers. prec selects the element
+ * type: MG_FP64 -> double, MG_FP32_IR -> float. bh is the scaled right-hand
+ * side h_l^2 b_l unless b_unscaled != 0, in which case b is unscaled and the
+ * kernel forms h^2 b itself (h = 1/(n+1)). stream: cudaStream_t. */
+
+/* One SPAI sweep u_out = u + W (bh - h^2 A u) (Sec. 2, Eq. (2.1)); u == NULL
+ * means u = 0. If rnorm2_out (HOST) is non-NULL it receives the sum of the
+ * squared scaled residuals h^4 |b - A u|^2 of the input u; this synchronises. */
+mg_status mg_op_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs, const void *u,
+                      const void *bh, int b_unscaled, void *u_out, double *rnorm2_out, void *stream);
+
+/* Scaled residual rh = bh - h^2 A u (Sec. 1, Eq. (1.3)). */
+mg_status mg_op_residual(int d, int n, mg_prec prec, const void *u, const void *bh, int b_unscaled,
+                         void *rh_out, void *stream);
+
+/* Coarse right-hand side bh_c = 4 R (bh - h^2 A u), full weighting R
+ * (Sec. 4); bh_c has ((n-1)/2)^d points. */
+mg_status mg_op_residual_restrict(int d, int n, mg_prec prec, const void *u, const void *bh, int b_unscaled,
+                                  void *bh_coarse_out, void *stream);
+
+/* u += P e, P = bilinear/trilinear interpolation of the coarse correction
+ * e (((n-1)/2)^d points) (Sec. 4), in place on u. */
+mg_status mg_op_prolong_correct(int d, int n, mg_prec prec, const void *e_coarse, void *u, void *stream);
+
+/* Exact solve of h0^2 A_h0 x = bh on the coarsest grid (n = 3, 3^d points). */
+mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* diagnostics                                                            */
+/* ---------------------------------------------------------------------- */
+const char *mg_strerror(mg_status status);
+const char *mg_last_cuda_error(void);
+/* Number of kernels the library launched (directly or as graph nodes)
+ * since the process started; graph replays count every node. */
+unsigned long long mg_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of the C ABI in include/mg.h (argument marshalling only).
+
+Every numerical step runs inside libmg.so (CUDA, sm_103a); this module only
+passes torch tensors' device pointers, the current CUDA stream and sizes
+across the ABI and turns status codes into exceptions. There is no fallback:
+if the library or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+from . import smoothers
+
+MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOCONV, MG_ENAN, MG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+MG_FP64, MG_FP32_IR = 0, 1
+PRECISIONS = {"fp64": MG_FP64, "fp32_ir": MG_FP32_IR, "mixed": MG_FP32_IR}
+
+_lock = threading.Lock()
+_lib = None
+
+#: symbols declared in include/mg.h, with (restype, argtypes)
+_P, _I, _D, _U = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+SIGNATURES = {
+    "mg_setup": (_I, [_I, _I, _DP, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
+    "mg_setup_ex": (_I, [_I, _I, _DP, _I, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
+    "mg_vcycle": (_I, [_P, _P, _P]),
+    "mg_solve": (_I, [_P, _P, _P, _D, _I, _IP, _DP, _DP]),
+    "mg_residual_norm": (_I, [_P, _P, _P, _DP]),
+    "mg_destroy": (None, [_P]),
+    "mg_op_sweep": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _DP, _P]),
+    "mg_op_residual": (_I, [_I, _I, _I, _P, _P, _I, _P, _P]),
+    "mg_op_residual_restrict": (_I, [_I, _I, _I, _P, _P, _I, _P, _P]),
+    "mg_op_prolong_correct": (_I, [_I, _I, _I, _P, _P, _P]),
+    "mg_op_coarse_solve": (_I, [_I, _I, _P, _P, _P]),
+    "mg_strerror": (ctypes.c_char_p, [_I]),
+    "mg_last_cuda_error": (ctypes.c_char_p, []),
+    "mg_kernel_launch_count": (_U, []),
+}
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {lib().mg_strerror(status).decode()} ({status})"
+        if status == MG_ECUDA:
+            msg += f": {lib().mg_last_cuda_error().decode()}"
+        super().__init__(msg)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libmg.so (building it with nvcc when stale or missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str, ok=(MG_OK,)):
+    if status not in ok:
+        raise MGError(status, where)
+    return status
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA GPU is required: this library has no CPU path")
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _coeff_array(c):
+    arr = (ctypes.c_double * len(c))(*[float(x) for x in c])
+    return arr, len(c)
+
+
+def _dev_ptr(t, dtype, shape, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_launch_count() -> int:
+    return int(lib().mg_kernel_launch_count())
+
+
+class SolveInfo:
+    def __init__(self, u, status, cycles, relres, hist):
+        self.u, self.status, self.cycles, self.relres, self.hist = u, status, cycles, relres, hist
+
+    @property
+    def converged(self) -> bool:
+        return self.status == MG_OK
+
+    def rate(self) -> float:
+        """rho^(k) = (||r_k|| / ||r_0||)^(1/k) at the last cycle (Sec. 4, Eq. (4.1))."""
+        k = self.cycles
+        return float((self.hist[k] / self.hist[0]) ** (1.0 / k)) if k > 0 else 0.0
+
+
+class Solver:
+    """Multigrid solver for A_h u = b on (0,1)^d, h = 1/N (one CUDA context object).
+
+    coeffs: omega-folded SPAI weights (see smoothers.py; default M9 / M7).
+    precision: "fp64" (plain FP64 cycle) or "fp32_ir" (FP32 cycle inside FP64
+    iterative refinement). gamma = 1: V cycle, 2: W cycle.
+    """
+
+    def __init__(self, d: int, N: int, coeffs=None, nu1: int = 1, nu2: int = 1, gamma: int = 1,
+                 precision: str = "fp64", stream=None):
+        torch = _torch()
+        self.d, self.N = int(d), int(N)
+        self.n = self.N - 1
+        self.shape = (self.n,) * self.d
+        self.coeffs = tuple(coeffs if coeffs is not None else smoothers.default(self.d))
+        self.precision = precision
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        arr, nc = _coeff_array(self.coeffs)
+        ctx = ctypes.c_void_p()
+        _check(lib().mg_setup_ex(self.d, self.N, arr, nc, nu1, nu2, gamma, PRECISIONS[precision],
+                                 ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(ctx)), "mg_setup")
+        self._ctx = ctx
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().mg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _args(self, u, b):
+        torch = _torch()
+        return (_dev_ptr(u, torch.float64, self.shape, "u"), _dev_ptr(b, torch.float64, self.shape, "b"))
+
+    def vcycle(self, u, b):
+        """One cycle in place on u (asynchronous on the solver's stream)."""
+        pu, pb = self._args(u, b)
+        _check(lib().mg_vcycle(self._ctx, pu, pb), "mg_vcycle")
+        return u
+
+    def solve(self, b, u=None, tol: float = 1e-10, max_cycles: int = 100) -> SolveInfo:
+        torch = _torch()
+        if u is None:
+            u = torch.zeros(self.shape, dtype=torch.float64, device=b.device)
+        pu, pb = self._args(u, b)
+        hist = np.zeros(max_cycles + 1)
+        cyc = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = lib().mg_solve(self._ctx, pb, pu, float(tol), int(max_cycles), ctypes.byref(cyc), ctypes.byref(rel),
+                            hist.ctypes.data_as(_DP))
+        _check(st, "mg_solve", ok=(MG_OK, MG_ENOCONV, MG_ENAN))
+        return SolveInfo(u, st, cyc.value, rel.value, hist[: cyc.value + 1].copy())
+
+    def residual_norm(self, u, b) -> float:
+        pu, pb = self._args(u, b)
+        out = ctypes.c_double(0.0)
+        _check(lib().mg_residual_norm(self._ctx, pu, pb, ctypes.byref(out)), "mg_residual_norm")
+        return out.value
+
+
+# ---------------------------------------------------------------------------
+# single operators (one level; arrays in that level's interior layout)
+# ---------------------------------------------------------------------------
+
+def _prec_of(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return MG_FP64
+    if t.dtype == torch.float32:
+        return MG_FP32_IR
+    raise TypeError("float64 or float32 tensors expected")
+
+
+def _level(t):
+    d = t.dim()
+    n = t.shape[0]
+    if d not in (2, 3) or any(s != n for s in t.shape):
+        raise ValueError("expected an (n, n) or (n, n, n) tensor")
+    return d, n
+
+
+def op_sweep(u, bh, coeffs, b_unscaled: bool = False, want_norm: bool = False, stream=None, out=None):
+    """One SPAI sweep; u None = zero initial value. Returns (u_out, sum rh^2 or None)."""
+    torch = _torch()
+    d, n = _level(bh)
+    prec = _prec_of(bh)
+    if out is None:
+        out = torch.empty_like(bh)
+    else:
+        _dev_ptr(out, bh.dtype, bh.shape, "out")
+    arr, nc = _coeff_array(coeffs)
+    pu = ctypes.c_void_p(0) if u is None else _dev_ptr(u, bh.dtype, bh.shape, "u")
+    nrm = ctypes.c_double(0.0)
+    _check(lib().mg_op_sweep(d, n, prec, arr, nc, pu, _dev_ptr(bh, bh.dtype, bh.shape, "bh"), int(b_unscaled),
+                             ctypes.c_void_p(out.data_ptr()), ctypes.byref(nrm) if want_norm else None,
+                             _stream_ptr(stream)), "mg_op_sweep")
+    return out, (nrm.value if want_norm else None)
+
+
+def op_residual(u, bh, b_unscaled: bool = False, stream=None):
+    torch = _torch()
+    d, n = _level(bh)
+    out = torch.empty_like(bh)
+    _check(lib().mg_op_residual(d, n, _prec_of(bh), _dev_ptr(u, bh.dtype, bh.shape, "u"),
+                                _dev_ptr(bh, bh.dtype, bh.shape, "bh"), int(b_unscaled),
+                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "mg_op_residual")
+    return out
+
+
+def op_residual_restrict(u, bh, b_unscaled: bool = False, stream=None):
+    torch = _torch()
+    d, n = _level(bh)
+    nc = (n - 1) // 2
+    out = torch.empty((nc,) * d, dtype=bh.dtype, device=bh.device)
+    _check(lib().mg_op_residual_restrict(d, n, _prec_of(bh), _dev_ptr(u, bh.dtype, bh.shape, "u"),
+                                         _dev_ptr(bh, bh.dtype, bh.shape, "bh"), int(b_unscaled),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "mg_op_residual_restrict")
+    return out
+
+
+def op_prolong_correct(e_coarse, u, stream=None):
+    """u += P e_coarse in place; returns u."""
+    d, nc = _level(e_coarse)
+    n = 2 * nc + 1
+    _check(lib().mg_op_prolong_correct(d, n, _prec_of(u), _dev_ptr(e_coarse, u.dtype, (nc,) * d, "e"),
+                                       _dev_ptr(u, u.dtype, (n,) * d, "u"), _stream_ptr(stream)),
+           "mg_op_prolong_correct")
+    return u
+
+
+def op_coarse_solve(bh, stream=None):
+    torch = _torch()
+    d, n = _level(bh)
+    if n != 3:
+        raise ValueError("the coarsest grid has 3 points per axis")
+    out = torch.empty_like(bh)
+    _check(lib().mg_op_coarse_solve(d, _prec_of(bh), _dev_ptr(bh, bh.dtype, bh.shape, "bh"),
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "mg_op_coarse_solve")
+    return out

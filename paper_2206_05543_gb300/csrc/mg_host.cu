@@ -1,0 +1,769 @@
+// mg_host.cu -- solver contexts, cycle scheduling, CUDA-graph capture and the
+// C ABI declared in include/mg.h (He, Liu, Wang, arXiv:2206.05543, Sec. 4).
+//
+// A context owns the level hierarchy N, N/2, ..., 4 of one problem. The
+// cycle is recorded once into two CUDA graphs on a private stream:
+//   pre  - the first smoothing sweep on the finest level, which also yields
+//          ||b - A u_k|| of its input (or the FP64 residual in refinement
+//          mode), the fixed-order reduction and the copy of the norm to
+//          pinned host memory;
+//   rest - the remainder of the cycle: restriction, coarse levels (the last
+//          ones inside one block, see mg_tail.cu), interpolation and the
+//          post-smoothing sweeps.
+// mg_solve replays rest + pre once per cycle and reads one double back, so
+// the stopping test costs one synchronisation per cycle and a converged u is
+// never touched again (the pre sweep writes to the ping-pong buffer).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local unsigned long long *g_capture_counter = nullptr;
+static thread_local char g_last_error[256] = "";
+
+void count_launch(unsigned long long k)
+{
+    if (g_capture_counter)
+        *g_capture_counter += k;
+    else
+        g_launches += k;
+}
+
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            sms = v;
+        else
+            sms = 152;
+    }
+    return sms;
+}
+
+static mg_status cuda_fail(cudaError_t e)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return MG_ECUDA;
+}
+
+#define MG_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_);     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+__global__ void sum_partials_kernel(const double *__restrict__ p, int np, double *__restrict__ out)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) v += p[i];
+    block_sum_store<256>(v, out);
+}
+
+cudaError_t launch_sum_partials(const double *partials, int np, double *out, cudaStream_t s)
+{
+    sum_partials_kernel<<<1, 256, 0, s>>>(partials, np, out);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void add_to_f64_kernel(double *__restrict__ u, const T *__restrict__ e, size_t np)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < np; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = __dadd_rn(u[i], (double)e[i]);
+}
+
+template <typename T>
+cudaError_t launch_add_to_f64(double *u, const T *e, size_t np, cudaStream_t s)
+{
+    const int blocks = (int)std::min<size_t>((np + 255) / 256, (size_t)num_sms() * 8);
+    add_to_f64_kernel<T><<<blocks, 256, 0, s>>>(u, e, np);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void scale_copy_kernel(const double *__restrict__ b, T *__restrict__ bh, size_t np, double h2)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < np; i += (size_t)gridDim.x * blockDim.x)
+        bh[i] = (T)__dmul_rn(h2, b[i]);
+}
+
+template <typename T>
+cudaError_t launch_scale_copy(const double *b, T *bh, size_t np, double h2, cudaStream_t s)
+{
+    const int blocks = (int)std::min<size_t>((np + 255) / 256, (size_t)num_sms() * 8);
+    scale_copy_kernel<T><<<blocks, 256, 0, s>>>(b, bh, np, h2);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// dispatch on the dimension
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t op_sweep(int d, const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
+                            double *partials, cudaStream_t s)
+{
+    return d == 2 ? launch_sweep2d<T>(u, b, unscaled, out, n, c, partials, s)
+                  : launch_sweep3d<T>(u, b, unscaled, out, n, c, partials, s);
+}
+template <typename T>
+static cudaError_t op_resrestrict(int d, const T *u, const T *b, bool unscaled, T *bc, int n, cudaStream_t s)
+{
+    return d == 2 ? launch_resrestrict2d<T>(u, b, unscaled, bc, n, s)
+                  : launch_resrestrict3d<T>(u, b, unscaled, bc, n, s);
+}
+template <typename T>
+static cudaError_t op_prolong(int d, const T *e, T *u, int n, cudaStream_t s)
+{
+    return d == 2 ? launch_prolong2d<T>(e, u, n, s) : launch_prolong3d<T>(e, u, n, s);
+}
+template <typename InT, typename OutT>
+static cudaError_t op_residual(int d, const InT *u, const InT *b, bool unscaled, OutT *rh, int n,
+                               double *partials, cudaStream_t s)
+{
+    return d == 2 ? launch_residual2d<InT, OutT>(u, b, unscaled, rh, n, partials, s)
+                  : launch_residual3d<InT, OutT>(u, b, unscaled, rh, n, partials, s);
+}
+static int sweep_partials(int d, int n)
+{
+    if (d == 2) {
+        const Grid2 g = sweep2d_grid(n);
+        return g.bx * g.by;
+    }
+    const Grid3 g = sweep3d_grid(n);
+    return g.bx * g.by * g.bz;
+}
+static int residual_partials(int d, int n)
+{
+    if (d == 2) return sweep_partials(2, n);
+    const Grid3 g = residual3d_grid(n);
+    return g.bx * g.by * g.bz;
+}
+
+static size_t npoints(int d, int n) { return d == 2 ? (size_t)n * n : (size_t)n * n * n; }
+
+static bool valid_N(int N)
+{
+    if (N < 4 || N > (1 << 20)) return false;
+    return (N & (N - 1)) == 0;
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct GraphPair {
+    cudaGraphExec_t pre = nullptr, rest = nullptr;
+    unsigned long long pre_nodes = 0, rest_nodes = 0;
+};
+
+struct mg_ctx {
+    int d = 2, N = 0, L = 0, nu1 = 1, nu2 = 1, gamma = 1, lt = 0, dev = 0;
+    mg_prec prec = MG_FP64;
+    double c[3] = {0, 0, 0};
+    int ncoef = 0;
+    cudaStream_t user = nullptr, s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // hierarchy in the cycle's precision (double or float); level 0 of an
+    // FP64 context uses the caller's u and (unscaled) b for A and BH
+    std::vector<int> n;
+    std::vector<void *> A, B, BH, RH;
+    size_t esize = 8;
+    double *lu = nullptr;
+    double *partials = nullptr;
+    int npartials = 0;
+    double *d_norm2 = nullptr;
+    double *h_norm2 = nullptr;  // pinned
+    GraphPair g;
+    const void *cap_u = nullptr, *cap_b = nullptr;
+    std::vector<void *> owned;  // device allocations to free
+    // batched contexts
+    std::vector<mg_ctx *> members;
+};
+
+static void free_graphs(mg_ctx *c)
+{
+    if (c->g.pre) cudaGraphExecDestroy(c->g.pre);
+    if (c->g.rest) cudaGraphExecDestroy(c->g.rest);
+    c->g = GraphPair{};
+    c->cap_u = c->cap_b = nullptr;
+}
+
+static void destroy_ctx(mg_ctx *c)
+{
+    if (!c) return;
+    for (mg_ctx *m : c->members) destroy_ctx(m);
+    free_graphs(c);
+    for (void *p : c->owned) cudaFree(p);
+    if (c->h_norm2) cudaFreeHost(c->h_norm2);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->s) cudaStreamDestroy(c->s);
+    delete c;
+}
+
+static mg_status dalloc(mg_ctx *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return MG_ENOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    c->owned.push_back(*p);
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cycle recording
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+struct Recorder {
+    mg_ctx *c;
+    const T *b0;       // finest-level right-hand side (unscaled in FP64 mode)
+    bool b0_unscaled;
+    T *A0;             // finest-level primary buffer
+
+    T *A(int l) { return l == 0 ? A0 : (T *)c->A[l]; }
+    T *B(int l) { return (T *)c->B[l]; }
+    const T *BH(int l) { return l == 0 ? b0 : (const T *)c->BH[l]; }
+    bool unsc(int l) { return l == 0 && b0_unscaled; }
+
+    // ops of the tail kernel for a visit of level l (host recursion, the same
+    // order as the reference cycle)
+    void tail_ops(TailArgs &a, int l, bool &ok)
+    {
+        auto push = [&](int kind, int lev) {
+            if (a.nops >= kMaxTailOps) {
+                ok = false;
+                return;
+            }
+            a.ops[a.nops].kind = (short)kind;
+            a.ops[a.nops].level = (short)(lev - c->lt);
+            ++a.nops;
+        };
+        if (c->n[l] == 3) {
+            push(TAIL_SOLVE, l);
+            return;
+        }
+        for (int s = 0; s < c->nu1; ++s) push(TAIL_SWEEP, l);
+        push(TAIL_RESTRICT, l);
+        push(TAIL_ZERO, l + 1);
+        for (int g = 0; g < c->gamma; ++g) tail_ops(a, l + 1, ok);
+        push(TAIL_PROLONG, l);
+        for (int s = 0; s < c->nu2; ++s) push(TAIL_SWEEP, l);
+    }
+
+    cudaError_t tail(int l, bool zero_start)
+    {
+        TailArgs a;
+        memset(&a, 0, sizeof a);
+        a.d = c->d;
+        a.lu = c->lu;
+        for (int j = 0; j < 3; ++j) a.c[j] = c->c[j];
+        for (int k = c->lt; k < c->L; ++k) {
+            TailLevel &tl = a.lv[k - c->lt];
+            tl.u = A(k);
+            tl.tmp = B(k);
+            tl.bh = (void *)c->BH[k];  // the tail always reads a scaled rhs buffer
+            tl.rh = c->RH[k];
+            tl.n = c->n[k];
+        }
+        bool ok = true;
+        if (zero_start) {
+            a.ops[a.nops].kind = TAIL_ZERO;
+            a.ops[a.nops].level = (short)(l - c->lt);
+            ++a.nops;
+        }
+        tail_ops(a, l, ok);
+        if (!ok) return cudaErrorInvalidValue;
+        return launch_tail<T>(a, c->s);
+    }
+
+    // Record the remainder of a visit of level l whose current value is in
+    // A(l) (or zero when zero_start). `skip_first` says the first pre-sweep
+    // A(l) -> B(l) was already recorded elsewhere. On return the new value
+    // is in A(l).
+    cudaError_t visit(int l, bool zero_start, bool skip_first)
+    {
+        cudaError_t e;
+        if (l >= c->lt) {
+            if (l == 0 && b0_unscaled) {
+                // finest level inside the tail: form the scaled rhs first
+                e = launch_scale_copy<T>((const double *)b0, (T *)c->BH[0], npoints(c->d, c->n[0]),
+                                         1.0 / ((double)c->N * c->N), c->s);
+                if (e) return e;
+            }
+            return tail(l, zero_start);
+        }
+        const int n = c->n[l];
+        T *buf[2] = {A(l), B(l)};
+        int cur = 0;
+        bool zero = zero_start;
+        for (int s = 0; s < c->nu1; ++s) {
+            if (s == 0 && skip_first) {
+                cur = 1;
+                zero = false;
+                continue;
+            }
+            e = op_sweep<T>(c->d, zero ? nullptr : buf[cur], BH(l), unsc(l), buf[1 - cur], n, c->c, nullptr, c->s);
+            if (e) return e;
+            cur = 1 - cur;
+            zero = false;
+        }
+        if (zero) {
+            e = cudaMemsetAsync(buf[cur], 0, npoints(c->d, n) * sizeof(T), c->s);
+            if (e) return e;
+        }
+        e = op_resrestrict<T>(c->d, buf[cur], BH(l), unsc(l), (T *)c->BH[l + 1], n, c->s);
+        if (e) return e;
+        for (int g = 0; g < c->gamma; ++g) {
+            e = visit(l + 1, g == 0, false);
+            if (e) return e;
+        }
+        e = op_prolong<T>(c->d, A(l + 1), buf[cur], n, c->s);
+        if (e) return e;
+        for (int s = 0; s < c->nu2; ++s) {
+            e = op_sweep<T>(c->d, buf[cur], BH(l), unsc(l), buf[1 - cur], n, c->c, nullptr, c->s);
+            if (e) return e;
+            cur = 1 - cur;
+        }
+        if (cur != 0) {
+            e = cudaMemcpyAsync(buf[0], buf[1], npoints(c->d, n) * sizeof(T), cudaMemcpyDeviceToDevice, c->s);
+            if (e) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+template <typename F>
+static mg_status capture(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nodes, F &&body)
+{
+    cudaGraph_t graph = nullptr;
+    unsigned long long counter = 0;
+    MG_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+    g_capture_counter = &counter;
+    cudaError_t e = body();
+    g_capture_counter = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *nodes = counter;
+    return MG_OK;
+}
+
+// Record the pre/rest graphs for caller arrays u (FP64) and b (FP64).
+static mg_status record(mg_ctx *c, void *u, const void *b)
+{
+    if (c->g.pre && c->cap_u == u && c->cap_b == b) return MG_OK;
+    free_graphs(c);
+    const int d = c->d, n0 = c->n[0];
+    const size_t np0 = npoints(d, n0);
+    mg_status st;
+    if (c->prec == MG_FP64) {
+        Recorder<double> R{c, (const double *)b, true, (double *)u};
+        const bool fused = c->nu1 >= 1 && c->lt > 0;
+        st = capture(c, &c->g.pre, &c->g.pre_nodes, [&]() -> cudaError_t {
+            cudaError_t e;
+            if (fused)
+                e = op_sweep<double>(d, (const double *)u, (const double *)b, true, (double *)c->B[0], n0, c->c,
+                                     c->partials, c->s);
+            else
+                e = op_residual<double, double>(d, (const double *)u, (const double *)b, true, (double *)nullptr,
+                                                n0, c->partials, c->s);
+            if (e) return e;
+            const int np = fused ? sweep_partials(d, n0) : residual_partials(d, n0);
+            if ((e = launch_sum_partials(c->partials, np, c->d_norm2, c->s))) return e;
+            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+        });
+        if (st != MG_OK) return st;
+        st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t { return R.visit(0, false, fused); });
+        if (st != MG_OK) return st;
+    } else {
+        // refinement: FP64 residual -> FP32 scaled rhs of level 0; FP32 cycle
+        // from zero; u += e in FP64
+        Recorder<float> R{c, (const float *)c->BH[0], false, (float *)c->A[0]};
+        st = capture(c, &c->g.pre, &c->g.pre_nodes, [&]() -> cudaError_t {
+            cudaError_t e = op_residual<double, float>(d, (const double *)u, (const double *)b, true,
+                                                       (float *)c->BH[0], n0, c->partials, c->s);
+            if (e) return e;
+            if ((e = launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s))) return e;
+            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+        });
+        if (st != MG_OK) return st;
+        st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
+            cudaError_t e = R.visit(0, true, false);
+            if (e) return e;
+            return launch_add_to_f64<float>((double *)u, (const float *)c->A[0], np0, c->s);
+        });
+        if (st != MG_OK) return st;
+    }
+    c->cap_u = u;
+    c->cap_b = b;
+    return MG_OK;
+}
+
+static mg_status enter(mg_ctx *c)
+{
+    MG_CUDA(cudaSetDevice(c->dev));
+    MG_CUDA(cudaEventRecord(c->ev_in, c->user));
+    MG_CUDA(cudaStreamWaitEvent(c->s, c->ev_in, 0));
+    return MG_OK;
+}
+
+static mg_status leave(mg_ctx *c)
+{
+    MG_CUDA(cudaEventRecord(c->ev_out, c->s));
+    MG_CUDA(cudaStreamWaitEvent(c->user, c->ev_out, 0));
+    return MG_OK;
+}
+
+static mg_status launch_graph(mg_ctx *c, cudaGraphExec_t g, unsigned long long nodes)
+{
+    MG_CUDA(cudaGraphLaunch(g, c->s));
+    g_launches += nodes;
+    return MG_OK;
+}
+
+// ||r||_2 from the last pre graph: sqrt(sum rh^2) / h^2
+static double norm_from_host(mg_ctx *c)
+{
+    return std::sqrt(*c->h_norm2) * (double)c->N * (double)c->N;
+}
+
+static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int nu1, int nu2, int gamma,
+                            mg_prec prec, void *stream, mg_ctx **out)
+{
+    if (!out) return MG_EINVAL;
+    *out = nullptr;
+    if ((d != 2 && d != 3) || !valid_N(N) || !coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 2) ||
+        nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || gamma < 1 || gamma > 2 || (prec != MG_FP64 && prec != MG_FP32_IR))
+        return MG_EINVAL;
+    for (int j = 0; j < ncoeffs; ++j)
+        if (!std::isfinite(coeffs[j])) return MG_EINVAL;
+    if (d == 3 && (size_t)(N - 1) * (N - 1) * (N - 1) > (size_t)1 << 34) return MG_EINVAL;
+    mg_ctx *c = new (std::nothrow) mg_ctx;
+    if (!c) return MG_ENOMEM;
+    c->d = d;
+    c->N = N;
+    c->nu1 = nu1;
+    c->nu2 = nu2;
+    c->gamma = gamma;
+    c->prec = prec;
+    c->ncoef = ncoeffs;
+    for (int j = 0; j < ncoeffs; ++j) c->c[j] = coeffs[j];
+    c->user = (cudaStream_t)stream;
+    c->esize = prec == MG_FP64 ? sizeof(double) : sizeof(float);
+    mg_status st = MG_OK;
+#define MG_TRY(x)                      \
+    do {                               \
+        st = (x);                      \
+        if (st != MG_OK) goto fail;    \
+    } while (0)
+#define MG_TRYC(x)                              \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            st = cuda_fail(e_);                 \
+            goto fail;                          \
+        }                                       \
+    } while (0)
+    {
+        MG_TRYC(cudaGetDevice(&c->dev));
+        MG_TRYC(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+        MG_TRYC(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+        MG_TRYC(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+        for (int m = N; m >= 4; m /= 2) c->n.push_back(m - 1);
+        c->L = (int)c->n.size();
+        // levels with n <= 15 (2D) / 7 (3D) run inside the one-block tail
+        const int tail_n = d == 2 ? 15 : 7;
+        c->lt = c->L;
+        for (int l = 0; l < c->L; ++l)
+            if (c->n[l] <= tail_n) {
+                c->lt = l;
+                break;
+            }
+        if (c->L - c->lt > kMaxTailLevels) c->lt = c->L - kMaxTailLevels;
+        c->A.assign(c->L, nullptr);
+        c->B.assign(c->L, nullptr);
+        c->BH.assign(c->L, nullptr);
+        c->RH.assign(c->L, nullptr);
+        for (int l = 0; l < c->L; ++l) {
+            const size_t bytes = npoints(d, c->n[l]) * c->esize;
+            const bool caller_level = l == 0 && prec == MG_FP64;
+            if (!caller_level) MG_TRY(dalloc(c, &c->A[l], bytes));
+            MG_TRY(dalloc(c, &c->B[l], bytes));
+            if (!caller_level || c->lt == 0) MG_TRY(dalloc(c, &c->BH[l], bytes));
+            if (l >= c->lt) MG_TRY(dalloc(c, &c->RH[l], bytes));
+        }
+        int np = std::max(sweep_partials(d, c->n[0]), residual_partials(d, c->n[0]));
+        c->npartials = np;
+        MG_TRY(dalloc(c, (void **)&c->partials, (size_t)np * sizeof(double)));
+        MG_TRY(dalloc(c, (void **)&c->d_norm2, sizeof(double)));
+        MG_TRY(dalloc(c, (void **)&c->lu, 27 * 27 * sizeof(double)));
+        {
+            double lu[27 * 27];
+            coarse_lu(d, lu);
+            const int m = d == 2 ? 9 : 27;
+            MG_TRYC(cudaMemcpy(c->lu, lu, (size_t)m * m * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        MG_TRYC(cudaMallocHost((void **)&c->h_norm2, sizeof(double)));
+    }
+    *out = c;
+    return MG_OK;
+fail:
+    destroy_ctx(c);
+    return st;
+#undef MG_TRY
+#undef MG_TRYC
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// single operators
+// ---------------------------------------------------------------------------
+static bool valid_level(int d, int n)
+{
+    return (d == 2 || d == 3) && n >= 3 && (n & 1) && valid_N(n + 1);
+}
+
+template <typename T>
+static mg_status op_sweep_t(int d, int n, const double *c, const void *u, const void *bh, int unscaled, void *out,
+                            double *rnorm2, cudaStream_t s)
+{
+    double *partials = nullptr, *sum = nullptr;
+    cudaError_t e;
+    if (rnorm2) {
+        const int np = sweep_partials(d, n);
+        if ((e = cudaMalloc(&partials, (size_t)np * sizeof(double) + sizeof(double)))) return cuda_fail(e);
+        sum = partials + np;
+    }
+    e = op_sweep<T>(d, (const T *)u, (const T *)bh, unscaled != 0, (T *)out, n, c, partials, s);
+    if (!e && rnorm2) {
+        e = launch_sum_partials(partials, sweep_partials(d, n), sum, s);
+        if (!e) e = cudaMemcpyAsync(rnorm2, sum, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+    }
+    if (partials) cudaFree(partials);
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+mg_status mg_setup_ex(int d, int N, const double *spai_coeffs, int ncoeffs, int nu1, int nu2, int gamma,
+                      mg_prec prec, void *cuda_stream, mg_ctx **out)
+{
+    return setup_impl(d, N, spai_coeffs, ncoeffs, nu1, nu2, gamma, prec, cuda_stream, out);
+}
+
+mg_status mg_setup(int d, int N, const double *spai_coeffs, int ncoeffs, int nu1, int nu2, mg_prec prec,
+                   void *cuda_stream, mg_ctx **out)
+{
+    return setup_impl(d, N, spai_coeffs, ncoeffs, nu1, nu2, 1, prec, cuda_stream, out);
+}
+
+void mg_destroy(mg_ctx *ctx)
+{
+    if (ctx) {
+        cudaSetDevice(ctx->dev);
+        if (ctx->s) cudaStreamSynchronize(ctx->s);
+        destroy_ctx(ctx);
+    }
+}
+
+mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b)
+{
+    if (!ctx || !u || !b || !ctx->members.empty()) return MG_EINVAL;
+    mg_status st = enter(ctx);
+    if (st != MG_OK) return st;
+    if ((st = record(ctx, u, b)) != MG_OK) return st;
+    if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
+    if ((st = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return st;
+    return leave(ctx);
+}
+
+mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
+                   double *relres_out, double *hist_out)
+{
+    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || !ctx->members.empty()) return MG_EINVAL;
+    mg_status st = enter(ctx);
+    if (st != MG_OK) return st;
+    if ((st = record(ctx, u, b)) != MG_OK) return st;
+    if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
+    if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    const double r0 = norm_from_host(ctx);
+    double rk = r0;
+    int k = 0;
+    if (hist_out) hist_out[0] = r0;
+    st = std::isfinite(r0) ? MG_OK : MG_ENAN;
+    while (st == MG_OK && !(rk <= tol * r0)) {
+        if (k == max_cycles) {
+            st = MG_ENOCONV;
+            break;
+        }
+        if ((st = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return st;
+        if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
+        if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+        ++k;
+        rk = norm_from_host(ctx);
+        if (hist_out) hist_out[k] = rk;
+        if (!std::isfinite(rk)) st = MG_ENAN;
+    }
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = r0 > 0.0 ? rk / r0 : 0.0;
+    mg_status st2 = leave(ctx);
+    return st != MG_OK ? st : st2;
+}
+
+mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out)
+{
+    if (!ctx || !u || !b || !norm_out || !ctx->members.empty()) return MG_EINVAL;
+    mg_status st = enter(ctx);
+    if (st != MG_OK) return st;
+    const int n0 = ctx->n[0];
+    cudaError_t e = op_residual<double, double>(ctx->d, (const double *)u, (const double *)b, true,
+                                                (double *)nullptr, n0, ctx->partials, ctx->s);
+    if (!e) e = launch_sum_partials(ctx->partials, residual_partials(ctx->d, n0), ctx->d_norm2, ctx->s);
+    if (!e) e = cudaMemcpyAsync(ctx->h_norm2, ctx->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+    if (!e) e = cudaStreamSynchronize(ctx->s);
+    if (e) return cuda_fail(e);
+    *norm_out = norm_from_host(ctx);
+    return leave(ctx);
+}
+
+mg_status mg_op_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs, const void *u,
+                      const void *bh, int b_unscaled, void *u_out, double *rnorm2_out, void *stream)
+{
+    if (!valid_level(d, n) || !spai_coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 2) || !bh || !u_out)
+        return MG_EINVAL;
+    double c[3] = {0, 0, 0};
+    for (int j = 0; j < ncoeffs; ++j) c[j] = spai_coeffs[j];
+    if (prec == MG_FP64)
+        return op_sweep_t<double>(d, n, c, u, bh, b_unscaled, u_out, rnorm2_out, (cudaStream_t)stream);
+    if (prec == MG_FP32_IR)
+        return op_sweep_t<float>(d, n, c, u, bh, b_unscaled, u_out, rnorm2_out, (cudaStream_t)stream);
+    return MG_EINVAL;
+}
+
+mg_status mg_op_residual(int d, int n, mg_prec prec, const void *u, const void *bh, int b_unscaled, void *rh_out,
+                         void *stream)
+{
+    if (!valid_level(d, n) || !u || !bh || !rh_out) return MG_EINVAL;
+    cudaError_t e;
+    if (prec == MG_FP64)
+        e = op_residual<double, double>(d, (const double *)u, (const double *)bh, b_unscaled != 0, (double *)rh_out,
+                                        n, nullptr, (cudaStream_t)stream);
+    else if (prec == MG_FP32_IR)
+        e = op_residual<float, float>(d, (const float *)u, (const float *)bh, b_unscaled != 0, (float *)rh_out, n,
+                                      nullptr, (cudaStream_t)stream);
+    else
+        return MG_EINVAL;
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+mg_status mg_op_residual_restrict(int d, int n, mg_prec prec, const void *u, const void *bh, int b_unscaled,
+                                  void *bh_coarse_out, void *stream)
+{
+    if (!valid_level(d, n) || n < 7 || !u || !bh || !bh_coarse_out) return MG_EINVAL;
+    cudaError_t e;
+    if (prec == MG_FP64)
+        e = op_resrestrict<double>(d, (const double *)u, (const double *)bh, b_unscaled != 0,
+                                   (double *)bh_coarse_out, n, (cudaStream_t)stream);
+    else if (prec == MG_FP32_IR)
+        e = op_resrestrict<float>(d, (const float *)u, (const float *)bh, b_unscaled != 0, (float *)bh_coarse_out,
+                                  n, (cudaStream_t)stream);
+    else
+        return MG_EINVAL;
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+mg_status mg_op_prolong_correct(int d, int n, mg_prec prec, const void *e_coarse, void *u, void *stream)
+{
+    if (!valid_level(d, n) || n < 7 || !e_coarse || !u) return MG_EINVAL;
+    cudaError_t e;
+    if (prec == MG_FP64)
+        e = op_prolong<double>(d, (const double *)e_coarse, (double *)u, n, (cudaStream_t)stream);
+    else if (prec == MG_FP32_IR)
+        e = op_prolong<float>(d, (const float *)e_coarse, (float *)u, n, (cudaStream_t)stream);
+    else
+        return MG_EINVAL;
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, void *stream)
+{
+    if ((d != 2 && d != 3) || !bh || !x_out || (prec != MG_FP64 && prec != MG_FP32_IR)) return MG_EINVAL;
+    double lu[27 * 27];
+    coarse_lu(d, lu);
+    double *dlu = nullptr;
+    cudaError_t e = cudaMalloc(&dlu, sizeof lu);
+    if (e) return cuda_fail(e);
+    e = cudaMemcpy(dlu, lu, sizeof lu, cudaMemcpyHostToDevice);
+    TailArgs a;
+    memset(&a, 0, sizeof a);
+    a.d = d;
+    a.lu = dlu;
+    a.lv[0].u = x_out;
+    a.lv[0].bh = (void *)bh;
+    a.lv[0].n = 3;
+    a.ops[0].kind = TAIL_SOLVE;
+    a.ops[0].level = 0;
+    a.nops = 1;
+    if (!e) e = prec == MG_FP64 ? launch_tail<double>(a, (cudaStream_t)stream) : launch_tail<float>(a, (cudaStream_t)stream);
+    if (!e) e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(dlu);
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+const char *mg_strerror(mg_status s)
+{
+    switch (s) {
+    case MG_OK: return "success";
+    case MG_EINVAL: return "invalid argument";
+    case MG_ENOMEM: return "out of memory";
+    case MG_ECUDA: return "CUDA error";
+    case MG_ENOCONV: return "not converged within max_cycles";
+    case MG_ENAN: return "residual norm is NaN or Inf";
+    case MG_ETIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *mg_last_cuda_error(void) { return g_last_error; }
+
+unsigned long long mg_kernel_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// mg_internal.h -- declarations shared by the library's translation units
+// (launchers of the kernels, launch accounting, device properties).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+
+namespace mg {
+
+// Streaming multiprocessors of the current device (grid sizing only).
+int num_sms();
+// Launch accounting behind mg_kernel_launch_count().
+void count_launch(unsigned long long k);
+
+// Rows per block for the marching kernels: enough blocks to fill the GPU
+// (target_blocks), clamped to [lo, hi].
+inline int chunk_rows(int nblk_x, int nrows, int target_blocks, int lo, int hi)
+{
+    long want = ((long)nblk_x * nrows + target_blocks - 1) / target_blocks;
+    return (int)std::min<long>(std::max<long>(want, lo), hi);
+}
+
+struct Grid2 {
+    int bx, by, H;
+};
+Grid2 sweep2d_grid(int n);
+
+// 2D level operators; arrays in the interior layout of a level with n points
+// per axis. c = omega-folded weights (c0, c1, c2). u == nullptr: u = 0.
+// partials != nullptr: one squared-residual partial sum per block
+// (sweep2d_grid(n).bx * .by doubles).
+template <typename T>
+cudaError_t launch_sweep2d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
+                           double *partials, cudaStream_t s);
+template <typename T>
+cudaError_t launch_resrestrict2d(const T *u, const T *b, bool unscaled, T *bc, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong2d(const T *e, T *u, int n, cudaStream_t s);
+
+// Scaled residual rh = bh - h^2 A u in InT (bh = h^2 b formed in the kernel
+// when `unscaled`), written as OutT when rh != nullptr, plus squared partial
+// sums (one per block of sweep2d_grid(n)) when partials != nullptr.
+template <typename InT, typename OutT>
+cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
+                              cudaStream_t s);
+
+struct Grid3 {
+    int bx, by, bz, Z;
+};
+Grid3 sweep3d_grid(int n);
+Grid3 residual3d_grid(int n);
+
+// 3D level operators (same conventions as the 2D ones; c = (c0, c1)).
+template <typename T>
+cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
+                           double *partials, cudaStream_t s);
+template <typename T>
+cudaError_t launch_resrestrict3d(const T *u, const T *b, bool unscaled, T *bc, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong3d(const T *e, T *u, int n, cudaStream_t s);
+template <typename InT, typename OutT>
+cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
+                              cudaStream_t s);
+
+// ---- coarse tail (one block runs the last levels of a cycle) --------------
+constexpr int kTailThreads = 256;
+constexpr int kMaxTailLevels = 8;
+constexpr int kMaxTailOps = 480;
+enum TailOpKind : int { TAIL_ZERO = 0, TAIL_SWEEP = 1, TAIL_RESTRICT = 2, TAIL_SOLVE = 3, TAIL_PROLONG = 4 };
+struct TailLevel {
+    void *u, *tmp, *bh, *rh;  // element type = the kernel's T
+    int n;
+};
+struct TailOp {
+    short kind, level;  // level indexes TailArgs::lv
+};
+struct TailArgs {
+    TailLevel lv[kMaxTailLevels];
+    TailOp ops[kMaxTailOps];
+    double c[3];
+    const double *lu;  // coarsest LU factors (device)
+    int d, nops;
+};
+template <typename T>
+cudaError_t launch_tail(const TailArgs &a, cudaStream_t s);
+void coarse_lu(int d, double *lu);
+
+// ---- small helpers (mg_host.cu) -------------------------------------------
+cudaError_t launch_sum_partials(const double *partials, int np, double *out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_add_to_f64(double *u, const T *e, size_t np, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_copy(const double *b, T *bh, size_t np, double h2, cudaStream_t s);
+
+}  // namespace mg

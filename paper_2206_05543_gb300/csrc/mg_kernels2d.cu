@@ -1,0 +1,358 @@
+// mg_kernels2d.cu -- 2D kernels: SPAI sweep, residual + full weighting,
+// bilinear interpolation + correction (He, Liu, Wang, arXiv:2206.05543,
+// Sec. 2 Eq. (2.1), Sec. 3.1, Sec. 4).
+//
+// Design. All three kernels march along y: a block owns a strip of columns
+// (one column per thread) and a chunk of rows, and keeps a rolling window of
+// rows in registers; the horizontal neighbours come through a double-buffered
+// shared-memory row. Every residual and every interpolated value is computed
+// once per point (plus a two-row halo per chunk and a one-column halo per
+// strip), which matters because FP64 on this part is ALU-bound: the stencil
+// work, not the bytes, sets the time.
+//
+// Scaled form (per level, spacing h): bh = h^2 b, rh = h^2 (b - A u) and the
+// sweep weights c_j = omega m_j / h^2 are h-free. On the finest level b is
+// the caller's unscaled array and bh = h^2 b is formed in the kernel (exact:
+// h is a power of two).
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// SPAI sweep.  Canonical evaluation at each interior point p:
+//   s  = (u_W + u_E) + (u_S + u_N)
+//   rh = fma(-4, u_p, bh_p) + s             (rh := 0 outside the interior)
+//   E  = (rh_W + rh_E) + (rh_S + rh_N)
+//   C  = (rh_SW + rh_SE) + (rh_NW + rh_NE)
+//   u' = fma(c2, C, fma(c1, E, fma(c0, rh_p, u_p)))
+// The pairs are shared between points: hp(q) = rh(q - x) + rh(q + x) gives
+// E = hp(p) + (rh_S + rh_N) and C = hp(p - y) + hp(p + y).
+// Block: 256 threads, thread t owns column x = 254*bx - 1 + t; threads 1..254
+// write, threads 0 and 255 supply the halo residuals. Rows [y0, y0 + H).
+// ZERO_U: the input is u = 0 (first sweep on a coarse level): rh = bh.
+// NORM: accumulate the squared residual of the input over owned points.
+// ---------------------------------------------------------------------------
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+__global__ void __launch_bounds__(kSweepThreads)
+sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int H,
+               T c0, T c1, T c2, T h2, double *__restrict__ partials)
+{
+    __shared__ T su[2][kSweepThreads + 2];
+    __shared__ T sr[2][kSweepThreads];
+    const int t = threadIdx.x;
+    const int x = blockIdx.x * kSweepCols - 1 + t;
+    const int y0 = blockIdx.y * H;
+    const int y1 = min(y0 + H, n);
+    const bool xin = x >= 0 && x < n;
+    const bool owner = t >= 1 && t <= kSweepCols && xin;
+    const size_t ld = (size_t)n;
+
+    auto get = [&](const T *a, int yy, int xx) -> T {
+        return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : T(0);
+    };
+
+    T u_prev = T(0), u_cur = T(0), u_next = T(0);
+    if (!ZERO_U) {
+        u_prev = get(u, y0 - 2, x);
+        u_cur = get(u, y0 - 1, x);
+    }
+    T r1 = T(0), r2 = T(0), hp1 = T(0), hp2 = T(0);
+    double acc = 0.0;
+
+    for (int j = y0 - 1; j <= y1; ++j) {
+        const int buf = j & 1;
+        T bb = get(b, j, x);
+        if (UNSCALED_B) bb = rmul(h2, bb);
+        T r;
+        if (!ZERO_U) {
+            u_next = get(u, j + 1, x);
+            su[buf][t + 1] = u_cur;
+            if (t == 0) su[buf][0] = get(u, j, x - 1);
+            if (t == kSweepThreads - 1) su[buf][kSweepThreads + 1] = get(u, j, x + 1);
+            __syncthreads();
+            const T s = radd(radd(su[buf][t], su[buf][t + 2]), radd(u_prev, u_next));
+            r = radd(rfma(T(-4), u_cur, bb), s);
+        } else {
+            r = bb;
+        }
+        if (!(xin && j >= 0 && j < n)) r = T(0);
+        if (NORM && owner && j >= y0 && j < y1) acc = fma((double)r, (double)r, acc);
+        sr[buf][t] = r;
+        __syncthreads();
+        const T hp = (t >= 1 && t <= kSweepCols) ? radd(sr[buf][t - 1], sr[buf][t + 1]) : T(0);
+        if (owner && j - 1 >= y0) {  // output row j - 1
+            const T E = radd(hp1, radd(r2, r));
+            const T C = radd(hp2, hp);
+            const T base = ZERO_U ? rmul(c0, r1) : rfma(c0, r1, u_prev);
+            out[(size_t)(j - 1) * ld + x] = rfma(c2, C, rfma(c1, E, base));
+        }
+        r2 = r1;
+        r1 = r;
+        hp2 = hp1;
+        hp1 = hp;
+        if (!ZERO_U) {
+            u_prev = u_cur;
+            u_cur = u_next;
+        }
+    }
+    if (NORM) block_sum_store<kSweepThreads>(acc, &partials[blockIdx.y * gridDim.x + blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// Residual + full-weighting restriction. For coarse point (ic, jc) (0-based)
+// with fine centre (2ic+1, 2jc+1):
+//   along x, per fine row f:  t_f = (rh(2ic) + rh(2ic+2)) + 2 rh(2ic+1)
+//   along y:                  v   = (t_{2jc} + t_{2jc+2}) + 2 t_{2jc+1}
+//   bh_c = 0.25 v   (= 4 R rh with R = (1,2,1)/4 per axis, H^2/h^2 = 4)
+// with rh evaluated as in the sweep. Block: 256 threads, thread t owns fine
+// columns 2ic, 2ic+1 with ic = 255*bx + t; threads 0..254 write.
+// ---------------------------------------------------------------------------
+template <typename T, bool UNSCALED_B>
+__global__ void __launch_bounds__(kRestrictThreads)
+resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
+                     int Hc, T h2)
+{
+    __shared__ T su[2][2 * kRestrictThreads + 2];
+    __shared__ T sr[2][kRestrictThreads + 1];
+    const int nc = (n - 1) / 2;
+    const int t = threadIdx.x;
+    const int ic = blockIdx.x * kRestrictCols + t;
+    const int fx = 2 * ic;  // this thread's fine columns: fx, fx + 1
+    const int jc0 = blockIdx.y * Hc;
+    const int jc1 = min(jc0 + Hc, nc);
+    const size_t ld = (size_t)n;
+    auto get = [&](const T *a, int yy, int xx) -> T {
+        return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : T(0);
+    };
+    const bool in0 = fx < n, in1 = fx + 1 < n;
+
+    const int f0 = 2 * jc0, f1 = 2 * jc1;  // fine rows f0 .. f1 feed coarse rows jc0 .. jc1-1
+    T ua_prev = get(u, f0 - 1, fx), ub_prev = get(u, f0 - 1, fx + 1);
+    T ua = get(u, f0, fx), ub = get(u, f0, fx + 1);
+    T t1 = T(0), t2 = T(0);  // x-pass of fine rows f-1, f-2
+    for (int f = f0; f <= f1; ++f) {
+        const int buf = f & 1;
+        const T ua_next = get(u, f + 1, fx), ub_next = get(u, f + 1, fx + 1);
+        su[buf][2 * t + 1] = ua;
+        su[buf][2 * t + 2] = ub;
+        if (t == 0) su[buf][0] = get(u, f, fx - 1);
+        if (t == kRestrictThreads - 1) su[buf][2 * kRestrictThreads + 1] = get(u, f, fx + 2);
+        __syncthreads();
+        T ba = get(b, f, fx), bb = get(b, f, fx + 1);
+        if (UNSCALED_B) {
+            ba = rmul(h2, ba);
+            bb = rmul(h2, bb);
+        }
+        const T sa = radd(radd(su[buf][2 * t], su[buf][2 * t + 2]), radd(ua_prev, ua_next));
+        const T sb = radd(radd(su[buf][2 * t + 1], su[buf][2 * t + 3]), radd(ub_prev, ub_next));
+        T ra = radd(rfma(T(-4), ua, ba), sa);
+        T rb = radd(rfma(T(-4), ub, bb), sb);
+        if (!in0 || f >= n) ra = T(0);
+        if (!in1 || f >= n) rb = T(0);
+        sr[buf][t] = ra;
+        if (t == kRestrictThreads - 1) sr[buf][kRestrictThreads] = T(0);  // never read by a writer
+        __syncthreads();
+        const T tx = rfma(T(2), rb, radd(ra, sr[buf][t + 1]));
+        if (f >= f0 + 2 && (f & 1) == 0 && t < kRestrictCols && ic < nc) {
+            const int jc = f / 2 - 1;
+            const T v = rfma(T(2), t1, radd(t2, tx));
+            bc[(size_t)jc * nc + ic] = rmul(T(0.25), v);
+        }
+        t2 = t1;
+        t1 = tx;
+        ua_prev = ua;
+        ub_prev = ub;
+        ua = ua_next;
+        ub = ub_next;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bilinear interpolation + correction u += P e. Thread k owns fine columns
+// 2k (between coarse k-1 and k) and 2k+1 (on coarse k); per coarse row m:
+//   along x: ex(2k) = 0.5 (e[m][k-1] + e[m][k]),  ex(2k+1) = e[m][k]
+//   along y: fine row 2m+1 gets ex_m, fine row 2m gets 0.5 (ex_{m-1} + ex_m)
+//   u = u + value            (e is zero outside the coarse interior)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kProlongThreads)
+prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
+{
+    const int nc = (n - 1) / 2;
+    const int k = blockIdx.x * kProlongThreads + threadIdx.x;
+    if (k > nc) return;
+    const int m0 = blockIdx.y * Hc;
+    const int m1 = min(m0 + Hc, nc + 1);
+    const size_t ldc = (size_t)nc, ld = (size_t)n;
+    auto ge = [&](int mm, int kk) -> T {
+        return (mm >= 0 && mm < nc && kk >= 0 && kk < nc) ? e[(size_t)mm * ldc + kk] : T(0);
+    };
+    auto xpass = [&](int mm, T &odd, T &on) {
+        on = ge(mm, k);
+        odd = rmul(T(0.5), radd(ge(mm, k - 1), on));
+    };
+    T pa, pb;  // x-pass of coarse row m-1: columns 2k, 2k+1
+    xpass(m0 - 1, pa, pb);
+    const int fa = 2 * k, fb = 2 * k + 1;
+    const bool inb = fb < n;
+    for (int m = m0; m < m1; ++m) {
+        T ca, cb;
+        xpass(m, ca, cb);
+        {   // fine row 2m
+            T *row = u + (size_t)(2 * m) * ld;
+            row[fa] = radd(row[fa], rmul(T(0.5), radd(pa, ca)));
+            if (inb) row[fb] = radd(row[fb], rmul(T(0.5), radd(pb, cb)));
+        }
+        if (m < nc) {  // fine row 2m+1
+            T *row = u + (size_t)(2 * m + 1) * ld;
+            row[fa] = radd(row[fa], ca);
+            if (inb) row[fb] = radd(row[fb], cb);
+        }
+        pa = ca;
+        pb = cb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual for iterative refinement: rh = fma(-4, u, h^2 b) + s exactly
+// as in the sweep, written as OutT (the cycle's precision) together with one
+// partial sum of rh^2 per block. Same marching layout as the sweep (threads
+// 0 and 255 only supply the u halo).
+// ---------------------------------------------------------------------------
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(kSweepThreads)
+residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
+                  int n, int H, InT h2, bool unscaled, double *__restrict__ partials)
+{
+    __shared__ InT su[2][kSweepThreads + 2];
+    const int t = threadIdx.x;
+    const int x = blockIdx.x * kSweepCols - 1 + t;
+    const int y0 = blockIdx.y * H;
+    const int y1 = min(y0 + H, n);
+    const bool owner = t >= 1 && t <= kSweepCols && x < n;
+    const size_t ld = (size_t)n;
+    auto get = [&](const InT *a, int yy, int xx) -> InT {
+        return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : InT(0);
+    };
+    InT u_prev = get(u, y0 - 1, x), u_cur = get(u, y0, x);
+    double acc = 0.0;
+    for (int j = y0; j < y1; ++j) {
+        const int buf = j & 1;
+        const InT u_next = get(u, j + 1, x);
+        su[buf][t + 1] = u_cur;
+        if (t == 0) su[buf][0] = get(u, j, x - 1);
+        if (t == kSweepThreads - 1) su[buf][kSweepThreads + 1] = get(u, j, x + 1);
+        __syncthreads();
+        if (owner) {
+            const InT s = radd(radd(su[buf][t], su[buf][t + 2]), radd(u_prev, u_next));
+            InT bb = b[(size_t)j * ld + x];
+            if (unscaled) bb = rmul(h2, bb);
+            const InT r = radd(rfma(InT(-4), u_cur, bb), s);
+            acc = fma((double)r, (double)r, acc);
+            if (rh_out) rh_out[(size_t)j * ld + x] = (OutT)r;
+        }
+        u_prev = u_cur;
+        u_cur = u_next;
+    }
+    if (partials) block_sum_store<kSweepThreads>(acc, &partials[blockIdx.y * gridDim.x + blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+Grid2 sweep2d_grid(int n)
+{
+    Grid2 g;
+    g.bx = (n + kSweepCols - 1) / kSweepCols;
+    g.H = chunk_rows(g.bx, n, 8 * num_sms(), 8, 64);
+    g.by = (n + g.H - 1) / g.H;
+    return g;
+}
+
+template <typename T>
+cudaError_t launch_sweep2d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
+                           double *partials, cudaStream_t s)
+{
+    const Grid2 g = sweep2d_grid(n);
+    const dim3 grid(g.bx, g.by);
+    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]);
+#define MG_SWEEP(ZU, UB, NRM) \
+    sweep2d_kernel<T, ZU, UB, NRM><<<grid, kSweepThreads, 0, s>>>(u, b, out, n, g.H, c0, c1, c2, h2, partials)
+    const bool z = u == nullptr, nrm = partials != nullptr;
+    if (z) {
+        if (unscaled) {
+            if (nrm) MG_SWEEP(true, true, true); else MG_SWEEP(true, true, false);
+        } else {
+            if (nrm) MG_SWEEP(true, false, true); else MG_SWEEP(true, false, false);
+        }
+    } else {
+        if (unscaled) {
+            if (nrm) MG_SWEEP(false, true, true); else MG_SWEEP(false, true, false);
+        } else {
+            if (nrm) MG_SWEEP(false, false, true); else MG_SWEEP(false, false, false);
+        }
+    }
+#undef MG_SWEEP
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_resrestrict2d(const T *u, const T *b, bool unscaled, T *bc, int n, cudaStream_t s)
+{
+    const int nc = (n - 1) / 2;
+    const int bx = (nc + kRestrictCols - 1) / kRestrictCols;
+    const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 4, 32);
+    const dim3 grid(bx, (nc + Hc - 1) / Hc);
+    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    if (unscaled)
+        resrestrict2d_kernel<T, true><<<grid, kRestrictThreads, 0, s>>>(u, b, bc, n, Hc, h2);
+    else
+        resrestrict2d_kernel<T, false><<<grid, kRestrictThreads, 0, s>>>(u, b, bc, n, Hc, h2);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong2d(const T *e, T *u, int n, cudaStream_t s)
+{
+    const int nc = (n - 1) / 2;
+    const int bx = (nc + 1 + kProlongThreads - 1) / kProlongThreads;
+    const int Hc = chunk_rows(bx, nc + 1, 8 * num_sms(), 4, 32);
+    const dim3 grid(bx, (nc + 1 + Hc - 1) / Hc);
+    prolong2d_kernel<T><<<grid, kProlongThreads, 0, s>>>(e, u, n, Hc);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename InT, typename OutT>
+cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
+                              cudaStream_t s)
+{
+    const Grid2 g = sweep2d_grid(n);
+    const InT h2 = InT(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads, 0, s>>>(u, b, rh, n, g.H, h2, unscaled,
+                                                                           partials);
+    count_launch(1);
+    return cudaGetLastError();
+}
+template cudaError_t launch_residual2d<double, double>(const double *, const double *, bool, double *, int,
+                                                       double *, cudaStream_t);
+template cudaError_t launch_residual2d<double, float>(const double *, const double *, bool, float *, int,
+                                                      double *, cudaStream_t);
+template cudaError_t launch_residual2d<float, float>(const float *, const float *, bool, float *, int,
+                                                     double *, cudaStream_t);
+
+#define MG_INST(T)                                                                                   \
+    template cudaError_t launch_sweep2d<T>(const T *, const T *, bool, T *, int, const double *,     \
+                                           double *, cudaStream_t);                                  \
+    template cudaError_t launch_resrestrict2d<T>(const T *, const T *, bool, T *, int, cudaStream_t); \
+    template cudaError_t launch_prolong2d<T>(const T *, T *, int, cudaStream_t);
+MG_INST(double)
+MG_INST(float)
+#undef MG_INST
+
+}  // namespace mg

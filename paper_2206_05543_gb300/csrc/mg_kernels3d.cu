@@ -1,0 +1,407 @@
+// mg_kernels3d.cu -- 3D kernels: SPAI sweep (7-point A, 7-point M), residual
+// + full weighting, trilinear interpolation + correction, FP64 residual
+// (He, Liu, Wang, arXiv:2206.05543, Sec. 2 Eq. (2.1), Sec. 3.2, Sec. 4).
+//
+// Design. Every kernel marches along z over a chunk of planes while a block
+// owns a tile in (x, y); values along z live in registers, in-plane
+// neighbours come through double-buffered shared-memory planes. Formulas and
+// their rounding order are written next to each kernel and match the 2D
+// kernels' conventions (scaled right-hand sides, h-free weights).
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+constexpr int kS3 = 32;            // extended residual tile edge (sweep)
+constexpr int kS3Out = kS3 - 2;    // output tile edge (sweep)
+constexpr int kS3U = kS3 + 2;      // u plane edge incl. halo (sweep)
+constexpr int kS3Threads = 256;
+constexpr int kS3Pts = kS3 * kS3 / kS3Threads;  // extended points per thread (4)
+
+template <typename T>
+__device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
+{
+    return (x >= 0 && x < n && y >= 0 && y < n && z >= 0 && z < n) ? a[((size_t)z * n + y) * n + x] : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// SPAI sweep, canonical evaluation at interior point p:
+//   s  = ((u_W + u_E) + (u_S + u_N)) + (u_D + u_U)
+//   rh = fma(-6, u_p, bh_p) + s          (rh := 0 outside the interior)
+//   E  = ((rh_W + rh_E) + (rh_S + rh_N)) + (rh_D + rh_U)
+//   u' = fma(c1, E, fma(c0, rh_p, u_p))
+// (W/E = x-1/x+1, S/N = y-1/y+1, D/U = z-1/z+1). A block computes rh on a
+// 32x32 tile (output tile 30x30 plus its halo), thread t holding the tile
+// points t, t+256, t+512, t+768 with their z-windows in registers.
+// ---------------------------------------------------------------------------
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+__global__ void __launch_bounds__(kS3Threads)
+sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int Z,
+               T c0, T c1, T h2, double *__restrict__ partials)
+{
+    __shared__ T su[2][kS3U * kS3U];
+    __shared__ T sr[3][kS3 * kS3];  // three planes: the output reads the previous one
+    const int t = threadIdx.x;
+    const int ex0 = blockIdx.x * kS3Out - 1, ey0 = blockIdx.y * kS3Out - 1;
+    const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
+    const size_t plane = (size_t)n * n;
+
+    int px[kS3Pts], py[kS3Pts];
+    bool inside[kS3Pts], own[kS3Pts];
+    T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], r_m1[kS3Pts], r_0[kS3Pts];
+#pragma unroll
+    for (int k = 0; k < kS3Pts; ++k) {
+        const int i = (t + k * kS3Threads) % kS3, j = (t + k * kS3Threads) / kS3;
+        px[k] = ex0 + i;
+        py[k] = ey0 + j;
+        inside[k] = px[k] >= 0 && px[k] < n && py[k] >= 0 && py[k] < n;
+        own[k] = inside[k] && i >= 1 && i <= kS3Out && j >= 1 && j <= kS3Out;
+        u_prev[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0 - 2);
+        u_cur[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0 - 1);
+        u_next[k] = T(0);
+        r_m1[k] = T(0);
+        r_0[k] = T(0);
+    }
+    double acc = 0.0;
+
+    for (int zz = z0 - 1; zz <= z1; ++zz) {  // residual plane zz, output plane zz - 1
+        const int buf = zz & 1;
+        if (!ZERO_U) {
+#pragma unroll
+            for (int k = 0; k < kS3Pts; ++k) {
+                u_next[k] = get3(u, n, px[k], py[k], zz + 1);
+                const int i = px[k] - ex0, j = py[k] - ey0;
+                su[buf][(j + 1) * kS3U + (i + 1)] = u_cur[k];
+            }
+            // the one-point ring around the 32x32 tile: 4 * 33 = 132 points
+            if (t < 4 * (kS3 + 1)) {
+                const int side = t / (kS3 + 1), q = t % (kS3 + 1);
+                int i, j;  // tile-relative, in [-1, 32]
+                if (side == 0) { i = q - 1; j = -1; }
+                else if (side == 1) { i = kS3; j = q - 1; }
+                else if (side == 2) { i = q; j = kS3; }
+                else { i = -1; j = q; }
+                su[buf][(j + 1) * kS3U + (i + 1)] = get3(u, n, ex0 + i, ey0 + j, zz);
+            }
+            __syncthreads();
+        }
+        T r_new[kS3Pts];
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) {
+            const int i = px[k] - ex0, j = py[k] - ey0;
+            T bb = get3(b, n, px[k], py[k], zz);
+            if (UNSCALED_B) bb = rmul(h2, bb);
+            T r;
+            if (!ZERO_U) {
+                const T *row = &su[buf][(j + 1) * kS3U + (i + 1)];
+                const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kS3U], row[kS3U])),
+                                 radd(u_prev[k], u_next[k]));
+                r = radd(rfma(T(-6), u_cur[k], bb), s);
+            } else {
+                r = bb;
+            }
+            if (!(inside[k] && zz >= 0 && zz < n)) r = T(0);
+            if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma((double)r, (double)r, acc);
+            r_new[k] = r;
+            sr[(zz + 3) % 3][j * kS3 + i] = r;
+        }
+        __syncthreads();
+        if (zz - 1 >= z0) {
+            const T *rp = sr[(zz + 2) % 3];  // plane zz - 1
+#pragma unroll
+            for (int k = 0; k < kS3Pts; ++k) {
+                if (!own[k]) continue;
+                const int i = px[k] - ex0, j = py[k] - ey0;
+                const T *row = &rp[j * kS3 + i];
+                const T E = radd(radd(radd(row[-1], row[1]), radd(row[-kS3], row[kS3])),
+                                 radd(r_m1[k], r_new[k]));
+                const T base = ZERO_U ? rmul(c0, r_0[k]) : rfma(c0, r_0[k], u_prev[k]);
+                out[(size_t)(zz - 1) * plane + (size_t)py[k] * n + px[k]] = rfma(c1, E, base);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) {
+            r_m1[k] = r_0[k];
+            r_0[k] = r_new[k];
+            if (!ZERO_U) {
+                u_prev[k] = u_cur[k];
+                u_cur[k] = u_next[k];
+            }
+        }
+    }
+    if (NORM) block_sum_store<kS3Threads>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// Residual + full weighting. Coarse point (ic, jc, kc) has fine centre
+// (2ic+1, 2jc+1, 2kc+1) (0-based):
+//   along x: t1 = (rh(2ic) + rh(2ic+2)) + 2 rh(2ic+1)
+//   along y: t2 = (t1(2jc) + t1(2jc+2)) + 2 t1(2jc+1)
+//   along z: v  = (t2(2kc) + t2(2kc+2)) + 2 t2(2kc+1)
+//   bh_c = 0.0625 v        (= 4 R rh, R = (1,2,1)/4 per axis)
+// Block: 16x16 coarse columns; per fine plane the residual on the 33x33 fine
+// patch is formed in shared memory from a ring of three u planes.
+// ---------------------------------------------------------------------------
+constexpr int kR3 = 16;              // coarse tile edge
+constexpr int kR3F = 2 * kR3 + 1;    // fine residual patch edge (33)
+constexpr int kR3U = kR3F + 2;       // u patch edge incl. halo (35)
+constexpr int kR3Threads = kR3 * kR3;
+
+template <typename T, bool UNSCALED_B>
+__global__ void __launch_bounds__(kR3Threads)
+resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n, int Zc,
+                     T h2)
+{
+    __shared__ T su[3][kR3U * kR3U];
+    __shared__ T sr[kR3F * kR3F];
+    __shared__ T st1[kR3F * kR3];
+    const int nc = (n - 1) / 2;
+    const int t = threadIdx.x;
+    const int tic = t % kR3, tjc = t / kR3;
+    const int ic0 = blockIdx.x * kR3, jc0 = blockIdx.y * kR3;
+    const int ic = ic0 + tic, jc = jc0 + tjc;
+    const int fx0 = 2 * ic0, fy0 = 2 * jc0;  // fine patch origin (0-based)
+    const int kc0 = blockIdx.z * Zc, kc1 = min(kc0 + Zc, nc);
+    const int f0 = 2 * kc0, f1 = 2 * kc1;
+    const size_t plane = (size_t)n * n;
+
+    auto load_plane = [&](int slot, int fz) {
+        for (int q = t; q < kR3U * kR3U; q += kR3Threads) {
+            const int i = q % kR3U - 1, j = q / kR3U - 1;
+            su[slot][q] = get3(u, n, fx0 + i, fy0 + j, fz);
+        }
+    };
+    load_plane((f0 - 1 + 3) % 3, f0 - 1);
+    load_plane(f0 % 3, f0);
+    T t2a = T(0), t2b = T(0);  // y-pass of fine planes f-2, f-1
+    for (int f = f0; f <= f1; ++f) {
+        load_plane((f + 1) % 3, f + 1);
+        __syncthreads();
+        const T *um = su[(f + 2) % 3], *uc = su[f % 3], *up = su[(f + 1) % 3];
+        for (int q = t; q < kR3F * kR3F; q += kR3Threads) {
+            const int i = q % kR3F, j = q / kR3F;
+            const int x = fx0 + i, y = fy0 + j;
+            const int p = (j + 1) * kR3U + (i + 1);
+            T r = T(0);
+            if (x < n && y < n && f < n) {
+                T bb = b[(size_t)f * plane + (size_t)y * n + x];
+                if (UNSCALED_B) bb = rmul(h2, bb);
+                const T s = radd(radd(radd(uc[p - 1], uc[p + 1]), radd(uc[p - kR3U], uc[p + kR3U])),
+                                 radd(um[p], up[p]));
+                r = radd(rfma(T(-6), uc[p], bb), s);
+            }
+            sr[q] = r;
+        }
+        __syncthreads();
+        for (int q = t; q < kR3F * kR3; q += kR3Threads) {
+            const int k = q % kR3, j = q / kR3;
+            const T *row = &sr[j * kR3F + 2 * k];
+            st1[q] = rfma(T(2), row[1], radd(row[0], row[2]));
+        }
+        __syncthreads();
+        const T t2 = rfma(T(2), st1[(2 * tjc + 1) * kR3 + tic], radd(st1[2 * tjc * kR3 + tic], st1[(2 * tjc + 2) * kR3 + tic]));
+        if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
+            const int kc = f / 2 - 1;
+            const T v = rfma(T(2), t2b, radd(t2a, t2));
+            bc[((size_t)kc * nc + jc) * nc + ic] = rmul(T(0.0625), v);
+        }
+        t2a = t2b;
+        t2b = t2;
+        __syncthreads();  // the ring slot of plane f - 1 is reloaded next
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Trilinear interpolation + correction u += P e: the value at fine point
+// (fx, fy, fz) (0-based) is built along x, then y, then z:
+//   along x: fx = 2k+1 -> e(k);  fx = 2k -> 0.5 (e(k-1) + e(k))
+//   same along y on the x-values, then along z; u = u + value.
+// Thread per fine (x, y) column of a 32x8 tile, marching over coarse planes.
+// ---------------------------------------------------------------------------
+constexpr int kP3X = 32, kP3Y = 8;
+
+template <typename T>
+__device__ __forceinline__ T p3_interp_x(const T *e, int nc, int fx, int jc, int kc)
+{
+    if (fx & 1) return get3(e, nc, fx >> 1, jc, kc);
+    const int k = fx >> 1;
+    return rmul(T(0.5), radd(get3(e, nc, k - 1, jc, kc), get3(e, nc, k, jc, kc)));
+}
+
+template <typename T>
+__device__ __forceinline__ T p3_interp_xy(const T *e, int nc, int fx, int fy, int kc)
+{
+    if (fy & 1) return p3_interp_x(e, nc, fx, fy >> 1, kc);
+    const int m = fy >> 1;
+    return rmul(T(0.5), radd(p3_interp_x(e, nc, fx, m - 1, kc), p3_interp_x(e, nc, fx, m, kc)));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kP3X * kP3Y)
+prolong3d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Zc)
+{
+    const int nc = (n - 1) / 2;
+    const int fx = blockIdx.x * kP3X + threadIdx.x % kP3X;
+    const int fy = blockIdx.y * kP3Y + threadIdx.x / kP3X;
+    if (fx >= n || fy >= n) return;
+    const int m0 = blockIdx.z * Zc, m1 = min(m0 + Zc, nc + 1);
+    const size_t plane = (size_t)n * n;
+    T prev = p3_interp_xy(e, nc, fx, fy, m0 - 1);
+    for (int m = m0; m < m1; ++m) {
+        const T cur = p3_interp_xy(e, nc, fx, fy, m);
+        {
+            T *p = u + (size_t)(2 * m) * plane + (size_t)fy * n + fx;
+            *p = radd(*p, rmul(T(0.5), radd(prev, cur)));
+        }
+        if (m < nc) {
+            T *p = u + (size_t)(2 * m + 1) * plane + (size_t)fy * n + fx;
+            *p = radd(*p, cur);
+        }
+        prev = cur;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scaled residual rh = fma(-6, u, bh) + s (as in the sweep), InT arithmetic,
+// written as OutT, with one squared partial sum per block. Thread per (x, y)
+// column of a 32x8 tile; in-plane neighbours from global memory (L1).
+// ---------------------------------------------------------------------------
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(kP3X * kP3Y)
+residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out, int n,
+                  int Z, InT h2, bool unscaled, double *__restrict__ partials)
+{
+    const int x = blockIdx.x * kP3X + threadIdx.x % kP3X;
+    const int y = blockIdx.y * kP3Y + threadIdx.x / kP3X;
+    const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
+    const bool in = x < n && y < n;
+    const size_t plane = (size_t)n * n;
+    double acc = 0.0;
+    if (in) {
+        InT u_prev = get3(u, n, x, y, z0 - 1), u_cur = get3(u, n, x, y, z0);
+        for (int z = z0; z < z1; ++z) {
+            const InT u_next = get3(u, n, x, y, z + 1);
+            const InT s = radd(radd(radd(get3(u, n, x - 1, y, z), get3(u, n, x + 1, y, z)),
+                                    radd(get3(u, n, x, y - 1, z), get3(u, n, x, y + 1, z))),
+                               radd(u_prev, u_next));
+            const size_t p = (size_t)z * plane + (size_t)y * n + x;
+            InT bb = b[p];
+            if (unscaled) bb = rmul(h2, bb);
+            const InT r = radd(rfma(InT(-6), u_cur, bb), s);
+            acc = fma((double)r, (double)r, acc);
+            if (rh_out) rh_out[p] = (OutT)r;
+            u_prev = u_cur;
+            u_cur = u_next;
+        }
+    }
+    if (partials)
+        block_sum_store<kP3X * kP3Y>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+Grid3 sweep3d_grid(int n)
+{
+    Grid3 g;
+    g.bx = g.by = (n + kS3Out - 1) / kS3Out;
+    g.Z = chunk_rows(g.bx * g.by, n, 4 * num_sms(), 4, 64);
+    g.bz = (n + g.Z - 1) / g.Z;
+    return g;
+}
+
+Grid3 residual3d_grid(int n)
+{
+    Grid3 g;
+    g.bx = (n + kP3X - 1) / kP3X;
+    g.by = (n + kP3Y - 1) / kP3Y;
+    g.Z = chunk_rows(g.bx * g.by, n, 8 * num_sms(), 4, 64);
+    g.bz = (n + g.Z - 1) / g.Z;
+    return g;
+}
+
+template <typename T>
+cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
+                           double *partials, cudaStream_t s)
+{
+    const Grid3 g = sweep3d_grid(n);
+    const dim3 grid(g.bx, g.by, g.bz);
+    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    const T c0 = T(c[0]), c1 = T(c[1]);
+#define MG_SWEEP(ZU, UB, NRM) \
+    sweep3d_kernel<T, ZU, UB, NRM><<<grid, kS3Threads, 0, s>>>(u, b, out, n, g.Z, c0, c1, h2, partials)
+    const bool z = u == nullptr, nrm = partials != nullptr;
+    if (z) {
+        if (unscaled) {
+            if (nrm) MG_SWEEP(true, true, true); else MG_SWEEP(true, true, false);
+        } else {
+            if (nrm) MG_SWEEP(true, false, true); else MG_SWEEP(true, false, false);
+        }
+    } else {
+        if (unscaled) {
+            if (nrm) MG_SWEEP(false, true, true); else MG_SWEEP(false, true, false);
+        } else {
+            if (nrm) MG_SWEEP(false, false, true); else MG_SWEEP(false, false, false);
+        }
+    }
+#undef MG_SWEEP
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_resrestrict3d(const T *u, const T *b, bool unscaled, T *bc, int n, cudaStream_t s)
+{
+    const int nc = (n - 1) / 2;
+    const int bxy = (nc + kR3 - 1) / kR3;
+    const int Zc = chunk_rows(bxy * bxy, nc, 8 * num_sms(), 2, 32);
+    const dim3 grid(bxy, bxy, (nc + Zc - 1) / Zc);
+    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    if (unscaled)
+        resrestrict3d_kernel<T, true><<<grid, kR3Threads, 0, s>>>(u, b, bc, n, Zc, h2);
+    else
+        resrestrict3d_kernel<T, false><<<grid, kR3Threads, 0, s>>>(u, b, bc, n, Zc, h2);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong3d(const T *e, T *u, int n, cudaStream_t s)
+{
+    const int nc = (n - 1) / 2;
+    const int bx = (n + kP3X - 1) / kP3X, by = (n + kP3Y - 1) / kP3Y;
+    const int Zc = chunk_rows(bx * by, nc + 1, 8 * num_sms(), 2, 32);
+    const dim3 grid(bx, by, (nc + 1 + Zc - 1) / Zc);
+    prolong3d_kernel<T><<<grid, kP3X * kP3Y, 0, s>>>(e, u, n, Zc);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename InT, typename OutT>
+cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
+                              cudaStream_t s)
+{
+    const Grid3 g = residual3d_grid(n);
+    const InT h2 = InT(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kP3X * kP3Y, 0, s>>>(u, b, rh, n, g.Z, h2, unscaled,
+                                                                               partials);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+#define MG_INST(T)                                                                                   \
+    template cudaError_t launch_sweep3d<T>(const T *, const T *, bool, T *, int, const double *,     \
+                                           double *, cudaStream_t);                                  \
+    template cudaError_t launch_resrestrict3d<T>(const T *, const T *, bool, T *, int, cudaStream_t); \
+    template cudaError_t launch_prolong3d<T>(const T *, T *, int, cudaStream_t);
+MG_INST(double)
+MG_INST(float)
+#undef MG_INST
+template cudaError_t launch_residual3d<double, double>(const double *, const double *, bool, double *, int,
+                                                       double *, cudaStream_t);
+template cudaError_t launch_residual3d<double, float>(const double *, const double *, bool, float *, int,
+                                                      double *, cudaStream_t);
+template cudaError_t launch_residual3d<float, float>(const float *, const float *, bool, float *, int,
+                                                     double *, cudaStream_t);
+
+}  // namespace mg

@@ -1,0 +1,225 @@
+// mg_tail.cu -- the coarse tail of the cycle in one thread block, and the
+// coarsest-grid solve (He, Liu, Wang, arXiv:2206.05543, Sec. 4).
+//
+// The last levels of the hierarchy (a few hundred points) are far too small
+// to fill the GPU; one launch per operator per level would be pure launch
+// latency. One block therefore runs the whole tail of a cycle: the host
+// writes the cycle's operations on these levels (zero, sweep, residual +
+// restriction, exact solve, interpolation + correction, V or W order) into
+// the kernel's argument block, and the block executes them in order with a
+// block barrier between operations. Level arrays stay in global memory
+// (resident in L1/L2 at these sizes).
+//
+// Formulas and their rounding order are identical to the marching kernels
+// (see mg_kernels2d.cu / mg_kernels3d.cu); the coarsest solve uses the LU
+// factors of h0^2 A_h0 computed once on the host by Gaussian elimination
+// without pivoting in the natural order (unknowns x fastest):
+//   forward:  y_i = y_i - l_ik y_k          for k = 0 .. i-1
+//   backward: s = y_i - u_ij x_j (j = i+1 .. m-1, increasing); x_i = s / u_ii
+// with every product rounded before the subtraction.
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+template <typename T>
+__device__ __forceinline__ T at(const T *a, int n, int x, int y, int z)
+{
+    if (x < 0 || x >= n || y < 0 || y >= n || z < 0 || z >= n) return T(0);
+    return a[((size_t)z * n + y) * n + x];
+}
+
+template <typename T>
+__device__ T residual_at(int d, const T *u, const T *bh, int n, int x, int y, int z)
+{
+    const size_t p = ((size_t)z * n + y) * n + x;
+    if (d == 2) {
+        const T s = radd(radd(at(u, n, x - 1, y, 0), at(u, n, x + 1, y, 0)),
+                         radd(at(u, n, x, y - 1, 0), at(u, n, x, y + 1, 0)));
+        return radd(rfma(T(-4), u[p], bh[p]), s);
+    }
+    const T s = radd(radd(radd(at(u, n, x - 1, y, z), at(u, n, x + 1, y, z)),
+                          radd(at(u, n, x, y - 1, z), at(u, n, x, y + 1, z))),
+                     radd(at(u, n, x, y, z - 1), at(u, n, x, y, z + 1)));
+    return radd(rfma(T(-6), u[p], bh[p]), s);
+}
+
+template <typename T>
+__device__ T sweep_at(int d, const T *rh, const T *u, int n, int x, int y, int z, T c0, T c1, T c2)
+{
+    const size_t p = ((size_t)z * n + y) * n + x;
+    if (d == 2) {
+        const T E = radd(radd(at(rh, n, x - 1, y, 0), at(rh, n, x + 1, y, 0)),
+                         radd(at(rh, n, x, y - 1, 0), at(rh, n, x, y + 1, 0)));
+        const T C = radd(radd(at(rh, n, x - 1, y - 1, 0), at(rh, n, x + 1, y - 1, 0)),
+                         radd(at(rh, n, x - 1, y + 1, 0), at(rh, n, x + 1, y + 1, 0)));
+        return rfma(c2, C, rfma(c1, E, rfma(c0, rh[p], u[p])));
+    }
+    const T E = radd(radd(radd(at(rh, n, x - 1, y, z), at(rh, n, x + 1, y, z)),
+                          radd(at(rh, n, x, y - 1, z), at(rh, n, x, y + 1, z))),
+                     radd(at(rh, n, x, y, z - 1), at(rh, n, x, y, z + 1)));
+    return rfma(c1, E, rfma(c0, rh[p], u[p]));
+}
+
+// full weighting along x of fine row (fy, fz) around fine column 2ic+1
+template <typename T>
+__device__ __forceinline__ T fw_x(const T *rh, int n, int ic, int fy, int fz)
+{
+    const T *row = rh + ((size_t)fz * n + fy) * n;
+    return rfma(T(2), row[2 * ic + 1], radd(row[2 * ic], row[2 * ic + 2]));
+}
+
+template <typename T>
+__device__ T restrict_at(int d, const T *rh, int n, int ic, int jc, int kc)
+{
+    if (d == 2) {
+        const T t0 = fw_x(rh, n, ic, 2 * jc, 0), t1 = fw_x(rh, n, ic, 2 * jc + 1, 0),
+                t2 = fw_x(rh, n, ic, 2 * jc + 2, 0);
+        return rmul(T(0.25), rfma(T(2), t1, radd(t0, t2)));
+    }
+    T tz[3];
+    for (int k = 0; k < 3; ++k) {
+        const int fz = 2 * kc + k;
+        const T t0 = fw_x(rh, n, ic, 2 * jc, fz), t1 = fw_x(rh, n, ic, 2 * jc + 1, fz),
+                t2 = fw_x(rh, n, ic, 2 * jc + 2, fz);
+        tz[k] = rfma(T(2), t1, radd(t0, t2));
+    }
+    return rmul(T(0.0625), rfma(T(2), tz[1], radd(tz[0], tz[2])));
+}
+
+// linear interpolation of the coarse array e (nc points per axis) at fine
+// 0-based coordinates: along x, then y, then z.
+template <typename T>
+__device__ T interp_x(const T *e, int nc, int fx, int jc, int kc)
+{
+    // fine 0-based fx = 2k+1 sits on coarse k; fx = 2k lies between k-1 and k
+    if (fx & 1) return at(e, nc, fx >> 1, jc, kc);
+    const int k = fx >> 1;
+    return rmul(T(0.5), radd(at(e, nc, k - 1, jc, kc), at(e, nc, k, jc, kc)));
+}
+
+template <typename T>
+__device__ T interp_xy(const T *e, int nc, int fx, int fy, int kc)
+{
+    if (fy & 1) return interp_x(e, nc, fx, fy >> 1, kc);
+    const int m = fy >> 1;
+    return rmul(T(0.5), radd(interp_x(e, nc, fx, m - 1, kc), interp_x(e, nc, fx, m, kc)));
+}
+
+template <typename T>
+__device__ T interp_at(int d, const T *e, int nc, int fx, int fy, int fz)
+{
+    if (d == 2) return interp_xy(e, nc, fx, fy, 0);
+    if (fz & 1) return interp_xy(e, nc, fx, fy, fz >> 1);
+    const int q = fz >> 1;
+    return rmul(T(0.5), radd(interp_xy(e, nc, fx, fy, q - 1), interp_xy(e, nc, fx, fy, q)));
+}
+
+template <typename T>
+__device__ void coarse_substitution(int d, const double *lu, const T *bh, T *x)
+{
+    const int m = d == 2 ? 9 : 27;
+    double y[27], xs[27];
+    for (int i = 0; i < m; ++i) y[i] = (double)bh[i];
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < i; ++k) y[i] = __dsub_rn(y[i], __dmul_rn(lu[i * m + k], y[k]));
+    for (int i = m - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int j = i + 1; j < m; ++j) s = __dsub_rn(s, __dmul_rn(lu[i * m + j], xs[j]));
+        xs[i] = __ddiv_rn(s, lu[i * m + i]);
+    }
+    for (int i = 0; i < m; ++i) x[i] = (T)xs[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
+{
+    const int d = a.d;
+    const T c0 = T(a.c[0]), c1 = T(a.c[1]), c2 = T(a.c[2]);
+    for (int o = 0; o < a.nops; ++o) {
+        const int kind = a.ops[o].kind, l = a.ops[o].level;
+        const TailLevel &L = a.lv[l];
+        const int n = L.n;
+        const int np = d == 2 ? n * n : n * n * n;
+        T *u = (T *)L.u, *tmp = (T *)L.tmp, *bh = (T *)L.bh, *rh = (T *)L.rh;
+        auto coords = [&](int i, int nn, int &x, int &y, int &z) {
+            x = i % nn;
+            y = (i / nn) % nn;
+            z = d == 2 ? 0 : i / (nn * nn);
+        };
+        if (kind == TAIL_ZERO) {
+            for (int i = threadIdx.x; i < np; i += blockDim.x) u[i] = T(0);
+        } else if (kind == TAIL_SWEEP || kind == TAIL_RESTRICT) {
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                int x, y, z;
+                coords(i, n, x, y, z);
+                rh[i] = residual_at(d, u, bh, n, x, y, z);
+            }
+            __syncthreads();
+            if (kind == TAIL_SWEEP) {
+                for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                    int x, y, z;
+                    coords(i, n, x, y, z);
+                    tmp[i] = sweep_at(d, rh, u, n, x, y, z, c0, c1, c2);
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < np; i += blockDim.x) u[i] = tmp[i];
+            } else {
+                const TailLevel &C = a.lv[l + 1];
+                const int nc = C.n, npc = d == 2 ? nc * nc : nc * nc * nc;
+                T *bc = (T *)C.bh;
+                for (int i = threadIdx.x; i < npc; i += blockDim.x) {
+                    int x, y, z;
+                    coords(i, nc, x, y, z);
+                    bc[i] = restrict_at(d, rh, n, x, y, z);
+                }
+            }
+        } else if (kind == TAIL_SOLVE) {
+            if (threadIdx.x == 0) coarse_substitution<T>(d, a.lu, bh, u);
+        } else if (kind == TAIL_PROLONG) {
+            const TailLevel &C = a.lv[l + 1];
+            const T *e = (const T *)C.u;
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                int x, y, z;
+                coords(i, n, x, y, z);
+                u[i] = radd(u[i], interp_at(d, e, C.n, x, y, z));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_tail(const TailArgs &a, cudaStream_t s)
+{
+    tail_kernel<T><<<1, kTailThreads, 0, s>>>(a);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tail<double>(const TailArgs &, cudaStream_t);
+template cudaError_t launch_tail<float>(const TailArgs &, cudaStream_t);
+
+// LU factors of the scaled coarsest operator h0^2 A_h0 (3^d unknowns, natural
+// order), written into lu (m*m, row-major): strict lower part = multipliers,
+// upper part incl. diagonal = U. Host code, compiled without contraction.
+void coarse_lu(int d, double *lu)
+{
+    const int n = 3, m = d == 2 ? 9 : 27;
+    for (int i = 0; i < m; ++i) {
+        const int xi = i % n, yi = (i / n) % n, zi = i / (n * n);
+        for (int j = 0; j < m; ++j) {
+            const int xj = j % n, yj = (j / n) % n, zj = j / (n * n);
+            const int dist = abs(xi - xj) + abs(yi - yj) + abs(zi - zj);
+            lu[i * m + j] = i == j ? 2.0 * d : (dist == 1 ? -1.0 : 0.0);
+        }
+    }
+    for (int k = 0; k < m; ++k)
+        for (int i = k + 1; i < m; ++i) {
+            const double l = lu[i * m + k] / lu[k * m + k];
+            for (int j = k + 1; j < m; ++j) lu[i * m + j] = lu[i * m + j] - l * lu[k * m + j];
+            lu[i * m + k] = l;
+        }
+}
+
+}  // namespace mg

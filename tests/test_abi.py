@@ -1,0 +1,85 @@
+"""The C ABI library builds, loads and exports every symbol include/mg.h
+declares; argument validation happens before any GPU work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+from paper_2206_05543_gb300 import binding, smoothers
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = binding.lib()
+    declared = _declared()
+    assert {"mg_setup", "mg_solve", "mg_vcycle", "mg_destroy", "mg_strerror"} <= declared
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    assert declared == set(binding.SIGNATURES), "binding signatures out of sync with include/mg.h"
+
+
+def test_strerror_and_counters_without_gpu():
+    L = binding.lib()
+    assert L.mg_strerror(0) == b"success"
+    assert L.mg_strerror(-4).startswith(b"not converged")
+    assert L.mg_kernel_launch_count() >= 0
+
+
+@pytest.mark.parametrize("d,N,nc,nu1,nu2,prec", [
+    (4, 64, 1, 1, 1, 0),      # bad dimension
+    (2, 48, 1, 1, 1, 0),      # N not a power of two
+    (2, 2, 1, 1, 1, 0),       # N < 4
+    (2, 64, 4, 1, 1, 0),      # too many weights in 2D
+    (3, 64, 3, 1, 1, 0),      # too many weights in 3D
+    (2, 64, 1, 0, 0, 0),      # no smoothing at all
+    (2, 64, 1, -1, 1, 0),     # negative sweeps
+    (2, 64, 1, 1, 1, 7),      # unknown precision
+])
+def test_setup_rejects_bad_arguments(d, N, nc, nu1, nu2, prec):
+    L = binding.lib()
+    c = (ctypes.c_double * 4)(0.2, 0.05, 0.01, 0.0)
+    ctx = ctypes.c_void_p()
+    st = L.mg_setup(d, N, c, nc, nu1, nu2, prec, None, ctypes.byref(ctx))
+    assert st == binding.MG_EINVAL
+    assert not ctx.value
+
+
+def test_setup_rejects_non_finite_weights():
+    L = binding.lib()
+    c = (ctypes.c_double * 3)(0.2, float("nan"), 0.0)
+    ctx = ctypes.c_void_p()
+    assert L.mg_setup(2, 64, c, 3, 1, 1, 0, None, ctypes.byref(ctx)) == binding.MG_EINVAL
+
+
+def test_op_entry_points_validate_sizes():
+    L = binding.lib()
+    c = (ctypes.c_double * 3)(0.2, 0.05, 0.01)
+    # n must be 2^k - 1 >= 3; null buffers are rejected before any launch
+    assert L.mg_op_sweep(2, 8, 0, c, 3, None, None, 0, None, None, None) == binding.MG_EINVAL
+    assert L.mg_op_sweep(2, 7, 0, c, 3, None, None, 0, None, None, None) == binding.MG_EINVAL
+    assert L.mg_op_residual_restrict(3, 3, 0, None, None, 0, None, None) == binding.MG_EINVAL
+    assert L.mg_op_coarse_solve(5, 0, None, None, None) == binding.MG_EINVAL
+
+
+def test_package_weights_equal_oracle_weights():
+    """The library's default weights are the correctly rounded closed forms,
+    bit for bit equal to the oracle's independent derivation."""
+    from oracle import coeffs
+    for (d, name), w in smoothers.BY_NAME.items():
+        ref = coeffs.weights(d, name)
+        ref = ref[: len(w)]
+        assert np.array_equal(np.array(w), np.array(ref)), (d, name)
+        assert all(r == 0.0 for r in coeffs.weights(d, name)[len(w):])

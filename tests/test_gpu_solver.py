@@ -1,0 +1,168 @@
+"""GPU parity of the whole solver against the FP64 oracle, through the C ABI.
+
+FP64 contexts: every operator evaluates the oracle's operation order, so the
+iterates u_k are bit-identical and the per-cycle residual norms differ only
+by the order of the final sum of squares; the test bound is 1e-12 relative
+(the tolerance stated for FP64 sweeps and per-cycle residual norms).
+Refinement contexts (FP32 cycle inside FP64 refinement): the FP64 residual
+of the result, recomputed by the oracle, must be <= tol * ||b||, and the
+solution must match the oracle's FP64 solution to the accuracy the common
+stopping rule allows (bound stated in each test).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import coeffs, exact
+from paper_2206_05543_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2206_05543_gb300 import binding  # noqa: E402
+from paper_2206_05543_gb300.binding import MG_ENAN, MG_ENOCONV, MG_OK, MGError, Solver  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=torch.float64)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _parity(d, N, b, name=None, nu1=1, nu2=1, gamma=1, u0=None, tol=1e-10, max_cycles=60):
+    w = coeffs.weights(d, name) if name else coeffs.default(d)
+    ref = oracle.solve(b, w, u0=u0, tol=tol, max_cycles=max_cycles, nu1=nu1, nu2=nu2, gamma=gamma)
+    with Solver(d, N, w, nu1=nu1, nu2=nu2, gamma=gamma) as s:
+        u = dev(u0 if u0 is not None else np.zeros_like(b))
+        info = s.solve(dev(b), u, tol=tol, max_cycles=max_cycles)
+        got = host(info.u)
+    assert info.status == ref.status
+    assert info.cycles == ref.cycles
+    np.testing.assert_allclose(info.hist, ref.hist, rtol=1e-12, atol=0)
+    assert np.array_equal(got, ref.u)
+    return info, ref
+
+
+@pytest.mark.parametrize("rhs", ["sine", "uniform"])
+def test_config_2d_n64(rhs):
+    """2D, N = 64, manufactured sine and uniform[-1, 1] right-hand sides,
+    V(1,1) with M9, to 1e-10."""
+    b = inputs.sine(2, 64) if rhs == "sine" else inputs.uniform(2, 64, 0)
+    info, ref = _parity(2, 64, b)
+    assert info.converged and 8 <= info.cycles <= 12
+    if rhs == "sine":
+        uh = exact.manufactured_factor(64) * exact.sine_product(2, 64)
+        assert np.abs(ref.u - uh).max() <= 1e-9 * np.abs(uh).max()
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 128, 256, 512, 1024])
+def test_2d_sizes(N):
+    _parity(2, N, inputs.uniform(2, N, N))
+
+
+@pytest.mark.parametrize("name", ["jacobi", "m5", "vanka", "tw5"])
+def test_2d_other_smoothers(name):
+    _parity(2, 128, inputs.uniform(2, 128, 1), name=name, max_cycles=80)
+
+
+def test_2d_w_cycle_and_random_start():
+    """W(1+0) and the paper's uniform (0,1) initial guess (Sec. 4)."""
+    b = inputs.uniform(2, 128, 2)
+    u0 = np.random.default_rng(7).uniform(0.0, 1.0, b.shape)
+    _parity(2, 128, b, nu1=1, nu2=0, gamma=2, u0=u0)
+    _parity(2, 128, b, u0=u0)
+
+
+@pytest.mark.parametrize("N,nu", [(4, 1), (8, 1), (16, 1), (32, 1), (64, 1), (32, 2), (64, 2)])
+def test_3d_sizes(N, nu):
+    _parity(3, N, inputs.uniform(3, N, N), nu1=nu, nu2=nu)
+
+
+def test_3d_sine_and_jacobi():
+    _parity(3, 32, inputs.sine(3, 32))
+    _parity(3, 32, inputs.uniform(3, 32, 3), name="jacobi", max_cycles=80)
+
+
+def test_vcycle_single_cycle_bitwise():
+    for d, N in ((2, 256), (3, 32)):
+        b = inputs.uniform(d, N, 4)
+        u0 = np.random.default_rng(5).uniform(0, 1, b.shape)
+        ref = oracle.cycles(b, u0, coeffs.default(d), 1)
+        with Solver(d, N) as s:
+            u = dev(u0)
+            s.vcycle(u, dev(b))
+            assert np.array_equal(host(u), ref)
+            # a second call with other buffers re-records the graphs
+            u2, b2 = dev(u0), dev(b.copy())
+            s.vcycle(u2, b2)
+            assert np.array_equal(host(u2), ref)
+            assert s.residual_norm(u2, b2) == pytest.approx(oracle.residual_norm(ref, b), rel=1e-12)
+
+
+def test_zero_rhs_and_stopping_edge_cases():
+    with Solver(2, 64) as s:
+        info = s.solve(dev(np.zeros((63, 63))))
+        assert info.status == MG_OK and info.cycles == 0 and info.relres == 0.0
+        assert not host(info.u).any()
+        b = inputs.uniform(2, 64, 6)
+        info = s.solve(dev(b), max_cycles=1)
+        assert info.status == MG_ENOCONV and info.cycles == 1
+        assert np.array_equal(host(info.u), oracle.cycles(b, np.zeros_like(b), coeffs.default(2), 1))
+        info = s.solve(dev(b), max_cycles=0)
+        assert info.status == MG_ENOCONV and info.cycles == 0
+        bad = b.copy()
+        bad[10, 10] = np.nan
+        info = s.solve(dev(bad))
+        assert info.status == MG_ENAN
+
+
+def test_invalid_arguments_raise():
+    with pytest.raises(MGError):
+        Solver(2, 48)
+    with pytest.raises(MGError):
+        Solver(3, 64, coeffs=(0.1, 0.2, 0.3))
+    with Solver(2, 64) as s:
+        with pytest.raises(ValueError):
+            s.solve(dev(np.zeros((64, 64))))
+
+
+@pytest.mark.parametrize("d,N,nu,tol_u", [(2, 256, 1, 1e-8), (2, 1024, 1, 1e-8), (3, 32, 2, 1e-8), (3, 64, 2, 1e-8)])
+def test_mixed_precision_refinement(d, N, nu, tol_u):
+    """FP32 cycle inside FP64 refinement reaches the FP64 tolerance 1e-10.
+    Check: the oracle's FP64 residual of the result and the distance to the
+    exact discrete solution (sine transform) against the plain FP64 solve."""
+    b = inputs.uniform(d, N, 8)
+    with Solver(d, N, nu1=nu, nu2=nu, precision="fp32_ir") as s:
+        info = s.solve(dev(b), tol=1e-10, max_cycles=60)
+        u = host(info.u)
+    assert info.converged
+    r = oracle.residual_norm(u, b)
+    assert r <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
+    assert info.hist[-1] == pytest.approx(r, rel=1e-6)
+    ustar = exact.dst_solve(b)
+    ref = oracle.solve(b, coeffs.default(d), tol=1e-10, nu1=nu, nu2=nu)
+    err_mixed = np.linalg.norm(u - ustar) / np.linalg.norm(ustar)
+    err_fp64 = np.linalg.norm(ref.u - ustar) / np.linalg.norm(ustar)
+    assert err_mixed <= max(tol_u, 10 * err_fp64)
+
+
+@pytest.mark.slow
+def test_config_2d_n8192_two_cycles_bitwise():
+    """Full-size 2D workload (N = 8192, 67M unknowns, uniform b seed 0, zero
+    start): the first two V(1,1) cycles and the residual norms r_0..r_2 in
+    the launch configuration the benchmark times."""
+    N = 8192
+    b = inputs.uniform(2, N, 0)
+    ref = oracle.solve(b, coeffs.default(2), tol=0.0, max_cycles=2)
+    with Solver(2, N) as s:
+        info = s.solve(dev(b), tol=0.0, max_cycles=2)
+        got = host(info.u)
+    assert info.cycles == 2
+    np.testing.assert_allclose(info.hist, ref.hist, rtol=1e-12, atol=0)
+    assert np.array_equal(got, ref.u)
