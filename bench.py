@@ -221,6 +221,15 @@ def run_ours(args):
     barrier()
     launches = binding.kernel_launch_count() - launches0
     ms = e0.elapsed_time(e1)
+    if args.only_solve:
+        clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": UNKNOWNS * cycles / (ms * 1e-3), "unit": "DOF/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": ms / args.steps, "cycles": cycles, "gpu_launches": launches,
+                              "note": "solve-only run"}), flush=True)
+        solver.close()
+        return
     if world > 1:
         t = torch.tensor([ms, cycles], dtype=torch.float64, device="cuda")
         tmax = t.clone()
@@ -333,6 +342,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="time the solves only (no e2e, kernel, mixed or CPU legs); used for profiler launch lists")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
