@@ -128,6 +128,28 @@ mg_status mg_op_prolong_correct(int d, int n, mg_prec prec, const void *e_coarse
 /* Exact solve of h0^2 A_h0 x = bh on the coarsest grid (n = 3, 3^d points). */
 mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, void *stream);
 
+/* One SPAI sweep with the squared residual norm of its input, allocating
+ * nothing. The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc -- code running while its stream is captured into a
+ * CUDA graph, code confined to a framework's own memory pool, or loops that
+ * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * Arguments as for mg_op_sweep, except that the norm goes to DEVICE memory:
+ * rnorm2_dev_out (one double, caller-owned) receives sum(rh^2) of the input
+ * u, written by a kernel on `stream`; nothing is copied to the host and the
+ * call does not synchronise.
+ * Scratch: the per-block partial sums live in a fixed 256 KiB array in device
+ * memory inside the library (every GPU that loads the library holds it until
+ * the process exits). Sizes beyond it are rejected with MG_EINVAL before any
+ * CUDA work: n <= 16383 in 2D, n <= 1023 in 3D (and at most 32768 blocks).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Every block overwrites its own partial sum, so no clearing is needed. */
+mg_status mg_op_sweep_norm_noalloc(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs,
+                                   const void *u, const void *bh, int b_unscaled, void *u_out,
+                                   double *rnorm2_dev_out, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* diagnostics                                                            */
 /* ---------------------------------------------------------------------- */

@@ -39,6 +39,7 @@ SIGNATURES = {
     "mg_op_residual_restrict": (_I, [_I, _I, _I, _P, _P, _I, _P, _P]),
     "mg_op_prolong_correct": (_I, [_I, _I, _I, _P, _P, _P]),
     "mg_op_coarse_solve": (_I, [_I, _I, _P, _P, _P]),
+    "mg_op_sweep_norm_noalloc": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _P, _P]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_cuda_error": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (_U, []),
