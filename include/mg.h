@@ -55,9 +55,10 @@ typedef enum {
 } mg_status;
 
 typedef enum {
-    MG_FP64 = 0,   /* every level and every operation in FP64 */
-    MG_FP32_IR = 1 /* FP32 cycle inside FP64 iterative refinement: the outer
-                      residual b - A u and the update u += e in FP64 */
+    MG_FP64 = 0,    /* every level and every operation in FP64; u, b are double */
+    MG_FP32_IR = 1, /* FP32 cycle inside FP64 iterative refinement: the outer
+                       residual b - A u and the update u += e in FP64; u, b double */
+    MG_FP32 = 2     /* every level and every operation in FP32; u, b are float */
 } mg_prec;
 
 /* ---------------------------------------------------------------------- */
@@ -78,13 +79,15 @@ mg_status mg_setup(int d, int N, const double *spai_coeffs, int ncoeffs, int nu1
 mg_status mg_setup_ex(int d, int N, const double *spai_coeffs, int ncoeffs, int nu1, int nu2,
                       int gamma, mg_prec prec, void *cuda_stream, mg_ctx **out);
 
-/* One cycle in place on u for right-hand side b (device arrays, FP64,
- * (N-1)^d). MG_FP64: one V/W cycle. MG_FP32_IR: one refinement step (FP64
- * residual, FP32 cycle for the correction, FP64 update). Asynchronous. */
+/* One cycle in place on u for right-hand side b (device arrays, (N-1)^d,
+ * double for MG_FP64 / MG_FP32_IR, float for MG_FP32). MG_FP64, MG_FP32: one
+ * V/W cycle. MG_FP32_IR: one refinement step (FP64 residual, FP32 cycle for
+ * the correction, FP64 update). Asynchronous. */
 mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b);
 
 /* Solve from the initial guess in u until ||b - A u_k||_2 <= tol ||b - A u_0||_2
- * or max_cycles cycles ran (Sec. 4). b, u: device FP64 arrays. cycles_out,
+ * or max_cycles cycles ran (Sec. 4). b, u: device arrays of the context's
+ * type (see mg_vcycle); residual norms are accumulated in FP64. cycles_out,
  * relres_out (= ||r_k||/||r_0||): nullable HOST pointers. hist_out: nullable
  * HOST array of max_cycles + 1 doubles receiving ||r_k||_2, k = 0..cycles.
  * Returns MG_OK, MG_ENOCONV (u and outputs still written) or MG_ENAN.
@@ -92,10 +95,35 @@ mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b);
 mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
                    double *relres_out, double *hist_out);
 
-/* ||b - A_h u||_2 (FP64) of device arrays u, b; result in *norm_out (HOST). */
+/* ||b - A_h u||_2 of device arrays u, b (context's type, norm accumulated in
+ * FP64); result in *norm_out (HOST). */
 mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out);
 
 void mg_destroy(mg_ctx *ctx);
+
+/* Replace the omega-folded weights of a context (HOST array, same rules as
+ * mg_setup); the recorded cycle is re-recorded on the next call. */
+mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs);
+
+/* ---------------------------------------------------------------------- */
+/* adjoint of K cycles                                                    */
+/* ---------------------------------------------------------------------- */
+
+/* Reverse-mode derivative of u_K = K cycles from u_0 = 0 for right-hand
+ * side b (the transpose of each step of Sec. 4's cycle: the sweep
+ * u' = u + W (bh - Ah u) of Eq. (2.1) becomes g <- g - Ah (W g) with
+ * dL/dbh += W g and dL/dc_j += <g, N_j rh>; restriction and interpolation
+ * swap roles, R^T = P / 2^d; the coarsest solve is symmetric).
+ * Inputs: b and grad_uK = dL/du_K, device arrays of the context's type
+ * (double for MG_FP64, float for MG_FP32; MG_FP32_IR is rejected).
+ * Outputs: grad_b_out = dL/db (device, same type) and grad_coeffs_out =
+ * dL/dc (HOST, ncoeffs doubles, summed over every sweep of every level and
+ * cycle, accumulated in FP64). Requires a V cycle (gamma = 1), nu1 >= 1 and N >= 8.
+ * The forward is replayed once keeping the input of every sweep of every
+ * level visit and each visit's right-hand side (device workspace owned by
+ * the context, allocated on the first call for a given K). Synchronises. */
+mg_status mg_vcycles_adjoint(mg_ctx *ctx, int K, const void *b, const void *grad_uK, void *grad_b_out,
+                             double *grad_coeffs_out);
 
 /* ---------------------------------------------------------------------- */
 /* single operators on one level (each step of the cycle, for checking)    */

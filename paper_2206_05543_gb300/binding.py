@@ -17,8 +17,8 @@ from . import build as _build
 from . import smoothers
 
 MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOCONV, MG_ENAN, MG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-MG_FP64, MG_FP32_IR = 0, 1
-PRECISIONS = {"fp64": MG_FP64, "fp32_ir": MG_FP32_IR, "mixed": MG_FP32_IR}
+MG_FP64, MG_FP32_IR, MG_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": MG_FP64, "fp32_ir": MG_FP32_IR, "mixed": MG_FP32_IR, "fp32": MG_FP32}
 
 _lock = threading.Lock()
 _lib = None
@@ -40,6 +40,8 @@ SIGNATURES = {
     "mg_op_prolong_correct": (_I, [_I, _I, _I, _P, _P, _P]),
     "mg_op_coarse_solve": (_I, [_I, _I, _P, _P, _P]),
     "mg_op_sweep_norm_noalloc": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _P, _P]),
+    "mg_set_coeffs": (_I, [_P, _DP, _I]),
+    "mg_vcycles_adjoint": (_I, [_P, _I, _P, _P, _P, _DP]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_cuda_error": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (_U, []),
@@ -135,8 +137,9 @@ class Solver:
     """Multigrid solver for A_h u = b on (0,1)^d, h = 1/N (one CUDA context object).
 
     coeffs: omega-folded SPAI weights (see smoothers.py; default M9 / M7).
-    precision: "fp64" (plain FP64 cycle) or "fp32_ir" (FP32 cycle inside FP64
-    iterative refinement). gamma = 1: V cycle, 2: W cycle.
+    precision: "fp64" (plain FP64 cycle, float64 arrays), "fp32_ir" (FP32 cycle
+    inside FP64 iterative refinement, float64 arrays) or "fp32" (plain FP32
+    cycle, float32 arrays). gamma = 1: V cycle, 2: W cycle.
     """
 
     def __init__(self, d: int, N: int, coeffs=None, nu1: int = 1, nu2: int = 1, gamma: int = 1,
@@ -147,6 +150,7 @@ class Solver:
         self.shape = (self.n,) * self.d
         self.coeffs = tuple(coeffs if coeffs is not None else smoothers.default(self.d))
         self.precision = precision
+        self.nu1, self.nu2, self.gamma = int(nu1), int(nu2), int(gamma)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         arr, nc = _coeff_array(self.coeffs)
         ctx = ctypes.c_void_p()
@@ -171,9 +175,36 @@ class Solver:
     def __exit__(self, *exc):
         self.close()
 
-    def _args(self, u, b):
+    @property
+    def dtype(self):
         torch = _torch()
-        return (_dev_ptr(u, torch.float64, self.shape, "u"), _dev_ptr(b, torch.float64, self.shape, "b"))
+        return torch.float32 if self.precision == "fp32" else torch.float64
+
+    def _args(self, u, b):
+        return (_dev_ptr(u, self.dtype, self.shape, "u"), _dev_ptr(b, self.dtype, self.shape, "b"))
+
+    def set_coeffs(self, coeffs):
+        arr, nc = _coeff_array(coeffs)
+        _check(lib().mg_set_coeffs(self._ctx, arr, nc), "mg_set_coeffs")
+        self.coeffs = tuple(float(x) for x in coeffs)
+
+    def cycles(self, b, K: int):
+        """u_K = K cycles from u_0 = 0 (asynchronous)."""
+        torch = _torch()
+        u = torch.zeros(self.shape, dtype=self.dtype, device=b.device)
+        for _ in range(K):
+            self.vcycle(u, b)
+        return u
+
+    def vcycles_adjoint(self, b, grad_uK, K: int):
+        """(dL/db, dL/dc) of u_K = K cycles from zero, given dL/du_K."""
+        torch = _torch()
+        gb = torch.empty_like(b)
+        gc = (ctypes.c_double * len(self.coeffs))()
+        _check(lib().mg_vcycles_adjoint(self._ctx, int(K), _dev_ptr(b, self.dtype, self.shape, "b"),
+                                        _dev_ptr(grad_uK, self.dtype, self.shape, "grad_uK"),
+                                        ctypes.c_void_p(gb.data_ptr()), gc), "mg_vcycles_adjoint")
+        return gb, np.array(list(gc))
 
     def vcycle(self, u, b):
         """One cycle in place on u (asynchronous on the solver's stream)."""
@@ -184,7 +215,7 @@ class Solver:
     def solve(self, b, u=None, tol: float = 1e-10, max_cycles: int = 100) -> SolveInfo:
         torch = _torch()
         if u is None:
-            u = torch.zeros(self.shape, dtype=torch.float64, device=b.device)
+            u = torch.zeros(self.shape, dtype=self.dtype, device=b.device)
         pu, pb = self._args(u, b)
         hist = np.zeros(max_cycles + 1)
         cyc = ctypes.c_int(0)

@@ -1,0 +1,57 @@
+// mg_ctx.h -- the solver context shared by the host translation units
+// (cycle recording in mg_host.cu, the adjoint in mg_adjoint.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/mg.h"
+
+// device workspace of the adjoint (allocated on first use)
+struct AdjointWork {
+    int K = 0;
+    std::vector<std::vector<std::vector<void *>>> work;  // [k][level][slot]
+    std::vector<std::vector<void *>> bh;                 // [k][level], level >= 1
+    std::vector<void *> G, GB, T;                        // per level
+    double *partials = nullptr;                          // per-block coefficient partials (3 per block)
+    int npartials = 0;
+    double *acc = nullptr;                               // 3 coefficient gradients (device)
+    std::vector<void *> owned;
+};
+
+struct GraphPair {
+    cudaGraphExec_t pre = nullptr, rest = nullptr;
+    unsigned long long pre_nodes = 0, rest_nodes = 0;
+};
+
+struct mg_ctx {
+    int d = 2, N = 0, L = 0, nu1 = 1, nu2 = 1, gamma = 1, lt = 0, dev = 0;
+    mg_prec prec = MG_FP64;
+    double c[3] = {0, 0, 0};
+    int ncoef = 0;
+    cudaStream_t user = nullptr, s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // hierarchy in the cycle's precision (double or float); level 0 of an
+    // FP64 context uses the caller's u and (unscaled) b for A and BH
+    std::vector<int> n;
+    std::vector<void *> A, B, BH, RH;
+    size_t esize = 8;
+    double *lu = nullptr;
+    double *partials = nullptr;
+    int npartials = 0;
+    double *d_norm2 = nullptr;
+    double *h_norm2 = nullptr;  // pinned
+    GraphPair g;
+    const void *cap_u = nullptr, *cap_b = nullptr;
+    std::vector<void *> owned;  // device allocations to free
+    // batched contexts
+    std::vector<mg_ctx *> members;
+    AdjointWork *adj = nullptr;
+};
+
+
+namespace mg {
+mg_status cuda_fail(cudaError_t e);
+void free_adjoint(mg_ctx *c);
+}  // namespace mg

@@ -25,6 +25,7 @@
 #include "../../include/mg.h"
 #include "mg_common.cuh"
 #include "mg_internal.h"
+#include "mg_ctx.h"
 
 namespace mg {
 
@@ -54,7 +55,7 @@ int num_sms()
     return sms;
 }
 
-static mg_status cuda_fail(cudaError_t e)
+mg_status cuda_fail(cudaError_t e)
 {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
     return MG_ECUDA;
@@ -99,21 +100,23 @@ cudaError_t launch_add_to_f64(double *u, const T *e, size_t np, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void scale_copy_kernel(const double *__restrict__ b, T *__restrict__ bh, size_t np, double h2)
+template <typename InT, typename T>
+__global__ void scale_copy_kernel(const InT *__restrict__ b, T *__restrict__ bh, size_t np, InT h2)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < np; i += (size_t)gridDim.x * blockDim.x)
-        bh[i] = (T)__dmul_rn(h2, b[i]);
+        bh[i] = (T)rmul(h2, b[i]);  // exact: h2 is a power of two
 }
 
-template <typename T>
-cudaError_t launch_scale_copy(const double *b, T *bh, size_t np, double h2, cudaStream_t s)
+template <typename InT, typename T>
+cudaError_t launch_scale_copy(const InT *b, T *bh, size_t np, double h2, cudaStream_t s)
 {
     const int blocks = (int)std::min<size_t>((np + 255) / 256, (size_t)num_sms() * 8);
-    scale_copy_kernel<T><<<blocks, 256, 0, s>>>(b, bh, np, h2);
+    scale_copy_kernel<InT, T><<<blocks, 256, 0, s>>>(b, bh, np, (InT)h2);
     count_launch(1);
     return cudaGetLastError();
 }
+template cudaError_t launch_scale_copy<double, double>(const double *, double *, size_t, double, cudaStream_t);
+template cudaError_t launch_scale_copy<float, float>(const float *, float *, size_t, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // dispatch on the dimension
@@ -171,38 +174,6 @@ static bool valid_N(int N)
 
 using namespace mg;
 
-// ---------------------------------------------------------------------------
-// context
-// ---------------------------------------------------------------------------
-struct GraphPair {
-    cudaGraphExec_t pre = nullptr, rest = nullptr;
-    unsigned long long pre_nodes = 0, rest_nodes = 0;
-};
-
-struct mg_ctx {
-    int d = 2, N = 0, L = 0, nu1 = 1, nu2 = 1, gamma = 1, lt = 0, dev = 0;
-    mg_prec prec = MG_FP64;
-    double c[3] = {0, 0, 0};
-    int ncoef = 0;
-    cudaStream_t user = nullptr, s = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    // hierarchy in the cycle's precision (double or float); level 0 of an
-    // FP64 context uses the caller's u and (unscaled) b for A and BH
-    std::vector<int> n;
-    std::vector<void *> A, B, BH, RH;
-    size_t esize = 8;
-    double *lu = nullptr;
-    double *partials = nullptr;
-    int npartials = 0;
-    double *d_norm2 = nullptr;
-    double *h_norm2 = nullptr;  // pinned
-    GraphPair g;
-    const void *cap_u = nullptr, *cap_b = nullptr;
-    std::vector<void *> owned;  // device allocations to free
-    // batched contexts
-    std::vector<mg_ctx *> members;
-};
-
 static void free_graphs(mg_ctx *c)
 {
     if (c->g.pre) cudaGraphExecDestroy(c->g.pre);
@@ -215,6 +186,7 @@ static void destroy_ctx(mg_ctx *c)
 {
     if (!c) return;
     for (mg_ctx *m : c->members) destroy_ctx(m);
+    free_adjoint(c);
     free_graphs(c);
     for (void *p : c->owned) cudaFree(p);
     if (c->h_norm2) cudaFreeHost(c->h_norm2);
@@ -314,8 +286,8 @@ struct Recorder {
         if (l >= c->lt) {
             if (l == 0 && b0_unscaled) {
                 // finest level inside the tail: form the scaled rhs first
-                e = launch_scale_copy<T>((const double *)b0, (T *)c->BH[0], npoints(c->d, c->n[0]),
-                                         1.0 / ((double)c->N * c->N), c->s);
+                e = launch_scale_copy<T, T>(b0, (T *)c->BH[0], npoints(c->d, c->n[0]),
+                                            1.0 / ((double)c->N * c->N), c->s);
                 if (e) return e;
             }
             return tail(l, zero_start);
@@ -381,24 +353,21 @@ static mg_status capture(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *no
     return MG_OK;
 }
 
-// Record the pre/rest graphs for caller arrays u (FP64) and b (FP64).
-static mg_status record(mg_ctx *c, void *u, const void *b)
+// Plain cycles in precision T on the caller's arrays (level 0 = caller's u, b).
+template <typename T>
+static mg_status record_plain(mg_ctx *c, void *u, const void *b)
 {
-    if (c->g.pre && c->cap_u == u && c->cap_b == b) return MG_OK;
-    free_graphs(c);
     const int d = c->d, n0 = c->n[0];
-    const size_t np0 = npoints(d, n0);
     mg_status st;
-    if (c->prec == MG_FP64) {
-        Recorder<double> R{c, (const double *)b, true, (double *)u};
+        Recorder<T> R{c, (const T *)b, true, (T *)u};
         const bool fused = c->nu1 >= 1 && c->lt > 0;
         st = capture(c, &c->g.pre, &c->g.pre_nodes, [&]() -> cudaError_t {
             cudaError_t e;
             if (fused)
-                e = op_sweep<double>(d, (const double *)u, (const double *)b, true, (double *)c->B[0], n0, c->c,
+                e = op_sweep<T>(d, (const T *)u, (const T *)b, true, (T *)c->B[0], n0, c->c,
                                      c->partials, c->s);
             else
-                e = op_residual<double, double>(d, (const double *)u, (const double *)b, true, (double *)nullptr,
+                e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr,
                                                 n0, c->partials, c->s);
             if (e) return e;
             const int np = fused ? sweep_partials(d, n0) : residual_partials(d, n0);
@@ -407,6 +376,23 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t { return R.visit(0, false, fused); });
+        if (st != MG_OK) return st;
+    return MG_OK;
+}
+
+// Record the pre/rest graphs for the caller's arrays u and b.
+static mg_status record(mg_ctx *c, void *u, const void *b)
+{
+    if (c->g.pre && c->cap_u == u && c->cap_b == b) return MG_OK;
+    free_graphs(c);
+    const int d = c->d, n0 = c->n[0];
+    const size_t np0 = npoints(d, n0);
+    mg_status st;
+    if (c->prec == MG_FP64) {
+        st = record_plain<double>(c, u, b);
+        if (st != MG_OK) return st;
+    } else if (c->prec == MG_FP32) {
+        st = record_plain<float>(c, u, b);
         if (st != MG_OK) return st;
     } else {
         // refinement: FP64 residual -> FP32 scaled rhs of level 0; FP32 cycle
@@ -466,7 +452,8 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
     if (!out) return MG_EINVAL;
     *out = nullptr;
     if ((d != 2 && d != 3) || !valid_N(N) || !coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 2) ||
-        nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || gamma < 1 || gamma > 2 || (prec != MG_FP64 && prec != MG_FP32_IR))
+        nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || gamma < 1 || gamma > 2 ||
+        (prec != MG_FP64 && prec != MG_FP32_IR && prec != MG_FP32))
         return MG_EINVAL;
     for (int j = 0; j < ncoeffs; ++j)
         if (!std::isfinite(coeffs[j])) return MG_EINVAL;
@@ -519,7 +506,7 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
         c->RH.assign(c->L, nullptr);
         for (int l = 0; l < c->L; ++l) {
             const size_t bytes = npoints(d, c->n[l]) * c->esize;
-            const bool caller_level = l == 0 && prec == MG_FP64;
+            const bool caller_level = l == 0 && prec != MG_FP32_IR;
             if (!caller_level) MG_TRY(dalloc(c, &c->A[l], bytes));
             MG_TRY(dalloc(c, &c->B[l], bytes));
             if (!caller_level || c->lt == 0) MG_TRY(dalloc(c, &c->BH[l], bytes));
@@ -648,14 +635,30 @@ mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycl
     return st != MG_OK ? st : st2;
 }
 
+mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs)
+{
+    if (!ctx || !spai_coeffs || ncoeffs < 1 || ncoeffs > (ctx->d == 2 ? 3 : 2)) return MG_EINVAL;
+    for (int j = 0; j < ncoeffs; ++j)
+        if (!std::isfinite(spai_coeffs[j])) return MG_EINVAL;
+    if (cudaSetDevice(ctx->dev) != cudaSuccess || cudaStreamSynchronize(ctx->s) != cudaSuccess)
+        return cuda_fail(cudaGetLastError());
+    for (int j = 0; j < 3; ++j) ctx->c[j] = j < ncoeffs ? spai_coeffs[j] : 0.0;
+    ctx->ncoef = ncoeffs;
+    free_graphs(ctx);
+    return MG_OK;
+}
+
 mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out)
 {
     if (!ctx || !u || !b || !norm_out || !ctx->members.empty()) return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
     const int n0 = ctx->n[0];
-    cudaError_t e = op_residual<double, double>(ctx->d, (const double *)u, (const double *)b, true,
-                                                (double *)nullptr, n0, ctx->partials, ctx->s);
+    cudaError_t e = ctx->prec == MG_FP32
+                        ? op_residual<float, float>(ctx->d, (const float *)u, (const float *)b, true, (float *)nullptr,
+                                                    n0, ctx->partials, ctx->s)
+                        : op_residual<double, double>(ctx->d, (const double *)u, (const double *)b, true,
+                                                      (double *)nullptr, n0, ctx->partials, ctx->s);
     if (!e) e = launch_sum_partials(ctx->partials, residual_partials(ctx->d, n0), ctx->d_norm2, ctx->s);
     if (!e) e = cudaMemcpyAsync(ctx->h_norm2, ctx->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
     if (!e) e = cudaStreamSynchronize(ctx->s);
