@@ -41,7 +41,7 @@ __device__ __forceinline__ T ld(const T *a, int n, int x, int y, int z)
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
 adj_sweep_stage1(const T *__restrict__ g, const T *__restrict__ u, const T *__restrict__ b, bool unscaled,
-                 T *__restrict__ t, int n, T c0, T c1, T c2, T h2, double *__restrict__ partials)
+                 T *__restrict__ t, int n, T c0, T c1, T c2, int hk, double *__restrict__ partials)
 {
     const size_t np = D == 2 ? (size_t)n * n : (size_t)n * n * n;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -65,7 +65,7 @@ adj_sweep_stage1(const T *__restrict__ g, const T *__restrict__ u, const T *__re
             t[i] = rfma(c1, E, rmul(c0, gp));
         }
         T bb = b[i];
-        if (unscaled) bb = rmul(h2, bb);
+        if (unscaled) bb = scale2(bb, hk);
         const T rh = u ? radd(rfma(T(-2 * D), u[i], bb), s) : bb;
         a0 = fma((double)gp, (double)rh, a0);
         a1 = fma((double)E, (double)rh, a1);
@@ -287,14 +287,14 @@ struct Adjoint {
         const int nn = n(l);
         const size_t np = npts(c->d, nn);
         const int grid = grid_for(np);
-        const T h2 = T(1.0 / ((double)(nn + 1) * (nn + 1)));
+        const int hk = h2_exponent(nn);
         T *G = (T *)w->G[l], *Tt = (T *)w->T[l], *GB = (T *)w->GB[l];
         if (c->d == 2)
             adj_sweep_stage1<T, 2><<<grid, 256, 0, c->s>>>(G, u_in, bh(k, l), l == 0, Tt, nn, T(c->c[0]),
-                                                           T(c->c[1]), T(c->c[2]), h2, w->partials);
+                                                           T(c->c[1]), T(c->c[2]), hk, w->partials);
         else
             adj_sweep_stage1<T, 3><<<grid, 256, 0, c->s>>>(G, u_in, bh(k, l), l == 0, Tt, nn, T(c->c[0]),
-                                                           T(c->c[1]), T(0), h2, w->partials);
+                                                           T(c->c[1]), T(0), hk, w->partials);
         adj_accumulate<<<1, 32, 0, c->s>>>(w->partials, grid, w->acc);
         if (c->d == 2)
             adj_stage2<T, 2><<<grid, 256, 0, c->s>>>(G, Tt, GB, nn);

@@ -36,7 +36,7 @@ namespace mg {
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __global__ void __launch_bounds__(kSweepThreads)
 sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int H,
-               T c0, T c1, T c2, T h2, double *__restrict__ partials)
+               T c0, T c1, T c2, int hk, double *__restrict__ partials)
 {
     __shared__ T su[2][kSweepThreads + 2];
     __shared__ T sr[2][kSweepThreads];
@@ -63,7 +63,7 @@ sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
         T bb = get(b, j, x);
-        if (UNSCALED_B) bb = rmul(h2, bb);
+        if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
         T r;
         if (!ZERO_U) {
             u_next = get(u, j + 1, x);
@@ -111,7 +111,7 @@ sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 template <typename T, bool UNSCALED_B>
 __global__ void __launch_bounds__(kRestrictThreads)
 resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
-                     int Hc, T h2)
+                     int Hc, int hk)
 {
     __shared__ T su[2][2 * kRestrictThreads + 2];
     __shared__ T sr[2][kRestrictThreads + 1];
@@ -141,8 +141,8 @@ resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
         __syncthreads();
         T ba = get(b, f, fx), bb = get(b, f, fx + 1);
         if (UNSCALED_B) {
-            ba = rmul(h2, ba);
-            bb = rmul(h2, bb);
+            ba = scale2(ba, hk);
+            bb = scale2(bb, hk);
         }
         const T sa = radd(radd(su[buf][2 * t], su[buf][2 * t + 2]), radd(ua_prev, ua_next));
         const T sb = radd(radd(su[buf][2 * t + 1], su[buf][2 * t + 3]), radd(ub_prev, ub_next));
@@ -157,7 +157,7 @@ resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
         if (f >= f0 + 2 && (f & 1) == 0 && t < kRestrictCols && ic < nc) {
             const int jc = f / 2 - 1;
             const T v = rfma(T(2), t1, radd(t2, tx));
-            bc[(size_t)jc * nc + ic] = rmul(T(0.25), v);
+            bc[(size_t)jc * nc + ic] = scale2<-2>(v);  // 0.25 v
         }
         t2 = t1;
         t1 = tx;
@@ -190,7 +190,7 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
     };
     auto xpass = [&](int mm, T &odd, T &on) {
         on = ge(mm, k);
-        odd = rmul(T(0.5), radd(ge(mm, k - 1), on));
+        odd = scale2<-1>(radd(ge(mm, k - 1), on));  // 0.5 (a + b)
     };
     T pa, pb;  // x-pass of coarse row m-1: columns 2k, 2k+1
     xpass(m0 - 1, pa, pb);
@@ -201,8 +201,8 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
         xpass(m, ca, cb);
         {   // fine row 2m
             T *row = u + (size_t)(2 * m) * ld;
-            row[fa] = radd(row[fa], rmul(T(0.5), radd(pa, ca)));
-            if (inb) row[fb] = radd(row[fb], rmul(T(0.5), radd(pb, cb)));
+            row[fa] = radd(row[fa], scale2<-1>(radd(pa, ca)));
+            if (inb) row[fb] = radd(row[fb], scale2<-1>(radd(pb, cb)));
         }
         if (m < nc) {  // fine row 2m+1
             T *row = u + (size_t)(2 * m + 1) * ld;
@@ -223,7 +223,7 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kSweepThreads)
 residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
-                  int n, int H, InT h2, bool unscaled, double *__restrict__ partials)
+                  int n, int H, int hk, bool unscaled, double *__restrict__ partials)
 {
     __shared__ InT su[2][kSweepThreads + 2];
     const int t = threadIdx.x;
@@ -247,7 +247,7 @@ residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         if (owner) {
             const InT s = radd(radd(su[buf][t], su[buf][t + 2]), radd(u_prev, u_next));
             InT bb = b[(size_t)j * ld + x];
-            if (unscaled) bb = rmul(h2, bb);
+            if (unscaled) bb = scale2(bb, hk);
             const InT r = radd(rfma(InT(-4), u_cur, bb), s);
             acc = fma((double)r, (double)r, acc);
             if (rh_out) rh_out[(size_t)j * ld + x] = (OutT)r;
@@ -277,10 +277,10 @@ cudaError_t launch_sweep2d(const T *u, const T *b, bool unscaled, T *out, int n,
 {
     const Grid2 g = sweep2d_grid(n);
     const dim3 grid(g.bx, g.by);
-    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]);
 #define MG_SWEEP(ZU, UB, NRM) \
-    sweep2d_kernel<T, ZU, UB, NRM><<<grid, kSweepThreads, 0, s>>>(u, b, out, n, g.H, c0, c1, c2, h2, partials)
+    sweep2d_kernel<T, ZU, UB, NRM><<<grid, kSweepThreads, 0, s>>>(u, b, out, n, g.H, c0, c1, c2, hk, partials)
     const bool z = u == nullptr, nrm = partials != nullptr;
     if (z) {
         if (unscaled) {
@@ -307,11 +307,11 @@ cudaError_t launch_resrestrict2d(const T *u, const T *b, bool unscaled, T *bc, i
     const int bx = (nc + kRestrictCols - 1) / kRestrictCols;
     const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 4, 32);
     const dim3 grid(bx, (nc + Hc - 1) / Hc);
-    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    const int hk = h2_exponent(n);
     if (unscaled)
-        resrestrict2d_kernel<T, true><<<grid, kRestrictThreads, 0, s>>>(u, b, bc, n, Hc, h2);
+        resrestrict2d_kernel<T, true><<<grid, kRestrictThreads, 0, s>>>(u, b, bc, n, Hc, hk);
     else
-        resrestrict2d_kernel<T, false><<<grid, kRestrictThreads, 0, s>>>(u, b, bc, n, Hc, h2);
+        resrestrict2d_kernel<T, false><<<grid, kRestrictThreads, 0, s>>>(u, b, bc, n, Hc, hk);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -333,9 +333,8 @@ cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *r
                               cudaStream_t s)
 {
     const Grid2 g = sweep2d_grid(n);
-    const InT h2 = InT(1.0 / ((double)(n + 1) * (double)(n + 1)));
-    residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads, 0, s>>>(u, b, rh, n, g.H, h2, unscaled,
-                                                                           partials);
+    residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads, 0, s>>>(u, b, rh, n, g.H, h2_exponent(n),
+                                                                           unscaled, partials);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -37,7 +37,7 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __global__ void __launch_bounds__(kS3Threads)
 sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int Z,
-               T c0, T c1, T h2, double *__restrict__ partials)
+               T c0, T c1, int hk, double *__restrict__ partials)
 {
     __shared__ T su[2][kS3U * kS3U];
     __shared__ T sr[3][kS3 * kS3];  // three planes: the output reads the previous one
@@ -90,7 +90,7 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
         for (int k = 0; k < kS3Pts; ++k) {
             const int i = px[k] - ex0, j = py[k] - ey0;
             T bb = get3(b, n, px[k], py[k], zz);
-            if (UNSCALED_B) bb = rmul(h2, bb);
+            if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
             T r;
             if (!ZERO_U) {
                 const T *row = &su[buf][(j + 1) * kS3U + (i + 1)];
@@ -150,7 +150,7 @@ constexpr int kR3Threads = kR3 * kR3;
 template <typename T, bool UNSCALED_B>
 __global__ void __launch_bounds__(kR3Threads)
 resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n, int Zc,
-                     T h2)
+                     int hk)
 {
     __shared__ T su[3][kR3U * kR3U];
     __shared__ T sr[kR3F * kR3F];
@@ -185,7 +185,7 @@ resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
             T r = T(0);
             if (x < n && y < n && f < n) {
                 T bb = b[(size_t)f * plane + (size_t)y * n + x];
-                if (UNSCALED_B) bb = rmul(h2, bb);
+                if (UNSCALED_B) bb = scale2(bb, hk);
                 const T s = radd(radd(radd(uc[p - 1], uc[p + 1]), radd(uc[p - kR3U], uc[p + kR3U])),
                                  radd(um[p], up[p]));
                 r = radd(rfma(T(-6), uc[p], bb), s);
@@ -203,7 +203,7 @@ resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
         if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
             const int kc = f / 2 - 1;
             const T v = rfma(T(2), t2b, radd(t2a, t2));
-            bc[((size_t)kc * nc + jc) * nc + ic] = rmul(T(0.0625), v);
+            bc[((size_t)kc * nc + jc) * nc + ic] = scale2<-4>(v);  // 0.0625 v
         }
         t2a = t2b;
         t2b = t2;
@@ -225,7 +225,7 @@ __device__ __forceinline__ T p3_interp_x(const T *e, int nc, int fx, int jc, int
 {
     if (fx & 1) return get3(e, nc, fx >> 1, jc, kc);
     const int k = fx >> 1;
-    return rmul(T(0.5), radd(get3(e, nc, k - 1, jc, kc), get3(e, nc, k, jc, kc)));
+    return scale2<-1>(radd(get3(e, nc, k - 1, jc, kc), get3(e, nc, k, jc, kc)));
 }
 
 template <typename T>
@@ -233,7 +233,7 @@ __device__ __forceinline__ T p3_interp_xy(const T *e, int nc, int fx, int fy, in
 {
     if (fy & 1) return p3_interp_x(e, nc, fx, fy >> 1, kc);
     const int m = fy >> 1;
-    return rmul(T(0.5), radd(p3_interp_x(e, nc, fx, m - 1, kc), p3_interp_x(e, nc, fx, m, kc)));
+    return scale2<-1>(radd(p3_interp_x(e, nc, fx, m - 1, kc), p3_interp_x(e, nc, fx, m, kc)));
 }
 
 template <typename T>
@@ -251,7 +251,7 @@ prolong3d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Zc)
         const T cur = p3_interp_xy(e, nc, fx, fy, m);
         {
             T *p = u + (size_t)(2 * m) * plane + (size_t)fy * n + fx;
-            *p = radd(*p, rmul(T(0.5), radd(prev, cur)));
+            *p = radd(*p, scale2<-1>(radd(prev, cur)));
         }
         if (m < nc) {
             T *p = u + (size_t)(2 * m + 1) * plane + (size_t)fy * n + fx;
@@ -269,7 +269,7 @@ prolong3d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Zc)
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kP3X * kP3Y)
 residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out, int n,
-                  int Z, InT h2, bool unscaled, double *__restrict__ partials)
+                  int Z, int hk, bool unscaled, double *__restrict__ partials)
 {
     const int x = blockIdx.x * kP3X + threadIdx.x % kP3X;
     const int y = blockIdx.y * kP3Y + threadIdx.x / kP3X;
@@ -286,7 +286,7 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
                                radd(u_prev, u_next));
             const size_t p = (size_t)z * plane + (size_t)y * n + x;
             InT bb = b[p];
-            if (unscaled) bb = rmul(h2, bb);
+            if (unscaled) bb = scale2(bb, hk);
             const InT r = radd(rfma(InT(-6), u_cur, bb), s);
             acc = fma((double)r, (double)r, acc);
             if (rh_out) rh_out[p] = (OutT)r;
@@ -326,10 +326,10 @@ cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n,
 {
     const Grid3 g = sweep3d_grid(n);
     const dim3 grid(g.bx, g.by, g.bz);
-    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]);
 #define MG_SWEEP(ZU, UB, NRM) \
-    sweep3d_kernel<T, ZU, UB, NRM><<<grid, kS3Threads, 0, s>>>(u, b, out, n, g.Z, c0, c1, h2, partials)
+    sweep3d_kernel<T, ZU, UB, NRM><<<grid, kS3Threads, 0, s>>>(u, b, out, n, g.Z, c0, c1, hk, partials)
     const bool z = u == nullptr, nrm = partials != nullptr;
     if (z) {
         if (unscaled) {
@@ -356,11 +356,11 @@ cudaError_t launch_resrestrict3d(const T *u, const T *b, bool unscaled, T *bc, i
     const int bxy = (nc + kR3 - 1) / kR3;
     const int Zc = chunk_rows(bxy * bxy, nc, 8 * num_sms(), 2, 32);
     const dim3 grid(bxy, bxy, (nc + Zc - 1) / Zc);
-    const T h2 = T(1.0 / ((double)(n + 1) * (double)(n + 1)));
+    const int hk = h2_exponent(n);
     if (unscaled)
-        resrestrict3d_kernel<T, true><<<grid, kR3Threads, 0, s>>>(u, b, bc, n, Zc, h2);
+        resrestrict3d_kernel<T, true><<<grid, kR3Threads, 0, s>>>(u, b, bc, n, Zc, hk);
     else
-        resrestrict3d_kernel<T, false><<<grid, kR3Threads, 0, s>>>(u, b, bc, n, Zc, h2);
+        resrestrict3d_kernel<T, false><<<grid, kR3Threads, 0, s>>>(u, b, bc, n, Zc, hk);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -382,9 +382,8 @@ cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *r
                               cudaStream_t s)
 {
     const Grid3 g = residual3d_grid(n);
-    const InT h2 = InT(1.0 / ((double)(n + 1) * (double)(n + 1)));
-    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kP3X * kP3Y, 0, s>>>(u, b, rh, n, g.Z, h2, unscaled,
-                                                                               partials);
+    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kP3X * kP3Y, 0, s>>>(u, b, rh, n, g.Z, h2_exponent(n),
+                                                                               unscaled, partials);
     count_launch(1);
     return cudaGetLastError();
 }

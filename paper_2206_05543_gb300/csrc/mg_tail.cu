@@ -75,7 +75,7 @@ __device__ T restrict_at(int d, const T *rh, int n, int ic, int jc, int kc)
     if (d == 2) {
         const T t0 = fw_x(rh, n, ic, 2 * jc, 0), t1 = fw_x(rh, n, ic, 2 * jc + 1, 0),
                 t2 = fw_x(rh, n, ic, 2 * jc + 2, 0);
-        return rmul(T(0.25), rfma(T(2), t1, radd(t0, t2)));
+        return scale2<-2>(rfma(T(2), t1, radd(t0, t2)));  // 0.25 v
     }
     T tz[3];
     for (int k = 0; k < 3; ++k) {
@@ -84,7 +84,7 @@ __device__ T restrict_at(int d, const T *rh, int n, int ic, int jc, int kc)
                 t2 = fw_x(rh, n, ic, 2 * jc + 2, fz);
         tz[k] = rfma(T(2), t1, radd(t0, t2));
     }
-    return rmul(T(0.0625), rfma(T(2), tz[1], radd(tz[0], tz[2])));
+    return scale2<-4>(rfma(T(2), tz[1], radd(tz[0], tz[2])));  // 0.0625 v
 }
 
 // linear interpolation of the coarse array e (nc points per axis) at fine
@@ -95,7 +95,7 @@ __device__ T interp_x(const T *e, int nc, int fx, int jc, int kc)
     // fine 0-based fx = 2k+1 sits on coarse k; fx = 2k lies between k-1 and k
     if (fx & 1) return at(e, nc, fx >> 1, jc, kc);
     const int k = fx >> 1;
-    return rmul(T(0.5), radd(at(e, nc, k - 1, jc, kc), at(e, nc, k, jc, kc)));
+    return scale2<-1>(radd(at(e, nc, k - 1, jc, kc), at(e, nc, k, jc, kc)));
 }
 
 template <typename T>
@@ -103,7 +103,7 @@ __device__ T interp_xy(const T *e, int nc, int fx, int fy, int kc)
 {
     if (fy & 1) return interp_x(e, nc, fx, fy >> 1, kc);
     const int m = fy >> 1;
-    return rmul(T(0.5), radd(interp_x(e, nc, fx, m - 1, kc), interp_x(e, nc, fx, m, kc)));
+    return scale2<-1>(radd(interp_x(e, nc, fx, m - 1, kc), interp_x(e, nc, fx, m, kc)));
 }
 
 template <typename T>
@@ -112,7 +112,7 @@ __device__ T interp_at(int d, const T *e, int nc, int fx, int fy, int fz)
     if (d == 2) return interp_xy(e, nc, fx, fy, 0);
     if (fz & 1) return interp_xy(e, nc, fx, fy, fz >> 1);
     const int q = fz >> 1;
-    return rmul(T(0.5), radd(interp_xy(e, nc, fx, fy, q - 1), interp_xy(e, nc, fx, fy, q)));
+    return scale2<-1>(radd(interp_xy(e, nc, fx, fy, q - 1), interp_xy(e, nc, fx, fy, q)));
 }
 
 template <typename T>
