@@ -106,6 +106,32 @@ void mg_destroy(mg_ctx *ctx);
 mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs);
 
 /* ---------------------------------------------------------------------- */
+/* batched solves (many right-hand sides, uneven grid sizes)              */
+/* ---------------------------------------------------------------------- */
+
+/* A context for `count` independent 2D problems with grid sizes Ns[0..count-1]
+ * (HOST array; each a power of two, 4 <= N <= 32768), solved by FP32 V(nu1,nu2)
+ * cycles inside FP64 iterative refinement (prec must be MG_FP32_IR; d must
+ * be 2; 1 <= nu1 <= 4, 0 <= nu2 <= 4). The cycles of all problems are aligned
+ * by grid size (Sec. 4 cycle): one launch per operator and size serves every
+ * problem that has a level of that size; the levels with at most 15 points
+ * per axis run in one block per problem. The row-chunk height of each launch
+ * is chosen by timing at setup (cached per device and size; persisted when
+ * the environment variable MG_AUTOTUNE_CACHE names a file). */
+mg_status mg_setup_batched(int d, int count, const int *Ns, const double *spai_coeffs, int ncoeffs,
+                           int nu1, int nu2, mg_prec prec, void *cuda_stream, mg_ctx **out);
+
+/* Solve every problem i to ||b_i - A u_i||_2 <= tol ||b_i - A u_i^0||_2:
+ * b[i], u[i] are device FP64 arrays ((Ns[i]-1)^2, u[i] holds the initial
+ * guess), passed as HOST arrays of device pointers. A problem that has
+ * converged is masked out of later iterations. cycles_out, relres_out:
+ * nullable HOST arrays of count entries. MG_OK when all converged,
+ * MG_ENOCONV if some ran out of max_cycles, MG_ENAN if some norm became
+ * NaN/Inf. Synchronises once per refinement iteration. */
+mg_status mg_solve_batched(mg_ctx *ctx, const void *const *b, void *const *u, double tol, int max_cycles,
+                           int *cycles_out, double *relres_out);
+
+/* ---------------------------------------------------------------------- */
 /* adjoint of K cycles                                                    */
 /* ---------------------------------------------------------------------- */
 

@@ -41,6 +41,8 @@ SIGNATURES = {
     "mg_op_coarse_solve": (_I, [_I, _I, _P, _P, _P]),
     "mg_op_sweep_norm_noalloc": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _P, _P]),
     "mg_set_coeffs": (_I, [_P, _DP, _I]),
+    "mg_setup_batched": (_I, [_I, _I, _IP, _DP, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
+    "mg_solve_batched": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _IP, _DP]),
     "mg_vcycles_adjoint": (_I, [_P, _I, _P, _P, _P, _DP]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_cuda_error": (ctypes.c_char_p, []),
@@ -230,6 +232,61 @@ class Solver:
         out = ctypes.c_double(0.0)
         _check(lib().mg_residual_norm(self._ctx, pu, pb, ctypes.byref(out)), "mg_residual_norm")
         return out.value
+
+
+class BatchedSolver:
+    """Many independent 2D problems of uneven sizes, FP32 V(nu1, nu2) cycles
+    inside FP64 refinement, one launch per operator and grid size across the
+    batch (mg_setup_batched / mg_solve_batched)."""
+
+    def __init__(self, Ns, coeffs=None, nu1: int = 1, nu2: int = 1, stream=None):
+        torch = _torch()
+        self.Ns = [int(N) for N in Ns]
+        self.count = len(self.Ns)
+        self.coeffs = tuple(coeffs if coeffs is not None else smoothers.default(2))
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        arr, nc = _coeff_array(self.coeffs)
+        ns = (ctypes.c_int * self.count)(*self.Ns)
+        ctx = ctypes.c_void_p()
+        _check(lib().mg_setup_batched(2, self.count, ns, arr, nc, int(nu1), int(nu2), MG_FP32_IR,
+                                      ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(ctx)),
+               "mg_setup_batched")
+        self._ctx = ctx
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().mg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, bs, us=None, tol: float = 1e-10, max_cycles: int = 100):
+        """Returns (us, status, cycles per problem, relres per problem)."""
+        torch = _torch()
+        if len(bs) != self.count:
+            raise ValueError(f"expected {self.count} right-hand sides")
+        if us is None:
+            us = [torch.zeros_like(b) for b in bs]
+        pb = (ctypes.c_void_p * self.count)()
+        pu = (ctypes.c_void_p * self.count)()
+        for i, (b, u, N) in enumerate(zip(bs, us, self.Ns)):
+            pb[i] = _dev_ptr(b, torch.float64, (N - 1, N - 1), f"b[{i}]").value
+            pu[i] = _dev_ptr(u, torch.float64, (N - 1, N - 1), f"u[{i}]").value
+        cyc = (ctypes.c_int * self.count)()
+        rel = (ctypes.c_double * self.count)()
+        st = lib().mg_solve_batched(self._ctx, pb, pu, float(tol), int(max_cycles), cyc, rel)
+        _check(st, "mg_solve_batched", ok=(MG_OK, MG_ENOCONV, MG_ENAN))
+        return us, st, list(cyc), list(rel)
 
 
 # ---------------------------------------------------------------------------

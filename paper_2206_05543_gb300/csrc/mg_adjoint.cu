@@ -431,7 +431,7 @@ static mg_status run_adjoint(mg_ctx *c, int K, const T *b, const T *g_uK, T *g_b
 extern "C" mg_status mg_vcycles_adjoint(mg_ctx *ctx, int K, const void *b, const void *grad_uK, void *grad_b_out,
                                         double *grad_coeffs_out)
 {
-    if (!ctx || K < 1 || !b || !grad_uK || !grad_b_out || !grad_coeffs_out || !ctx->members.empty() ||
+    if (!ctx || K < 1 || !b || !grad_uK || !grad_b_out || !grad_coeffs_out || ctx->batch ||
         ctx->gamma != 1 || ctx->nu1 < 1 || ctx->prec == MG_FP32_IR || ctx->L < 2)
         return MG_EINVAL;
     if (cudaSetDevice(ctx->dev) != cudaSuccess) return cuda_fail(cudaGetLastError());

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <vector>
 
 #include "../../include/mg.h"
@@ -19,6 +20,8 @@ struct AdjointWork {
     double *acc = nullptr;                               // 3 coefficient gradients (device)
     std::vector<void *> owned;
 };
+
+struct BatchWork;  // mg_batched.cu
 
 struct GraphPair {
     cudaGraphExec_t pre = nullptr, rest = nullptr;
@@ -45,13 +48,17 @@ struct mg_ctx {
     GraphPair g;
     const void *cap_u = nullptr, *cap_b = nullptr;
     std::vector<void *> owned;  // device allocations to free
-    // batched contexts
-    std::vector<mg_ctx *> members;
     AdjointWork *adj = nullptr;
+    BatchWork *batch = nullptr;  // set for batched contexts
 };
 
 
 namespace mg {
 mg_status cuda_fail(cudaError_t e);
 void free_adjoint(mg_ctx *c);
+void free_batch(mg_ctx *c);
+// Record the work issued by body() on the context's stream into a CUDA graph;
+// *nodes receives the number of kernels it launches per replay.
+mg_status capture_graph(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nodes,
+                        const std::function<cudaError_t()> &body);
 }  // namespace mg

@@ -170,6 +170,28 @@ static bool valid_N(int N)
     return (N & (N - 1)) == 0;
 }
 
+mg_status capture_graph(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nodes,
+                        const std::function<cudaError_t()> &body)
+{
+    cudaGraph_t graph = nullptr;
+    unsigned long long counter = 0;
+    cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_capture_counter = &counter;
+    e = body();
+    g_capture_counter = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *nodes = counter;
+    return MG_OK;
+}
+
 }  // namespace mg
 
 using namespace mg;
@@ -185,7 +207,7 @@ static void free_graphs(mg_ctx *c)
 static void destroy_ctx(mg_ctx *c)
 {
     if (!c) return;
-    for (mg_ctx *m : c->members) destroy_ctx(m);
+    free_batch(c);
     free_adjoint(c);
     free_graphs(c);
     for (void *p : c->owned) cudaFree(p);
@@ -335,22 +357,7 @@ struct Recorder {
 template <typename F>
 static mg_status capture(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nodes, F &&body)
 {
-    cudaGraph_t graph = nullptr;
-    unsigned long long counter = 0;
-    MG_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-    g_capture_counter = &counter;
-    cudaError_t e = body();
-    g_capture_counter = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(c->s, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(e != cudaSuccess ? e : e2);
-    }
-    e = cudaGraphInstantiate(out, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e);
-    *nodes = counter;
-    return MG_OK;
+    return mg::capture_graph(c, out, nodes, std::function<cudaError_t()>(body));
 }
 
 // Plain cycles in precision T on the caller's arrays (level 0 = caller's u, b).
@@ -593,7 +600,7 @@ void mg_destroy(mg_ctx *ctx)
 
 mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b)
 {
-    if (!ctx || !u || !b || !ctx->members.empty()) return MG_EINVAL;
+    if (!ctx || !u || !b || ctx->batch) return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
     if ((st = record(ctx, u, b)) != MG_OK) return st;
@@ -605,7 +612,7 @@ mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b)
 mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
                    double *relres_out, double *hist_out)
 {
-    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || !ctx->members.empty()) return MG_EINVAL;
+    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch) return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
     if ((st = record(ctx, u, b)) != MG_OK) return st;
@@ -650,7 +657,7 @@ mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs)
 
 mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out)
 {
-    if (!ctx || !u || !b || !norm_out || !ctx->members.empty()) return MG_EINVAL;
+    if (!ctx || !u || !b || !norm_out || ctx->batch) return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
     const int n0 = ctx->n[0];

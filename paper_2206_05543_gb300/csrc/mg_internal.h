@@ -64,6 +64,34 @@ template <typename InT, typename OutT>
 cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
                               cudaStream_t s);
 
+// ---- batched 2D operators (one launch per grid size across problems) -------
+template <typename T>
+struct BItem {  // one problem's level in a batched launch
+    const T *u;   // input (sweep), residual input (restrict), coarse e (interpolation)
+    const T *b;   // scaled right-hand side of the level
+    T *out;       // sweep output, coarse rhs (restrict), fine u corrected in place (interpolation)
+    int problem;  // index into the active flags
+    int flags;    // bit 0: b is the unscaled caller array
+};
+template <typename OutT>
+struct BRes {  // FP64 residual of one problem's caller arrays
+    const double *u, *b;
+    OutT *out;
+    double *partials;  // residual2d_batched_tiles(n) partial sums
+    int problem, pad;
+};
+template <typename T>
+cudaError_t launch_sweep2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int H, bool zero_u,
+                                   const double *c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_resrestrict2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc,
+                                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc, cudaStream_t s);
+template <typename OutT>
+cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s);
+int residual2d_batched_tiles(int n);
+
 // ---- coarse tail (one block runs the last levels of a cycle) --------------
 constexpr int kTailThreads = 256;
 constexpr int kMaxTailLevels = 8;
@@ -85,6 +113,10 @@ struct TailArgs {
 };
 template <typename T>
 cudaError_t launch_tail(const TailArgs &a, cudaStream_t s);
+// lv: count x kMaxTailLevels levels; problem p runs ops[op_off[p] .. + op_cnt[p]]
+template <typename T>
+cudaError_t launch_tail_batched(const TailLevel *lv, const TailOp *ops, const int *op_off, const int *op_cnt,
+                                const int *active, int count, int d, const double *c, const double *lu, cudaStream_t s);
 void coarse_lu(int d, double *lu);
 
 // ---- small helpers (mg_host.cu) -------------------------------------------

@@ -34,15 +34,15 @@ namespace mg {
 // NORM: accumulate the squared residual of the input over owned points.
 // ---------------------------------------------------------------------------
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__global__ void __launch_bounds__(kSweepThreads)
-sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int H,
-               T c0, T c1, T c2, int hk, double *__restrict__ partials)
+__device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out,
+                                             int n, int H, T c0, T c1, T c2, int hk, int tbx, int tby,
+                                             double *__restrict__ partial)
 {
     __shared__ T su[2][kSweepThreads + 2];
     __shared__ T sr[2][kSweepThreads];
     const int t = threadIdx.x;
-    const int x = blockIdx.x * kSweepCols - 1 + t;
-    const int y0 = blockIdx.y * H;
+    const int x = tbx * kSweepCols - 1 + t;
+    const int y0 = tby * H;
     const int y1 = min(y0 + H, n);
     const bool xin = x >= 0 && x < n;
     const bool owner = t >= 1 && t <= kSweepCols && xin;
@@ -96,7 +96,16 @@ sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
             u_cur = u_next;
         }
     }
-    if (NORM) block_sum_store<kSweepThreads>(acc, &partials[blockIdx.y * gridDim.x + blockIdx.x]);
+    if (NORM) block_sum_store<kSweepThreads>(acc, partial);
+}
+
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+__global__ void __launch_bounds__(kSweepThreads)
+sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int H,
+               T c0, T c1, T c2, int hk, double *__restrict__ partials)
+{
+    sweep2d_tile<T, ZERO_U, UNSCALED_B, NORM>(u, b, out, n, H, c0, c1, c2, hk, blockIdx.x, blockIdx.y,
+                                              NORM ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -109,17 +118,16 @@ sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 // columns 2ic, 2ic+1 with ic = 255*bx + t; threads 0..254 write.
 // ---------------------------------------------------------------------------
 template <typename T, bool UNSCALED_B>
-__global__ void __launch_bounds__(kRestrictThreads)
-resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
-                     int Hc, int hk)
+__device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, const T *__restrict__ b,
+                                                   T *__restrict__ bc, int n, int Hc, int hk, int tbx, int tby)
 {
     __shared__ T su[2][2 * kRestrictThreads + 2];
     __shared__ T sr[2][kRestrictThreads + 1];
     const int nc = (n - 1) / 2;
     const int t = threadIdx.x;
-    const int ic = blockIdx.x * kRestrictCols + t;
+    const int ic = tbx * kRestrictCols + t;
     const int fx = 2 * ic;  // this thread's fine columns: fx, fx + 1
-    const int jc0 = blockIdx.y * Hc;
+    const int jc0 = tby * Hc;
     const int jc1 = min(jc0 + Hc, nc);
     const size_t ld = (size_t)n;
     auto get = [&](const T *a, int yy, int xx) -> T {
@@ -168,6 +176,14 @@ resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
     }
 }
 
+template <typename T, bool UNSCALED_B>
+__global__ void __launch_bounds__(kRestrictThreads)
+resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
+                     int Hc, int hk)
+{
+    resrestrict2d_tile<T, UNSCALED_B>(u, b, bc, n, Hc, hk, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Bilinear interpolation + correction u += P e. Thread k owns fine columns
 // 2k (between coarse k-1 and k) and 2k+1 (on coarse k); per coarse row m:
@@ -176,13 +192,13 @@ resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
 //   u = u + value            (e is zero outside the coarse interior)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kProlongThreads)
-prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
+__device__ __forceinline__ void prolong2d_tile(const T *__restrict__ e, T *__restrict__ u, int n, int Hc, int tbx,
+                                               int tby)
 {
     const int nc = (n - 1) / 2;
-    const int k = blockIdx.x * kProlongThreads + threadIdx.x;
+    const int k = tbx * kProlongThreads + threadIdx.x;
     if (k > nc) return;
-    const int m0 = blockIdx.y * Hc;
+    const int m0 = tby * Hc;
     const int m1 = min(m0 + Hc, nc + 1);
     const size_t ldc = (size_t)nc, ld = (size_t)n;
     auto ge = [&](int mm, int kk) -> T {
@@ -214,6 +230,13 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kProlongThreads)
+prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
+{
+    prolong2d_tile<T>(e, u, n, Hc, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 residual for iterative refinement: rh = fma(-4, u, h^2 b) + s exactly
 // as in the sweep, written as OutT (the cycle's precision) together with one
@@ -221,14 +244,14 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
 // 0 and 255 only supply the u halo).
 // ---------------------------------------------------------------------------
 template <typename InT, typename OutT>
-__global__ void __launch_bounds__(kSweepThreads)
-residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
-                  int n, int H, int hk, bool unscaled, double *__restrict__ partials)
+__device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const InT *__restrict__ b,
+                                                OutT *__restrict__ rh_out, int n, int H, int hk, bool unscaled,
+                                                int tbx, int tby, double *__restrict__ partial)
 {
     __shared__ InT su[2][kSweepThreads + 2];
     const int t = threadIdx.x;
-    const int x = blockIdx.x * kSweepCols - 1 + t;
-    const int y0 = blockIdx.y * H;
+    const int x = tbx * kSweepCols - 1 + t;
+    const int y0 = tby * H;
     const int y1 = min(y0 + H, n);
     const bool owner = t >= 1 && t <= kSweepCols && x < n;
     const size_t ld = (size_t)n;
@@ -255,7 +278,91 @@ residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         u_prev = u_cur;
         u_cur = u_next;
     }
-    if (partials) block_sum_store<kSweepThreads>(acc, &partials[blockIdx.y * gridDim.x + blockIdx.x]);
+    if (partial) block_sum_store<kSweepThreads>(acc, partial);
+}
+
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(kSweepThreads)
+residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
+                  int n, int H, int hk, bool unscaled, double *__restrict__ partials)
+{
+    residual2d_tile<InT, OutT>(u, b, rh_out, n, H, hk, unscaled, blockIdx.x, blockIdx.y,
+                               partials ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch covers the same-size level of many problems.
+// The launch is persistent: gridDim.x blocks loop over (problem, tile) items;
+// items of problems whose flag in `active` is 0 are skipped (a converged
+// problem costs nothing). All problems in one launch share n, so the item ->
+// (problem, tile) map is a division.
+// ---------------------------------------------------------------------------
+template <typename T, bool ZERO_U>
+__global__ void __launch_bounds__(kSweepThreads)
+sweep2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int H,
+                int bx, int by, T c0, T c1, T c2, int hk)
+{
+    const int per = bx * by, total = nprob * per;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int j = it / per, r = it - j * per;
+        const BItem<T> e = tab[j];
+        if (active[e.problem]) {
+            if (e.flags & 1)
+                sweep2d_tile<T, ZERO_U, true, false>(e.u, e.b, e.out, n, H, c0, c1, c2, hk, r % bx, r / bx, nullptr);
+            else
+                sweep2d_tile<T, ZERO_U, false, false>(e.u, e.b, e.out, n, H, c0, c1, c2, hk, r % bx, r / bx, nullptr);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRestrictThreads)
+resrestrict2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int Hc,
+                      int bx, int by, int hk)
+{
+    const int per = bx * by, total = nprob * per;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int j = it / per, r = it - j * per;
+        const BItem<T> e = tab[j];
+        if (active[e.problem]) {
+            if (e.flags & 1)
+                resrestrict2d_tile<T, true>(e.u, e.b, e.out, n, Hc, hk, r % bx, r / bx);
+            else
+                resrestrict2d_tile<T, false>(e.u, e.b, e.out, n, Hc, hk, r % bx, r / bx);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kProlongThreads)
+prolong2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int Hc, int bx,
+                  int by)
+{
+    const int per = bx * by, total = nprob * per;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int j = it / per, r = it - j * per;
+        const BItem<T> e = tab[j];
+        if (active[e.problem]) prolong2d_tile<T>(e.u, e.out, n, Hc, r % bx, r / bx);  // u: coarse e, out: fine u
+    }
+}
+
+// FP64 residual of the caller's arrays, written as OutT, with one partial sum
+// per tile at the item's partial offset.
+template <typename OutT>
+__global__ void __launch_bounds__(kSweepThreads)
+residual2d_batched(const BRes<OutT> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int H,
+                   int bx, int by, int hk)
+{
+    const int per = bx * by, total = nprob * per;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int j = it / per, r = it - j * per;
+        const BRes<OutT> e = tab[j];
+        if (active[e.problem])
+            residual2d_tile<double, OutT>(e.u, e.b, e.out, n, H, hk, true, r % bx, r / bx, e.partials + r);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -344,6 +451,89 @@ template cudaError_t launch_residual2d<double, float>(const double *, const doub
                                                       double *, cudaStream_t);
 template cudaError_t launch_residual2d<float, float>(const float *, const float *, bool, float *, int,
                                                      double *, cudaStream_t);
+
+
+// ---- batched launchers ------------------------------------------------------
+static int persistent_grid(const void *fn, int threads, long items)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return (int)std::max<long>(1, std::min<long>(items, (long)per_sm * num_sms()));
+}
+
+template <typename T>
+cudaError_t launch_sweep2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int H, bool zero_u,
+                                   const double *c, cudaStream_t s)
+{
+    const int bx = (n + kSweepCols - 1) / kSweepCols, by = (n + H - 1) / H;
+    const long items = (long)nprob * bx * by;
+    const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]);
+    const int hk = h2_exponent(n);
+    if (zero_u) {
+        const int g = persistent_grid((const void *)sweep2d_batched<T, true>, kSweepThreads, items);
+        sweep2d_batched<T, true><<<g, kSweepThreads, 0, s>>>(tab, nprob, active, n, H, bx, by, c0, c1, c2, hk);
+    } else {
+        const int g = persistent_grid((const void *)sweep2d_batched<T, false>, kSweepThreads, items);
+        sweep2d_batched<T, false><<<g, kSweepThreads, 0, s>>>(tab, nprob, active, n, H, bx, by, c0, c1, c2, hk);
+    }
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_resrestrict2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc,
+                                         cudaStream_t s)
+{
+    const int nc = (n - 1) / 2;
+    const int bx = (nc + kRestrictCols - 1) / kRestrictCols, by = (nc + Hc - 1) / Hc;
+    const long items = (long)nprob * bx * by;
+    const int g = persistent_grid((const void *)resrestrict2d_batched<T>, kRestrictThreads, items);
+    resrestrict2d_batched<T><<<g, kRestrictThreads, 0, s>>>(tab, nprob, active, n, Hc, bx, by, h2_exponent(n));
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc, cudaStream_t s)
+{
+    const int nc = (n - 1) / 2;
+    const int bx = (nc + 1 + kProlongThreads - 1) / kProlongThreads, by = (nc + 1 + Hc - 1) / Hc;
+    const long items = (long)nprob * bx * by;
+    const int g = persistent_grid((const void *)prolong2d_batched<T>, kProlongThreads, items);
+    prolong2d_batched<T><<<g, kProlongThreads, 0, s>>>(tab, nprob, active, n, Hc, bx, by);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+int residual2d_batched_tiles(int n)
+{
+    const Grid2 g = sweep2d_grid(n);
+    return g.bx * g.by;
+}
+
+template <typename OutT>
+cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s)
+{
+    const Grid2 g = sweep2d_grid(n);
+    const long items = (long)nprob * g.bx * g.by;
+    const int grid = persistent_grid((const void *)residual2d_batched<OutT>, kSweepThreads, items);
+    residual2d_batched<OutT><<<grid, kSweepThreads, 0, s>>>(tab, nprob, active, n, g.H, g.bx, g.by, h2_exponent(n));
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep2d_batched<float>(const BItem<float> *, int, const int *, int, int, bool,
+                                                   const double *, cudaStream_t);
+template cudaError_t launch_sweep2d_batched<double>(const BItem<double> *, int, const int *, int, int, bool,
+                                                    const double *, cudaStream_t);
+template cudaError_t launch_resrestrict2d_batched<float>(const BItem<float> *, int, const int *, int, int,
+                                                         cudaStream_t);
+template cudaError_t launch_resrestrict2d_batched<double>(const BItem<double> *, int, const int *, int, int,
+                                                          cudaStream_t);
+template cudaError_t launch_prolong2d_batched<float>(const BItem<float> *, int, const int *, int, int, cudaStream_t);
+template cudaError_t launch_prolong2d_batched<double>(const BItem<double> *, int, const int *, int, int, cudaStream_t);
+template cudaError_t launch_residual2d_batched<float>(const BRes<float> *, int, const int *, int, cudaStream_t);
+template cudaError_t launch_residual2d_batched<double>(const BRes<double> *, int, const int *, int, cudaStream_t);
 
 #define MG_INST(T)                                                                                   \
     template cudaError_t launch_sweep2d<T>(const T *, const T *, bool, T *, int, const double *,     \

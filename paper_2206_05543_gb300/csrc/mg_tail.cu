@@ -132,13 +132,12 @@ __device__ void coarse_substitution(int d, const double *lu, const T *bh, T *x)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
+__device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d, T c0, T c1, T c2,
+                         const double *lu)
 {
-    const int d = a.d;
-    const T c0 = T(a.c[0]), c1 = T(a.c[1]), c2 = T(a.c[2]);
-    for (int o = 0; o < a.nops; ++o) {
-        const int kind = a.ops[o].kind, l = a.ops[o].level;
-        const TailLevel &L = a.lv[l];
+    for (int o = 0; o < nops; ++o) {
+        const int kind = ops[o].kind, l = ops[o].level;
+        const TailLevel &L = lv[l];
         const int n = L.n;
         const int np = d == 2 ? n * n : n * n * n;
         T *u = (T *)L.u, *tmp = (T *)L.tmp, *bh = (T *)L.bh, *rh = (T *)L.rh;
@@ -165,7 +164,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
                 __syncthreads();
                 for (int i = threadIdx.x; i < np; i += blockDim.x) u[i] = tmp[i];
             } else {
-                const TailLevel &C = a.lv[l + 1];
+                const TailLevel &C = lv[l + 1];
                 const int nc = C.n, npc = d == 2 ? nc * nc : nc * nc * nc;
                 T *bc = (T *)C.bh;
                 for (int i = threadIdx.x; i < npc; i += blockDim.x) {
@@ -175,9 +174,9 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
                 }
             }
         } else if (kind == TAIL_SOLVE) {
-            if (threadIdx.x == 0) coarse_substitution<T>(d, a.lu, bh, u);
+            if (threadIdx.x == 0) coarse_substitution<T>(d, lu, bh, u);
         } else if (kind == TAIL_PROLONG) {
-            const TailLevel &C = a.lv[l + 1];
+            const TailLevel &C = lv[l + 1];
             const T *e = (const T *)C.u;
             for (int i = threadIdx.x; i < np; i += blockDim.x) {
                 int x, y, z;
@@ -188,6 +187,37 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
         __syncthreads();
     }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
+{
+    run_tail<T>(a.lv, a.ops, a.nops, a.d, T(a.c[0]), T(a.c[1]), T(a.c[2]), a.lu);
+}
+
+// one block per problem: the tail of problem blockIdx.x (skipped when inactive)
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads)
+tail_batched(const TailLevel *__restrict__ lv, const TailOp *__restrict__ ops, const int *__restrict__ op_off,
+             const int *__restrict__ op_cnt, const int *__restrict__ active, int d, double c0, double c1, double c2,
+             const double *__restrict__ lu)
+{
+    const int p = blockIdx.x;
+    if (!active[p]) return;
+    run_tail<T>(lv + (size_t)p * kMaxTailLevels, ops + op_off[p], op_cnt[p], d, T(c0), T(c1), T(c2), lu);
+}
+
+template <typename T>
+cudaError_t launch_tail_batched(const TailLevel *lv, const TailOp *ops, const int *op_off, const int *op_cnt,
+                                const int *active, int count, int d, const double *c, const double *lu, cudaStream_t s)
+{
+    tail_batched<T><<<count, kTailThreads, 0, s>>>(lv, ops, op_off, op_cnt, active, d, c[0], c[1], c[2], lu);
+    count_launch(1);
+    return cudaGetLastError();
+}
+template cudaError_t launch_tail_batched<float>(const TailLevel *, const TailOp *, const int *, const int *,
+                                                const int *, int, int, const double *, const double *, cudaStream_t);
+template cudaError_t launch_tail_batched<double>(const TailLevel *, const TailOp *, const int *, const int *,
+                                                 const int *, int, int, const double *, const double *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_tail(const TailArgs &a, cudaStream_t s)
