@@ -176,6 +176,81 @@ def _cpu_baseline_sample():
             "sample": f"1 V(1,1) cycle of the full-size problem in {dt:.1f} s (C oracle, 1 thread)"}
 
 
+def make_workload(name, torch):
+    """(step, unknowns, description, close) for one workload; step() runs one
+    full solve (or adjoint) and returns the cycle count."""
+    import numpy as np
+
+    from paper_2206_05543_gb300 import inputs, smoothers
+    from paper_2206_05543_gb300.binding import BatchedSolver, Solver
+
+    if name in ("2d8192", "2d8192-mixed", "2d64"):
+        n_ = 64 if name == "2d64" else N
+        prec = "fp32_ir" if name.endswith("mixed") else "fp64"
+        b = torch.from_numpy(inputs.sine(2, n_) if name == "2d64" else inputs.uniform(2, n_, SEED)).cuda()
+        u = torch.zeros_like(b)
+        s = Solver(2, n_, smoothers.M9, nu1=1, nu2=1, precision=prec)
+
+        def step():
+            u.zero_()
+            return s.solve(b, u, tol=TOL, max_cycles=100).cycles
+        return step, (n_ - 1) ** 2, f"2D N={n_} {prec} V(1,1) M9 to 1e-10", s.close
+    if name in ("3d512-fp64", "3d512-mixed"):
+        prec = "fp32_ir" if name.endswith("mixed") else "fp64"
+        b = torch.from_numpy(inputs.uniform(3, 512, SEED)).cuda()
+        u = torch.zeros_like(b)
+        s = Solver(3, 512, smoothers.M7, nu1=2, nu2=2, precision=prec)
+
+        def step():
+            u.zero_()
+            return s.solve(b, u, tol=TOL, max_cycles=100).cycles
+        return step, 511 ** 3, f"3D N=512 {prec} V(2,2) M7 to 1e-10", s.close
+    if name == "batch256":
+        Ns = [int(x) for x in inputs.batch_sizes(256, 0)]
+        bs = [torch.from_numpy(b).cuda() for b in inputs.batch_rhs(Ns, 1)]
+        us = [torch.zeros_like(b) for b in bs]
+        s = BatchedSolver(Ns, smoothers.M9, nu1=1, nu2=1)
+        tot = sum((n_ - 1) ** 2 for n_ in Ns)
+
+        def step():
+            for x in us:
+                x.zero_()
+            _, st, cyc, _ = s.solve(bs, us, tol=TOL, max_cycles=100)
+            return sum((n_ - 1) ** 2 * c for n_, c in zip(Ns, cyc)) / tot
+        return step, tot, "256 2D problems, N in {64..1024}, FP32 V(1,1) in FP64 refinement to 1e-10", s.close
+    if name == "adjoint128":
+        b = torch.from_numpy(inputs.gaussian(3, 128, 0)).to("cuda", torch.float32)
+        g = torch.from_numpy(np.random.default_rng(1).standard_normal(b.shape)).to("cuda", torch.float32)
+        s = Solver(3, 128, smoothers.M7, nu1=1, nu2=1, precision="fp32")
+
+        def step():
+            s.vcycles_adjoint(b, g, 4)
+            return 4
+        return step, 127 ** 3, "adjoint of 4 FP32 V(1,1) cycles, 3D N=128 (forward replay + reverse)", s.close
+    raise ValueError(name)
+
+
+ROWS = ["2d64", "2d8192-mixed", "3d512-fp64", "3d512-mixed", "batch256", "adjoint128"]
+
+
+def time_workload(name, torch, warmup=2, steps=3):
+    step, unknowns, desc, close = make_workload(name, torch)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times, cycles = [], 0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cycles = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    close()
+    ms = min(times)
+    return {"workload": desc, "ms": ms, "cycles": cycles, "dof_per_s": unknowns * cycles / (ms * 1e-3)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -188,6 +263,12 @@ def run_ours(args):
     from paper_2206_05543_gb300 import binding, inputs, smoothers
     from paper_2206_05543_gb300.binding import Solver
 
+    if args.workload != "2d8192":
+        # profiling entry: time --steps runs of another workload
+        r = time_workload(args.workload, torch, args.warmup, args.steps)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, **r, "note": "single-workload run"}), flush=True)
+        return
     peaks = _peaks()
     stream = torch.cuda.current_stream()
     b_host = torch.from_numpy(inputs.uniform(D, N, SEED)).pin_memory()
@@ -286,22 +367,9 @@ def run_ours(args):
         with open(tpath) as f:
             traffic = json.load(f).get("sweep2d_fp64_n8191")
 
-    # time to 1e-10: FP64 vs FP32-in-FP64 refinement on the same 2D grid
-    mixed = Solver(D, N, smoothers.M9, nu1=NU1, nu2=NU2, precision="fp32_ir")
-    um = torch.zeros_like(b)
-    for _ in range(2):
-        um.zero_()
-        minfo = mixed.solve(b, um, tol=TOL, max_cycles=100)
-    barrier()
-    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    m0.record(stream)
-    um.zero_()
-    minfo = mixed.solve(b, um, tol=TOL, max_cycles=100)
-    m1.record(stream)
-    torch.cuda.synchronize()
-    mixed_ms = m0.elapsed_time(m1)
-    mixed.close()
-
+    rows = {} if args.no_rows else {w: time_workload(w, torch) for w in ROWS}
+    if rows:
+        rows["3d512_mixed_speedup_vs_fp64"] = rows["3d512-fp64"]["ms"] / rows["3d512-mixed"]["ms"]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
@@ -314,8 +382,10 @@ def run_ours(args):
             "vcycles_per_s": total_cycles / (ms * 1e-3) / world,
             "cycles_per_solve": cycles / args.steps,
             "time_to_tol_ms": ms / args.steps,
-            "mixed_fp32_ir": {"time_to_tol_ms": mixed_ms, "iterations": minfo.cycles,
-                              "relres": minfo.relres, "speedup_vs_fp64": (ms / args.steps) / mixed_ms},
+            "mixed_fp32_ir": ({"time_to_tol_ms": rows["2d8192-mixed"]["ms"],
+                               "iterations": rows["2d8192-mixed"]["cycles"],
+                               "speedup_vs_fp64": (ms / args.steps) / rows["2d8192-mixed"]["ms"]}
+                              if rows else None),
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": peak_ops / 1e9,
                          "unit": "Gop/s FP64", "frac": achieved_ops / peak_ops, "traffic": traffic,
                          "kernel": "sweep2d_kernel<double> (finest level, n=8191)",
@@ -327,6 +397,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": u.numel() * 8},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
+            "rows": rows,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline_sample()
@@ -343,6 +414,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
+    ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--workload", default="2d8192", choices=["2d8192"] + ROWS,
+                    help="with --only-solve: which workload to time (profiling)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, kernel, mixed or CPU legs); used for profiler launch lists")
     args = ap.parse_args()
