@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmg.so")
-SOURCES = ["mg_kernels2d.cu", "mg_kernels3d.cu", "mg_tail.cu", "mg_host.cu", "mg_adjoint.cu", "mg_batched.cu", "mg_noalloc.cu"]
+SOURCES = ["mg_kernels2d.cu", "mg_pl2d.cu", "mg_pl3d.cu", "mg_kernels3d.cu", "mg_tail.cu", "mg_host.cu", "mg_adjoint.cu", "mg_batched.cu", "mg_noalloc.cu"]
 HEADERS = ["mg_common.cuh", "mg_internal.h", "mg_ctx.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -60,7 +60,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"]
+           "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64",
+           # fail at build time, not at load time, on a missing definition
+           "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

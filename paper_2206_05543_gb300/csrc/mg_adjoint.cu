@@ -233,9 +233,7 @@ struct Adjoint {
         memset(&a, 0, sizeof a);
         a.d = c->d;
         a.lu = c->lu;
-        a.lv[0].u = x;
-        a.lv[0].bh = (void *)rhs;
-        a.lv[0].n = 3;
+        a.lv[0] = tail_level(x, nullptr, (void *)rhs, nullptr, 3);
         a.ops[0].kind = TAIL_SOLVE;
         a.nops = 1;
         ok(launch_tail<T>(a, c->s));

@@ -54,9 +54,11 @@ __global__ void batched_sums(const double *__restrict__ partials, const int *__r
 }
 
 struct UpdItem {
-    double *u;
-    const float *e;
-    long long np;
+    double *u;        // compact FP64 caller array
+    const float *e;   // padded FP32 level 0 result
+    long long np;     // n * n
+    int n, pitch;
+    long long off;
 };
 
 constexpr int kUpdChunk = 8192;
@@ -67,10 +69,16 @@ __global__ void batched_update(const UpdItem *__restrict__ tab, const int *__res
     const int p = blockIdx.y;
     if (!active[p]) return;
     const UpdItem it = tab[p];
-    const long long beg = (long long)blockIdx.x * kUpdChunk;
-    if (beg >= it.np) return;
-    const long long end = beg + kUpdChunk < it.np ? beg + kUpdChunk : it.np;
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) it.u[i] = __dadd_rn(it.u[i], (double)it.e[i]);
+    // chunk = kUpdChunk / n_pad rows of the problem (whole rows)
+    const int rows = max(1, kUpdChunk / it.n);
+    const int y0 = blockIdx.x * rows;
+    if (y0 >= it.n) return;
+    const int y1 = min(y0 + rows, it.n);
+    for (int y = y0; y < y1; ++y) {
+        double *ur = it.u + (long long)y * it.n;
+        const float *er = it.e + it.off + (long long)y * it.pitch;
+        for (int x = threadIdx.x; x < it.n; x += blockDim.x) ur[x] = __dadd_rn(ur[x], (double)er[x]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -243,13 +251,13 @@ mg_status autotune(mg_ctx *c, BatchWork *w)
         static const int sweep_c[] = {4, 8, 16, 32, 64};
         static const int rr_c[] = {2, 4, 8, 16, 32};
         tune("sweep", sweep_c, 5, S.H, [&](int H) {
-            launch_sweep2d_batched<float>(S.pre[0], np, w->active, S.n, H, true, c->c, c->s);
+            launch_sweep2d_pl_batched(S.pre[0], np, w->active, S.n, H, true, c->c, c->s);
         });
         tune("restrict", rr_c, 5, S.Hrr, [&](int H) {
-            launch_resrestrict2d_batched<float>(S.rr, np, w->active, S.n, H, c->s);
+            launch_resrestrict2d_pl_batched(S.rr, np, w->active, S.n, H, c->s);
         });
         tune("prolong", rr_c, 5, S.Hpro, [&](int H) {
-            launch_prolong2d_batched<float>(S.pro, np, w->active, S.n, H, c->s);
+            launch_prolong2d_pl_batched(S.pro, np, w->active, S.n, H, c->s);
         });
     }
     cudaEventDestroy(e0);
@@ -268,16 +276,16 @@ cudaError_t record_rest(mg_ctx *c, BatchWork *w)
     for (BatchSize &S : w->sizes) {
         const int np = (int)S.probs.size();
         for (int k = 0; k < nu1; ++k)
-            if ((e = launch_sweep2d_batched<float>(S.pre[k], np, w->active, S.n, S.H, k == 0, c->c, c->s))) return e;
+            if ((e = launch_sweep2d_pl_batched(S.pre[k], np, w->active, S.n, S.H, k == 0, c->c, c->s))) return e;
         if (nu1 == 0) {
             // no pre-sweep: the level's value is zero
             for (size_t j = 0; j < S.probs.size(); ++j) {
                 const int p = S.probs[j], l = S.lev[j];
-                const size_t bytes = (size_t)S.n * S.n * sizeof(float);
+                const size_t bytes = pitch2_floats(S.n) * sizeof(float);
                 if ((e = cudaMemsetAsync(w->A[p][l], 0, bytes, c->s))) return e;
             }
         }
-        if ((e = launch_resrestrict2d_batched<float>(S.rr, np, w->active, S.n, S.Hrr, c->s))) return e;
+        if ((e = launch_resrestrict2d_pl_batched(S.rr, np, w->active, S.n, S.Hrr, c->s))) return e;
     }
     // tails, one block per problem
     if ((e = launch_tail_batched<float>(w->tail_lv, w->tail_ops, w->op_off, w->op_cnt, w->active, w->count, w->d, c->c,
@@ -287,9 +295,9 @@ cudaError_t record_rest(mg_ctx *c, BatchWork *w)
     for (auto it = w->sizes.rbegin(); it != w->sizes.rend(); ++it) {
         BatchSize &S = *it;
         const int np = (int)S.probs.size();
-        if ((e = launch_prolong2d_batched<float>(S.pro, np, w->active, S.n, S.Hpro, c->s))) return e;
+        if ((e = launch_prolong2d_pl_batched(S.pro, np, w->active, S.n, S.Hpro, c->s))) return e;
         for (int k = 0; k < nu2; ++k)
-            if ((e = launch_sweep2d_batched<float>(S.post[k], np, w->active, S.n, S.H, false, c->c, c->s))) return e;
+            if ((e = launch_sweep2d_pl_batched(S.post[k], np, w->active, S.n, S.H, false, c->c, c->s))) return e;
     }
     // u_i += e_i in FP64
     batched_update<<<dim3(w->upd_chunks, w->count), 256, 0, c->s>>>(w->upd, w->active);
@@ -301,7 +309,11 @@ cudaError_t record_pre(mg_ctx *c, BatchWork *w)
 {
     cudaError_t e;
     for (BatchGroup &G : w->groups)
-        if ((e = launch_residual2d_batched<float>(G.res, (int)G.probs.size(), w->active, G.n, c->s))) return e;
+    {
+        const Pitch2 g = pitch2(G.n);
+        if ((e = launch_residual2d_batched<float>(G.res, (int)G.probs.size(), w->active, G.n, c->s, g.pitch, g.off)))
+            return e;
+    }
     batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2);
     count_launch(1);
     if ((e = cudaGetLastError())) return e;
@@ -420,7 +432,7 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
                 w->RH[p].assign(L, nullptr);
             }
             for (int l = 0; l < L; ++l) {
-                const size_t bytes = (size_t)w->n[p][l] * w->n[p][l] * sizeof(float);
+                const size_t bytes = pitch2_floats(w->n[p][l]) * sizeof(float);
                 float *A = (float *)a.take(bytes), *B = (float *)a.take(bytes), *BH = (float *)a.take(bytes);
                 float *RH = l >= w->lt[p] ? (float *)a.take(bytes) : nullptr;
                 if (real) {
@@ -480,6 +492,11 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
     Arena real;
     real.base = w->arena;
     carve(real, true);
+    // ghost rings and row padding of every padded level must read as zero
+    if ((ce = cudaMemset(w->arena, 0, plan.off)) != cudaSuccess) {
+        mg_destroy(c);
+        return cuda_fail(ce);
+    }
     if (cudaMallocHost((void **)&w->h_norm2, count * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&w->h_active, count * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -527,11 +544,10 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
         for (int p = 0; p < count; ++p)
             for (int l = w->lt[p]; l < (int)w->n[p].size(); ++l) {
                 TailLevel &t = tl[(size_t)p * kMaxTailLevels + (l - w->lt[p])];
-                t.u = w->A[p][l];
-                t.tmp = w->B[p][l];
-                t.bh = w->BH[p][l];
-                t.rh = w->RH[p][l];
-                t.n = w->n[p][l];
+                t = tail_level(w->A[p][l], w->B[p][l], w->BH[p][l], w->RH[p][l], w->n[p][l]);
+                const Pitch2 g = pitch2(w->n[p][l]);
+                t.pitch = g.pitch;
+                t.off = g.off;
             }
         up(w->tail_lv, tl.data(), tl.size() * sizeof(TailLevel));
         up(w->tail_ops, ops_all.data(), ops_all.size() * sizeof(TailOp));
@@ -550,13 +566,17 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
         }
     }
     w->upd_host.resize(count);
-    long long maxnp = 1;
     for (int p = 0; p < count; ++p) {
         const long long np = (long long)w->n[p][0] * w->n[p][0];
-        maxnp = std::max(maxnp, np);
-        w->upd_host[p] = UpdItem{nullptr, result_buf(w, p, 0, nu1 + nu2), np};
+        const Pitch2 g = pitch2(w->n[p][0]);
+        w->upd_host[p] = UpdItem{nullptr, result_buf(w, p, 0, nu1 + nu2), np, w->n[p][0], g.pitch, g.off};
     }
-    w->upd_chunks = (int)((maxnp + kUpdChunk - 1) / kUpdChunk);
+    int maxchunks = 1;
+    for (int p = 0; p < count; ++p) {
+        const int n = w->n[p][0], rows = std::max(1, kUpdChunk / n);
+        maxchunks = std::max(maxchunks, (n + rows - 1) / rows);
+    }
+    w->upd_chunks = maxchunks;
     for (cudaError_t e : errs)
         if (e != cudaSuccess) {
             mg_destroy(c);

@@ -40,6 +40,7 @@ struct mg_ctx {
     std::vector<int> n;
     std::vector<void *> A, B, BH, RH;
     size_t esize = 8;
+    bool pl = false;  // FP32 levels in the padded layout (refinement, 2D)
     double *lu = nullptr;
     double *partials = nullptr;
     int npartials = 0;

@@ -100,6 +100,27 @@ cudaError_t launch_add_to_f64(double *u, const T *e, size_t np, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// u (compact FP64) += e (padded FP32 layout); block y = row, x-threads = columns
+__global__ void add_pl2d_kernel(double *__restrict__ u, const float *__restrict__ e, Pitch2 g)
+{
+    const int n = g.n;
+    for (int y = blockIdx.y; y < n; y += gridDim.y) {
+        double *ur = u + (long)y * n;
+        const float *er = e + g.off + (long)y * g.pitch;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+            ur[x] = __dadd_rn(ur[x], (double)er[x]);
+    }
+}
+
+cudaError_t launch_add_pl2d(double *u, const float *e, int n, cudaStream_t s)
+{
+    const int bx = (n + 255) / 256;
+    const int by = (int)std::min<long>(n, std::max<long>(1, (long)num_sms() * 16 / bx));
+    add_pl2d_kernel<<<dim3(bx, by), 256, 0, s>>>(u, e, pitch2(n));
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 template <typename InT, typename T>
 __global__ void scale_copy_kernel(const InT *__restrict__ b, T *__restrict__ bh, size_t np, InT h2)
 {
@@ -235,14 +256,45 @@ static mg_status dalloc(mg_ctx *c, void **p, size_t bytes)
 // ---------------------------------------------------------------------------
 namespace {
 
+// bytes of one buffer of level l in the context's layout
+size_t level_bytes(const mg_ctx *c, int l)
+{
+    const int n = c->n[l];
+    if (c->pl) return (c->d == 2 ? pitch2_floats(n) : pitch3_floats(n)) * sizeof(float);
+    return npoints(c->d, n) * c->esize;
+}
+
 template <typename T>
 struct Recorder {
     mg_ctx *c;
     const T *b0;       // finest-level right-hand side (unscaled in FP64 mode)
     bool b0_unscaled;
     T *A0;             // finest-level primary buffer
+    double *acc64 = nullptr;    // refinement: FP64 solution the last sweep adds into
+    bool fused_update = false;  // set when that addition was recorded
 
     T *A(int l) { return l == 0 ? A0 : (T *)c->A[l]; }
+    bool pl() const { return c->pl; }
+    cudaError_t sweep(const T *u, const T *b, bool unsc, T *out, int n)
+    {
+        if (pl() && c->d == 2)
+            return launch_sweep2d_pl((const float *)u, (const float *)b, (float *)out, n, c->c, nullptr, c->s);
+        if (pl()) return launch_sweep3d_pl((const float *)u, (const float *)b, (float *)out, nullptr, n, c->c, c->s);
+        return op_sweep<T>(c->d, u, b, unsc, out, n, c->c, nullptr, c->s);
+    }
+    cudaError_t resrestrict(const T *u, const T *b, bool unsc, T *bc, int n)
+    {
+        if (pl() && c->d == 2) return launch_resrestrict2d_pl((const float *)u, (const float *)b, (float *)bc, n, c->s);
+        if (pl()) return launch_resrestrict3d_pl((const float *)u, (const float *)b, (float *)bc, n, c->s);
+        return op_resrestrict<T>(c->d, u, b, unsc, bc, n, c->s);
+    }
+    cudaError_t prolong(const T *e, T *u, int n)
+    {
+        if (pl() && c->d == 2) return launch_prolong2d_pl((const float *)e, (float *)u, n, c->s);
+        if (pl()) return launch_prolong3d_pl((const float *)e, (float *)u, n, c->s);
+        return op_prolong<T>(c->d, e, u, n, c->s);
+    }
+    size_t bytes(int l) const { return level_bytes(c, l); }
     T *B(int l) { return (T *)c->B[l]; }
     const T *BH(int l) { return l == 0 ? b0 : (const T *)c->BH[l]; }
     bool unsc(int l) { return l == 0 && b0_unscaled; }
@@ -280,12 +332,18 @@ struct Recorder {
         a.lu = c->lu;
         for (int j = 0; j < 3; ++j) a.c[j] = c->c[j];
         for (int k = c->lt; k < c->L; ++k) {
-            TailLevel &tl = a.lv[k - c->lt];
-            tl.u = A(k);
-            tl.tmp = B(k);
-            tl.bh = (void *)c->BH[k];  // the tail always reads a scaled rhs buffer
-            tl.rh = c->RH[k];
-            tl.n = c->n[k];
+            // the tail always reads a scaled rhs buffer
+            a.lv[k - c->lt] = tail_level(A(k), B(k), (void *)c->BH[k], c->RH[k], c->n[k]);
+            if (c->pl && c->d == 2) {
+                const Pitch2 g = pitch2(c->n[k]);
+                a.lv[k - c->lt].pitch = g.pitch;
+                a.lv[k - c->lt].off = g.off;
+            } else if (c->pl) {
+                const Pitch3 g = pitch3(c->n[k]);
+                a.lv[k - c->lt].pitch = g.pitch;
+                a.lv[k - c->lt].plane = g.plane;
+                a.lv[k - c->lt].off = g.off;
+            }
         }
         bool ok = true;
         if (zero_start) {
@@ -324,30 +382,35 @@ struct Recorder {
                 zero = false;
                 continue;
             }
-            e = op_sweep<T>(c->d, zero ? nullptr : buf[cur], BH(l), unsc(l), buf[1 - cur], n, c->c, nullptr, c->s);
+            e = sweep(zero ? nullptr : buf[cur], BH(l), unsc(l), buf[1 - cur], n);
             if (e) return e;
             cur = 1 - cur;
             zero = false;
         }
         if (zero) {
-            e = cudaMemsetAsync(buf[cur], 0, npoints(c->d, n) * sizeof(T), c->s);
+            e = cudaMemsetAsync(buf[cur], 0, bytes(l), c->s);
             if (e) return e;
         }
-        e = op_resrestrict<T>(c->d, buf[cur], BH(l), unsc(l), (T *)c->BH[l + 1], n, c->s);
+        e = resrestrict(buf[cur], BH(l), unsc(l), (T *)c->BH[l + 1], n);
         if (e) return e;
         for (int g = 0; g < c->gamma; ++g) {
             e = visit(l + 1, g == 0, false);
             if (e) return e;
         }
-        e = op_prolong<T>(c->d, A(l + 1), buf[cur], n, c->s);
+        e = prolong(A(l + 1), buf[cur], n);
         if (e) return e;
         for (int s = 0; s < c->nu2; ++s) {
-            e = op_sweep<T>(c->d, buf[cur], BH(l), unsc(l), buf[1 - cur], n, c->c, nullptr, c->s);
+            if (l == 0 && acc64 && pl() && c->d == 2 && s == c->nu2 - 1) {
+                // refinement: the last finest sweep adds its result to the FP64 u
+                fused_update = true;
+                return launch_sweep2d_pl_acc64((const float *)buf[cur], (const float *)BH(l), acc64, n, c->c, c->s);
+            }
+            e = sweep(buf[cur], BH(l), unsc(l), buf[1 - cur], n);
             if (e) return e;
             cur = 1 - cur;
         }
         if (cur != 0) {
-            e = cudaMemcpyAsync(buf[0], buf[1], npoints(c->d, n) * sizeof(T), cudaMemcpyDeviceToDevice, c->s);
+            e = cudaMemcpyAsync(buf[0], buf[1], bytes(l), cudaMemcpyDeviceToDevice, c->s);
             if (e) return e;
         }
         return cudaSuccess;
@@ -406,16 +469,30 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
         // from zero; u += e in FP64
         Recorder<float> R{c, (const float *)c->BH[0], false, (float *)c->A[0]};
         st = capture(c, &c->g.pre, &c->g.pre_nodes, [&]() -> cudaError_t {
-            cudaError_t e = op_residual<double, float>(d, (const double *)u, (const double *)b, true,
-                                                       (float *)c->BH[0], n0, c->partials, c->s);
+            cudaError_t e;
+            if (c->pl && d == 2) {
+                const Pitch2 g = pitch2(n0);
+                e = launch_residual2d<double, float>((const double *)u, (const double *)b, true, (float *)c->BH[0],
+                                                     n0, c->partials, c->s, g.pitch, g.off);
+            } else if (c->pl) {
+                const Pitch3 g = pitch3(n0);
+                e = launch_residual3d<double, float>((const double *)u, (const double *)b, true, (float *)c->BH[0],
+                                                     n0, c->partials, c->s, g.pitch, g.plane, g.off);
+            } else {
+                e = op_residual<double, float>(d, (const double *)u, (const double *)b, true, (float *)c->BH[0], n0,
+                                               c->partials, c->s);
+            }
             if (e) return e;
             if ((e = launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s))) return e;
             return cudaMemcpyAsync(c->h_norm2, c->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, c->s);
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
+            R.acc64 = (double *)u;
             cudaError_t e = R.visit(0, true, false);
-            if (e) return e;
+            if (e || R.fused_update) return e;
+            if (c->pl && d == 2) return launch_add_pl2d((double *)u, (const float *)c->A[0], n0, c->s);
+            if (c->pl) return launch_add_pl3d((double *)u, (const float *)c->A[0], n0, c->s);
             return launch_add_to_f64<float>((double *)u, (const float *)c->A[0], np0, c->s);
         });
         if (st != MG_OK) return st;
@@ -511,13 +588,17 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
         c->B.assign(c->L, nullptr);
         c->BH.assign(c->L, nullptr);
         c->RH.assign(c->L, nullptr);
+        c->pl = prec == MG_FP32_IR;
         for (int l = 0; l < c->L; ++l) {
-            const size_t bytes = npoints(d, c->n[l]) * c->esize;
+            const size_t bytes = level_bytes(c, l);
             const bool caller_level = l == 0 && prec != MG_FP32_IR;
             if (!caller_level) MG_TRY(dalloc(c, &c->A[l], bytes));
             MG_TRY(dalloc(c, &c->B[l], bytes));
             if (!caller_level || c->lt == 0) MG_TRY(dalloc(c, &c->BH[l], bytes));
             if (l >= c->lt) MG_TRY(dalloc(c, &c->RH[l], bytes));
+            if (c->pl)  // ghost rings and row padding must read as zero
+                for (void *p : {c->A[l], c->B[l], c->BH[l], c->RH[l]})
+                    if (p) MG_TRYC(cudaMemset(p, 0, bytes));
         }
         int np = std::max(sweep_partials(d, c->n[0]), residual_partials(d, c->n[0]));
         c->npartials = np;
@@ -551,10 +632,60 @@ static bool valid_level(int d, int n)
     return (d == 2 || d == 3) && n >= 3 && (n & 1) && valid_N(n + 1);
 }
 
+// FP32 2D single operators run the padded-layout kernels of the FP32 cycles:
+// the compact arrays are packed into zero-ringed temporaries and unpacked.
+struct PaddedTmp {
+    int d = 2;
+    std::vector<float *> bufs;
+    explicit PaddedTmp(int dim) : d(dim) {}
+    ~PaddedTmp()
+    {
+        for (float *p : bufs) cudaFree(p);
+    }
+    float *make(int n, const void *compact, cudaStream_t s, cudaError_t &e)
+    {
+        float *p = nullptr;
+        const size_t bytes = (d == 2 ? pitch2_floats(n) : pitch3_floats(n)) * sizeof(float);
+        if (e == cudaSuccess) e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) bufs.push_back(p);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, s);
+        if (e == cudaSuccess && compact) e = pack((const float *)compact, p, n, true, s);
+        return p;
+    }
+    cudaError_t pack(const float *in, float *out, int n, bool to_padded, cudaStream_t s)
+    {
+        return d == 2 ? launch_pack2d(in, out, n, to_padded, s) : launch_pack3d(in, out, n, to_padded, s);
+    }
+};
+
+static mg_status op_sweep_pl(int d, int n, const double *c, const void *u, const void *bh, int unscaled, void *out,
+                             double *rnorm2, cudaStream_t s)
+{
+    if (unscaled) return MG_EINVAL;  // the FP32 cycles only see scaled right-hand sides
+    if (d == 3 && rnorm2) return MG_EINVAL;  // the 3D FP32 sweep has no fused norm
+    cudaError_t e = cudaSuccess;
+    PaddedTmp tmp(d);
+    float *pu = u ? tmp.make(n, u, s, e) : nullptr;
+    float *pb = tmp.make(n, bh, s, e), *po = tmp.make(n, nullptr, s, e);
+    double *partials = nullptr;
+    const int np = d == 2 ? sweep2d_pl_blocks(n, sweep2d_pl_H(n)) : 0;
+    if (!e && rnorm2) e = cudaMalloc(&partials, (size_t)(np + 1) * sizeof(double));
+    if (!e) e = d == 2 ? launch_sweep2d_pl(pu, pb, po, n, c, partials, s) : launch_sweep3d_pl(pu, pb, po, nullptr, n, c, s);
+    if (!e) e = tmp.pack(po, (float *)out, n, false, s);
+    if (!e && rnorm2) {
+        e = launch_sum_partials(partials, np, partials + np, s);
+        if (!e) e = cudaMemcpyAsync(rnorm2, partials + np, sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    if (!e) e = cudaStreamSynchronize(s);
+    if (partials) cudaFree(partials);
+    return e ? cuda_fail(e) : MG_OK;
+}
+
 template <typename T>
 static mg_status op_sweep_t(int d, int n, const double *c, const void *u, const void *bh, int unscaled, void *out,
                             double *rnorm2, cudaStream_t s)
 {
+    if (sizeof(T) == 4 && !unscaled && !(d == 3 && rnorm2)) return op_sweep_pl(d, n, c, u, bh, unscaled, out, rnorm2, s);
     double *partials = nullptr, *sum = nullptr;
     cudaError_t e;
     if (rnorm2) {
@@ -712,7 +843,15 @@ mg_status mg_op_residual_restrict(int d, int n, mg_prec prec, const void *u, con
     if (prec == MG_FP64)
         e = op_resrestrict<double>(d, (const double *)u, (const double *)bh, b_unscaled != 0,
                                    (double *)bh_coarse_out, n, (cudaStream_t)stream);
-    else if (prec == MG_FP32_IR)
+    else if (prec == MG_FP32_IR && !b_unscaled) {
+        PaddedTmp tmp(d);
+        e = cudaSuccess;
+        const cudaStream_t s = (cudaStream_t)stream;
+        float *pu = tmp.make(n, u, s, e), *pb = tmp.make(n, bh, s, e), *pc = tmp.make((n - 1) / 2, nullptr, s, e);
+        if (!e) e = d == 2 ? launch_resrestrict2d_pl(pu, pb, pc, n, s) : launch_resrestrict3d_pl(pu, pb, pc, n, s);
+        if (!e) e = tmp.pack(pc, (float *)bh_coarse_out, (n - 1) / 2, false, s);
+        if (!e) e = cudaStreamSynchronize(s);
+    } else if (prec == MG_FP32_IR)
         e = op_resrestrict<float>(d, (const float *)u, (const float *)bh, b_unscaled != 0, (float *)bh_coarse_out,
                                   n, (cudaStream_t)stream);
     else
@@ -726,7 +865,15 @@ mg_status mg_op_prolong_correct(int d, int n, mg_prec prec, const void *e_coarse
     cudaError_t e;
     if (prec == MG_FP64)
         e = op_prolong<double>(d, (const double *)e_coarse, (double *)u, n, (cudaStream_t)stream);
-    else if (prec == MG_FP32_IR)
+    else if (prec == MG_FP32_IR) {
+        PaddedTmp tmp(d);
+        e = cudaSuccess;
+        const cudaStream_t s = (cudaStream_t)stream;
+        float *pe = tmp.make((n - 1) / 2, e_coarse, s, e), *pu = tmp.make(n, u, s, e);
+        if (!e) e = d == 2 ? launch_prolong2d_pl(pe, pu, n, s) : launch_prolong3d_pl(pe, pu, n, s);
+        if (!e) e = tmp.pack(pu, (float *)u, n, false, s);
+        if (!e) e = cudaStreamSynchronize(s);
+    } else if (prec == MG_FP32_IR)
         e = op_prolong<float>(d, (const float *)e_coarse, (float *)u, n, (cudaStream_t)stream);
     else
         return MG_EINVAL;
@@ -746,9 +893,7 @@ mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, v
     memset(&a, 0, sizeof a);
     a.d = d;
     a.lu = dlu;
-    a.lv[0].u = x_out;
-    a.lv[0].bh = (void *)bh;
-    a.lv[0].n = 3;
+    a.lv[0] = tail_level(x_out, nullptr, (void *)bh, nullptr, 3);
     a.ops[0].kind = TAIL_SOLVE;
     a.ops[0].level = 0;
     a.nops = 1;

@@ -44,7 +44,7 @@ cudaError_t launch_prolong2d(const T *e, T *u, int n, cudaStream_t s);
 // sums (one per block of sweep2d_grid(n)) when partials != nullptr.
 template <typename InT, typename OutT>
 cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
-                              cudaStream_t s);
+                              cudaStream_t s, long out_pitch = 0, long out_off = 0);
 
 struct Grid3 {
     int bx, by, bz, Z;
@@ -62,7 +62,7 @@ template <typename T>
 cudaError_t launch_prolong3d(const T *e, T *u, int n, cudaStream_t s);
 template <typename InT, typename OutT>
 cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
-                              cudaStream_t s);
+                              cudaStream_t s, long out_pitch = 0, long out_plane = 0, long out_off = 0);
 
 // ---- batched 2D operators (one launch per grid size across problems) -------
 template <typename T>
@@ -89,8 +89,49 @@ cudaError_t launch_resrestrict2d_batched(const BItem<T> *tab, int nprob, const i
 template <typename T>
 cudaError_t launch_prolong2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc, cudaStream_t s);
 template <typename OutT>
-cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s);
+cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s,
+                                      long opitch = 0, long ooff = 0);
 int residual2d_batched_tiles(int n);
+cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, bool zero_u,
+                                      const double *c, cudaStream_t s);
+cudaError_t launch_resrestrict2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int Hc,
+                                            cudaStream_t s);
+cudaError_t launch_prolong2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int Hc,
+                                        cudaStream_t s);
+
+// ---- padded FP32 layout (mg_pl2d.cu) ---------------------------------------
+// A level with n points per axis stored with a zero ghost ring and padded,
+// 16-byte-aligned rows: element (x, y), x, y in [-1, n], at off + y*pitch + x.
+struct Pitch2 {
+    int n, pitch, rows;
+    long off;
+};
+Pitch2 pitch2(int n);
+size_t pitch2_floats(int n);
+cudaError_t launch_sweep2d_pl(const float *u, const float *b, float *out, int n, const double *c, double *partials,
+                              cudaStream_t s);
+cudaError_t launch_resrestrict2d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s);
+cudaError_t launch_prolong2d_pl(const float *e, float *u, int n, cudaStream_t s);
+cudaError_t launch_pack2d(const float *in, float *out, int n, bool to_padded, cudaStream_t s);
+cudaError_t launch_add_pl2d(double *u, const float *e, int n, cudaStream_t s);
+cudaError_t launch_sweep2d_pl_acc64(const float *u, const float *b, double *u64, int n, const double *c, cudaStream_t s);
+int sweep2d_pl_blocks(int n, int H);
+
+// 3D: element (x, y, z), each in [-1, n], at off + z*plane + y*pitch + x.
+struct Pitch3 {
+    int n, pitch;
+    long plane, off;
+};
+Pitch3 pitch3(int n);
+size_t pitch3_floats(int n);
+// u == nullptr: zero start; u64 != nullptr: refinement epilogue u64 += result
+cudaError_t launch_sweep3d_pl(const float *u, const float *b, float *out, double *u64, int n, const double *c,
+                              cudaStream_t s);
+cudaError_t launch_resrestrict3d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s);
+cudaError_t launch_prolong3d_pl(const float *e, float *u, int n, cudaStream_t s);
+cudaError_t launch_pack3d(const float *in, float *out, int n, bool to_padded, cudaStream_t s);
+cudaError_t launch_add_pl3d(double *u, const float *e, int n, cudaStream_t s);
+int sweep2d_pl_H(int n);
 
 // ---- coarse tail (one block runs the last levels of a cycle) --------------
 constexpr int kTailThreads = 256;
@@ -99,7 +140,8 @@ constexpr int kMaxTailOps = 480;
 enum TailOpKind : int { TAIL_ZERO = 0, TAIL_SWEEP = 1, TAIL_RESTRICT = 2, TAIL_SOLVE = 3, TAIL_PROLONG = 4 };
 struct TailLevel {
     void *u, *tmp, *bh, *rh;  // element type = the kernel's T
-    int n;
+    int n, pitch;             // element (x, y, z) at off + z*plane + y*pitch + x
+    long plane, off;          // compact: pitch = n, plane = n*n, off = 0
 };
 struct TailOp {
     short kind, level;  // level indexes TailArgs::lv
@@ -111,6 +153,19 @@ struct TailArgs {
     const double *lu;  // coarsest LU factors (device)
     int d, nops;
 };
+inline TailLevel tail_level(void *u, void *tmp, void *bh, void *rh, int n)
+{
+    TailLevel t;
+    t.u = u;
+    t.tmp = tmp;
+    t.bh = bh;
+    t.rh = rh;
+    t.n = n;
+    t.pitch = n;
+    t.plane = (long)n * n;
+    t.off = 0;
+    return t;
+}
 template <typename T>
 cudaError_t launch_tail(const TailArgs &a, cudaStream_t s);
 // lv: count x kMaxTailLevels levels; problem p runs ops[op_off[p] .. + op_cnt[p]]

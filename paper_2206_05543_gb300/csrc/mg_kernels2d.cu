@@ -246,7 +246,8 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
 template <typename InT, typename OutT>
 __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const InT *__restrict__ b,
                                                 OutT *__restrict__ rh_out, int n, int H, int hk, bool unscaled,
-                                                int tbx, int tby, double *__restrict__ partial)
+                                                int tbx, int tby, double *__restrict__ partial, long opitch = 0,
+                                                long ooff = 0)
 {
     __shared__ InT su[2][kSweepThreads + 2];
     const int t = threadIdx.x;
@@ -273,7 +274,7 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
             if (unscaled) bb = scale2(bb, hk);
             const InT r = radd(rfma(InT(-4), u_cur, bb), s);
             acc = fma((double)r, (double)r, acc);
-            if (rh_out) rh_out[(size_t)j * ld + x] = (OutT)r;
+            if (rh_out) rh_out[opitch ? ooff + j * opitch + x : (long)j * ld + x] = (OutT)r;
         }
         u_prev = u_cur;
         u_cur = u_next;
@@ -284,10 +285,10 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kSweepThreads)
 residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
-                  int n, int H, int hk, bool unscaled, double *__restrict__ partials)
+                  int n, int H, int hk, bool unscaled, double *__restrict__ partials, long opitch, long ooff)
 {
     residual2d_tile<InT, OutT>(u, b, rh_out, n, H, hk, unscaled, blockIdx.x, blockIdx.y,
-                               partials ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr);
+                               partials ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr, opitch, ooff);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,14 +354,15 @@ prolong2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__rest
 template <typename OutT>
 __global__ void __launch_bounds__(kSweepThreads)
 residual2d_batched(const BRes<OutT> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int H,
-                   int bx, int by, int hk)
+                   int bx, int by, int hk, long opitch, long ooff)
 {
     const int per = bx * by, total = nprob * per;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int j = it / per, r = it - j * per;
         const BRes<OutT> e = tab[j];
         if (active[e.problem])
-            residual2d_tile<double, OutT>(e.u, e.b, e.out, n, H, hk, true, r % bx, r / bx, e.partials + r);
+            residual2d_tile<double, OutT>(e.u, e.b, e.out, n, H, hk, true, r % bx, r / bx, e.partials + r, opitch,
+                                          ooff);
         __syncthreads();
     }
 }
@@ -437,20 +439,20 @@ cudaError_t launch_prolong2d(const T *e, T *u, int n, cudaStream_t s)
 
 template <typename InT, typename OutT>
 cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
-                              cudaStream_t s)
+                              cudaStream_t s, long out_pitch, long out_off)
 {
     const Grid2 g = sweep2d_grid(n);
     residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads, 0, s>>>(u, b, rh, n, g.H, h2_exponent(n),
-                                                                           unscaled, partials);
+                                                                           unscaled, partials, out_pitch, out_off);
     count_launch(1);
     return cudaGetLastError();
 }
 template cudaError_t launch_residual2d<double, double>(const double *, const double *, bool, double *, int,
-                                                       double *, cudaStream_t);
+                                                       double *, cudaStream_t, long, long);
 template cudaError_t launch_residual2d<double, float>(const double *, const double *, bool, float *, int,
-                                                      double *, cudaStream_t);
+                                                      double *, cudaStream_t, long, long);
 template cudaError_t launch_residual2d<float, float>(const float *, const float *, bool, float *, int,
-                                                     double *, cudaStream_t);
+                                                     double *, cudaStream_t, long, long);
 
 
 // ---- batched launchers ------------------------------------------------------
@@ -512,12 +514,14 @@ int residual2d_batched_tiles(int n)
 }
 
 template <typename OutT>
-cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s)
+cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s,
+                                      long opitch, long ooff)
 {
     const Grid2 g = sweep2d_grid(n);
     const long items = (long)nprob * g.bx * g.by;
     const int grid = persistent_grid((const void *)residual2d_batched<OutT>, kSweepThreads, items);
-    residual2d_batched<OutT><<<grid, kSweepThreads, 0, s>>>(tab, nprob, active, n, g.H, g.bx, g.by, h2_exponent(n));
+    residual2d_batched<OutT><<<grid, kSweepThreads, 0, s>>>(tab, nprob, active, n, g.H, g.bx, g.by, h2_exponent(n),
+                                                            opitch, ooff);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -532,8 +536,10 @@ template cudaError_t launch_resrestrict2d_batched<double>(const BItem<double> *,
                                                           cudaStream_t);
 template cudaError_t launch_prolong2d_batched<float>(const BItem<float> *, int, const int *, int, int, cudaStream_t);
 template cudaError_t launch_prolong2d_batched<double>(const BItem<double> *, int, const int *, int, int, cudaStream_t);
-template cudaError_t launch_residual2d_batched<float>(const BRes<float> *, int, const int *, int, cudaStream_t);
-template cudaError_t launch_residual2d_batched<double>(const BRes<double> *, int, const int *, int, cudaStream_t);
+template cudaError_t launch_residual2d_batched<float>(const BRes<float> *, int, const int *, int, cudaStream_t, long,
+                                                      long);
+template cudaError_t launch_residual2d_batched<double>(const BRes<double> *, int, const int *, int, cudaStream_t, long,
+                                                       long);
 
 #define MG_INST(T)                                                                                   \
     template cudaError_t launch_sweep2d<T>(const T *, const T *, bool, T *, int, const double *,     \

@@ -269,7 +269,7 @@ prolong3d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Zc)
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kP3X * kP3Y)
 residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out, int n,
-                  int Z, int hk, bool unscaled, double *__restrict__ partials)
+                  int Z, int hk, bool unscaled, double *__restrict__ partials, long opitch, long oplane, long ooff)
 {
     const int x = blockIdx.x * kP3X + threadIdx.x % kP3X;
     const int y = blockIdx.y * kP3Y + threadIdx.x / kP3X;
@@ -289,7 +289,7 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
             if (unscaled) bb = scale2(bb, hk);
             const InT r = radd(rfma(InT(-6), u_cur, bb), s);
             acc = fma((double)r, (double)r, acc);
-            if (rh_out) rh_out[p] = (OutT)r;
+            if (rh_out) rh_out[opitch ? ooff + z * oplane + (long)y * opitch + x : (long)p] = (OutT)r;
             u_prev = u_cur;
             u_cur = u_next;
         }
@@ -379,11 +379,11 @@ cudaError_t launch_prolong3d(const T *e, T *u, int n, cudaStream_t s)
 
 template <typename InT, typename OutT>
 cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *rh, int n, double *partials,
-                              cudaStream_t s)
+                              cudaStream_t s, long out_pitch, long out_plane, long out_off)
 {
     const Grid3 g = residual3d_grid(n);
-    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kP3X * kP3Y, 0, s>>>(u, b, rh, n, g.Z, h2_exponent(n),
-                                                                               unscaled, partials);
+    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kP3X * kP3Y, 0, s>>>(
+        u, b, rh, n, g.Z, h2_exponent(n), unscaled, partials, out_pitch, out_plane, out_off);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -397,10 +397,10 @@ MG_INST(double)
 MG_INST(float)
 #undef MG_INST
 template cudaError_t launch_residual3d<double, double>(const double *, const double *, bool, double *, int,
-                                                       double *, cudaStream_t);
+                                                       double *, cudaStream_t, long, long, long);
 template cudaError_t launch_residual3d<double, float>(const double *, const double *, bool, float *, int,
-                                                      double *, cudaStream_t);
+                                                      double *, cudaStream_t, long, long, long);
 template cudaError_t launch_residual3d<float, float>(const float *, const float *, bool, float *, int,
-                                                     double *, cudaStream_t);
+                                                     double *, cudaStream_t, long, long, long);
 
 }  // namespace mg

@@ -22,105 +22,114 @@
 
 namespace mg {
 
-template <typename T>
-__device__ __forceinline__ T at(const T *a, int n, int x, int y, int z)
+struct Lay {
+    int n, pitch;
+    long plane, off;
+};
+__device__ __forceinline__ long lidx(const Lay &L, int x, int y, int z)
 {
-    if (x < 0 || x >= n || y < 0 || y >= n || z < 0 || z >= n) return T(0);
-    return a[((size_t)z * n + y) * n + x];
+    return L.off + z * L.plane + (long)y * L.pitch + x;
 }
 
 template <typename T>
-__device__ T residual_at(int d, const T *u, const T *bh, int n, int x, int y, int z)
+__device__ __forceinline__ T at(const T *a, const Lay &L, int x, int y, int z)
 {
-    const size_t p = ((size_t)z * n + y) * n + x;
+    if (x < 0 || x >= L.n || y < 0 || y >= L.n || z < 0 || z >= L.n) return T(0);
+    return a[lidx(L, x, y, z)];
+}
+
+template <typename T>
+__device__ T residual_at(int d, const T *u, const T *bh, const Lay &L, int x, int y, int z)
+{
+    const long p = lidx(L, x, y, z);
     if (d == 2) {
-        const T s = radd(radd(at(u, n, x - 1, y, 0), at(u, n, x + 1, y, 0)),
-                         radd(at(u, n, x, y - 1, 0), at(u, n, x, y + 1, 0)));
+        const T s = radd(radd(at(u, L, x - 1, y, 0), at(u, L, x + 1, y, 0)),
+                         radd(at(u, L, x, y - 1, 0), at(u, L, x, y + 1, 0)));
         return radd(rfma(T(-4), u[p], bh[p]), s);
     }
-    const T s = radd(radd(radd(at(u, n, x - 1, y, z), at(u, n, x + 1, y, z)),
-                          radd(at(u, n, x, y - 1, z), at(u, n, x, y + 1, z))),
-                     radd(at(u, n, x, y, z - 1), at(u, n, x, y, z + 1)));
+    const T s = radd(radd(radd(at(u, L, x - 1, y, z), at(u, L, x + 1, y, z)),
+                          radd(at(u, L, x, y - 1, z), at(u, L, x, y + 1, z))),
+                     radd(at(u, L, x, y, z - 1), at(u, L, x, y, z + 1)));
     return radd(rfma(T(-6), u[p], bh[p]), s);
 }
 
 template <typename T>
-__device__ T sweep_at(int d, const T *rh, const T *u, int n, int x, int y, int z, T c0, T c1, T c2)
+__device__ T sweep_at(int d, const T *rh, const T *u, const Lay &L, int x, int y, int z, T c0, T c1, T c2)
 {
-    const size_t p = ((size_t)z * n + y) * n + x;
+    const long p = lidx(L, x, y, z);
     if (d == 2) {
-        const T E = radd(radd(at(rh, n, x - 1, y, 0), at(rh, n, x + 1, y, 0)),
-                         radd(at(rh, n, x, y - 1, 0), at(rh, n, x, y + 1, 0)));
-        const T C = radd(radd(at(rh, n, x - 1, y - 1, 0), at(rh, n, x + 1, y - 1, 0)),
-                         radd(at(rh, n, x - 1, y + 1, 0), at(rh, n, x + 1, y + 1, 0)));
+        const T E = radd(radd(at(rh, L, x - 1, y, 0), at(rh, L, x + 1, y, 0)),
+                         radd(at(rh, L, x, y - 1, 0), at(rh, L, x, y + 1, 0)));
+        const T C = radd(radd(at(rh, L, x - 1, y - 1, 0), at(rh, L, x + 1, y - 1, 0)),
+                         radd(at(rh, L, x - 1, y + 1, 0), at(rh, L, x + 1, y + 1, 0)));
         return rfma(c2, C, rfma(c1, E, rfma(c0, rh[p], u[p])));
     }
-    const T E = radd(radd(radd(at(rh, n, x - 1, y, z), at(rh, n, x + 1, y, z)),
-                          radd(at(rh, n, x, y - 1, z), at(rh, n, x, y + 1, z))),
-                     radd(at(rh, n, x, y, z - 1), at(rh, n, x, y, z + 1)));
+    const T E = radd(radd(radd(at(rh, L, x - 1, y, z), at(rh, L, x + 1, y, z)),
+                          radd(at(rh, L, x, y - 1, z), at(rh, L, x, y + 1, z))),
+                     radd(at(rh, L, x, y, z - 1), at(rh, L, x, y, z + 1)));
     return rfma(c1, E, rfma(c0, rh[p], u[p]));
 }
 
 // full weighting along x of fine row (fy, fz) around fine column 2ic+1
 template <typename T>
-__device__ __forceinline__ T fw_x(const T *rh, int n, int ic, int fy, int fz)
+__device__ __forceinline__ T fw_x(const T *rh, const Lay &L, int ic, int fy, int fz)
 {
-    const T *row = rh + ((size_t)fz * n + fy) * n;
+    const T *row = rh + lidx(L, 0, fy, fz);
     return rfma(T(2), row[2 * ic + 1], radd(row[2 * ic], row[2 * ic + 2]));
 }
 
 template <typename T>
-__device__ T restrict_at(int d, const T *rh, int n, int ic, int jc, int kc)
+__device__ T restrict_at(int d, const T *rh, const Lay &L, int ic, int jc, int kc)
 {
     if (d == 2) {
-        const T t0 = fw_x(rh, n, ic, 2 * jc, 0), t1 = fw_x(rh, n, ic, 2 * jc + 1, 0),
-                t2 = fw_x(rh, n, ic, 2 * jc + 2, 0);
+        const T t0 = fw_x(rh, L, ic, 2 * jc, 0), t1 = fw_x(rh, L, ic, 2 * jc + 1, 0),
+                t2 = fw_x(rh, L, ic, 2 * jc + 2, 0);
         return scale2<-2>(rfma(T(2), t1, radd(t0, t2)));  // 0.25 v
     }
     T tz[3];
     for (int k = 0; k < 3; ++k) {
         const int fz = 2 * kc + k;
-        const T t0 = fw_x(rh, n, ic, 2 * jc, fz), t1 = fw_x(rh, n, ic, 2 * jc + 1, fz),
-                t2 = fw_x(rh, n, ic, 2 * jc + 2, fz);
+        const T t0 = fw_x(rh, L, ic, 2 * jc, fz), t1 = fw_x(rh, L, ic, 2 * jc + 1, fz),
+                t2 = fw_x(rh, L, ic, 2 * jc + 2, fz);
         tz[k] = rfma(T(2), t1, radd(t0, t2));
     }
     return scale2<-4>(rfma(T(2), tz[1], radd(tz[0], tz[2])));  // 0.0625 v
 }
 
-// linear interpolation of the coarse array e (nc points per axis) at fine
-// 0-based coordinates: along x, then y, then z.
+// linear interpolation of the coarse array e at fine 0-based coordinates:
+// along x, then y, then z.
 template <typename T>
-__device__ T interp_x(const T *e, int nc, int fx, int jc, int kc)
+__device__ T interp_x(const T *e, const Lay &Lc, int fx, int jc, int kc)
 {
     // fine 0-based fx = 2k+1 sits on coarse k; fx = 2k lies between k-1 and k
-    if (fx & 1) return at(e, nc, fx >> 1, jc, kc);
+    if (fx & 1) return at(e, Lc, fx >> 1, jc, kc);
     const int k = fx >> 1;
-    return scale2<-1>(radd(at(e, nc, k - 1, jc, kc), at(e, nc, k, jc, kc)));
+    return scale2<-1>(radd(at(e, Lc, k - 1, jc, kc), at(e, Lc, k, jc, kc)));
 }
 
 template <typename T>
-__device__ T interp_xy(const T *e, int nc, int fx, int fy, int kc)
+__device__ T interp_xy(const T *e, const Lay &Lc, int fx, int fy, int kc)
 {
-    if (fy & 1) return interp_x(e, nc, fx, fy >> 1, kc);
+    if (fy & 1) return interp_x(e, Lc, fx, fy >> 1, kc);
     const int m = fy >> 1;
-    return scale2<-1>(radd(interp_x(e, nc, fx, m - 1, kc), interp_x(e, nc, fx, m, kc)));
+    return scale2<-1>(radd(interp_x(e, Lc, fx, m - 1, kc), interp_x(e, Lc, fx, m, kc)));
 }
 
 template <typename T>
-__device__ T interp_at(int d, const T *e, int nc, int fx, int fy, int fz)
+__device__ T interp_at(int d, const T *e, const Lay &Lc, int fx, int fy, int fz)
 {
-    if (d == 2) return interp_xy(e, nc, fx, fy, 0);
-    if (fz & 1) return interp_xy(e, nc, fx, fy, fz >> 1);
+    if (d == 2) return interp_xy(e, Lc, fx, fy, 0);
+    if (fz & 1) return interp_xy(e, Lc, fx, fy, fz >> 1);
     const int q = fz >> 1;
-    return scale2<-1>(radd(interp_xy(e, nc, fx, fy, q - 1), interp_xy(e, nc, fx, fy, q)));
+    return scale2<-1>(radd(interp_xy(e, Lc, fx, fy, q - 1), interp_xy(e, Lc, fx, fy, q)));
 }
 
 template <typename T>
-__device__ void coarse_substitution(int d, const double *lu, const T *bh, T *x)
+__device__ void coarse_substitution(int d, const double *lu, const T *bh, T *x, const Lay &L)
 {
     const int m = d == 2 ? 9 : 27;
     double y[27], xs[27];
-    for (int i = 0; i < m; ++i) y[i] = (double)bh[i];
+    for (int i = 0; i < m; ++i) y[i] = (double)bh[lidx(L, i % 3, (i / 3) % 3, i / 9)];
     for (int i = 0; i < m; ++i)
         for (int k = 0; k < i; ++k) y[i] = __dsub_rn(y[i], __dmul_rn(lu[i * m + k], y[k]));
     for (int i = m - 1; i >= 0; --i) {
@@ -128,7 +137,7 @@ __device__ void coarse_substitution(int d, const double *lu, const T *bh, T *x)
         for (int j = i + 1; j < m; ++j) s = __dsub_rn(s, __dmul_rn(lu[i * m + j], xs[j]));
         xs[i] = __ddiv_rn(s, lu[i * m + i]);
     }
-    for (int i = 0; i < m; ++i) x[i] = (T)xs[i];
+    for (int i = 0; i < m; ++i) x[lidx(L, i % 3, (i / 3) % 3, i / 9)] = (T)xs[i];
 }
 
 template <typename T>
@@ -137,51 +146,63 @@ __device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d
 {
     for (int o = 0; o < nops; ++o) {
         const int kind = ops[o].kind, l = ops[o].level;
-        const TailLevel &L = lv[l];
-        const int n = L.n;
+        const TailLevel &TL = lv[l];
+        const Lay L{TL.n, TL.pitch, TL.plane, TL.off};
+        const int n = TL.n;
         const int np = d == 2 ? n * n : n * n * n;
-        T *u = (T *)L.u, *tmp = (T *)L.tmp, *bh = (T *)L.bh, *rh = (T *)L.rh;
+        T *u = (T *)TL.u, *tmp = (T *)TL.tmp, *bh = (T *)TL.bh, *rh = (T *)TL.rh;
         auto coords = [&](int i, int nn, int &x, int &y, int &z) {
             x = i % nn;
             y = (i / nn) % nn;
             z = d == 2 ? 0 : i / (nn * nn);
         };
         if (kind == TAIL_ZERO) {
-            for (int i = threadIdx.x; i < np; i += blockDim.x) u[i] = T(0);
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                int x, y, z;
+                coords(i, n, x, y, z);
+                u[lidx(L, x, y, z)] = T(0);
+            }
         } else if (kind == TAIL_SWEEP || kind == TAIL_RESTRICT) {
             for (int i = threadIdx.x; i < np; i += blockDim.x) {
                 int x, y, z;
                 coords(i, n, x, y, z);
-                rh[i] = residual_at(d, u, bh, n, x, y, z);
+                rh[lidx(L, x, y, z)] = residual_at(d, u, bh, L, x, y, z);
             }
             __syncthreads();
             if (kind == TAIL_SWEEP) {
                 for (int i = threadIdx.x; i < np; i += blockDim.x) {
                     int x, y, z;
                     coords(i, n, x, y, z);
-                    tmp[i] = sweep_at(d, rh, u, n, x, y, z, c0, c1, c2);
+                    tmp[lidx(L, x, y, z)] = sweep_at(d, rh, u, L, x, y, z, c0, c1, c2);
                 }
                 __syncthreads();
-                for (int i = threadIdx.x; i < np; i += blockDim.x) u[i] = tmp[i];
+                for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                    int x, y, z;
+                    coords(i, n, x, y, z);
+                    u[lidx(L, x, y, z)] = tmp[lidx(L, x, y, z)];
+                }
             } else {
                 const TailLevel &C = lv[l + 1];
+                const Lay Lc{C.n, C.pitch, C.plane, C.off};
                 const int nc = C.n, npc = d == 2 ? nc * nc : nc * nc * nc;
                 T *bc = (T *)C.bh;
                 for (int i = threadIdx.x; i < npc; i += blockDim.x) {
                     int x, y, z;
                     coords(i, nc, x, y, z);
-                    bc[i] = restrict_at(d, rh, n, x, y, z);
+                    bc[lidx(Lc, x, y, z)] = restrict_at(d, rh, L, x, y, z);
                 }
             }
         } else if (kind == TAIL_SOLVE) {
-            if (threadIdx.x == 0) coarse_substitution<T>(d, lu, bh, u);
+            if (threadIdx.x == 0) coarse_substitution<T>(d, lu, bh, u, L);
         } else if (kind == TAIL_PROLONG) {
             const TailLevel &C = lv[l + 1];
+            const Lay Lc{C.n, C.pitch, C.plane, C.off};
             const T *e = (const T *)C.u;
             for (int i = threadIdx.x; i < np; i += blockDim.x) {
                 int x, y, z;
                 coords(i, n, x, y, z);
-                u[i] = radd(u[i], interp_at(d, e, C.n, x, y, z));
+                const long p = lidx(L, x, y, z);
+                u[p] = radd(u[p], interp_at(d, e, Lc, x, y, z));
             }
         }
         __syncthreads();
