@@ -195,16 +195,18 @@ def make_workload(name, torch):
             u.zero_()
             return s.solve(b, u, tol=TOL, max_cycles=100).cycles
         return step, (n_ - 1) ** 2, f"2D N={n_} {prec} V(1,1) M9 to 1e-10", s.close
-    if name in ("3d512-fp64", "3d512-mixed"):
+    if name.startswith("3d") and name.endswith(("-fp64", "-mixed")):
+        # 3d512-*: the rows; smaller sizes (3d256-mixed, ...) serve profiling
+        n_ = int(name[2:name.index("-")])
         prec = "fp32_ir" if name.endswith("mixed") else "fp64"
-        b = torch.from_numpy(inputs.uniform(3, 512, SEED)).cuda()
+        b = torch.from_numpy(inputs.uniform(3, n_, SEED)).cuda()
         u = torch.zeros_like(b)
-        s = Solver(3, 512, smoothers.M7, nu1=2, nu2=2, precision=prec)
+        s = Solver(3, n_, smoothers.M7, nu1=2, nu2=2, precision=prec)
 
         def step():
             u.zero_()
             return s.solve(b, u, tol=TOL, max_cycles=100).cycles
-        return step, 511 ** 3, f"3D N=512 {prec} V(2,2) M7 to 1e-10", s.close
+        return step, (n_ - 1) ** 3, f"3D N={n_} {prec} V(2,2) M7 to 1e-10", s.close
     if name == "batch256":
         Ns = [int(x) for x in inputs.batch_sizes(256, 0)]
         bs = [torch.from_numpy(b).cuda() for b in inputs.batch_rhs(Ns, 1)]
@@ -415,7 +417,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--workload", default="2d8192", choices=["2d8192"] + ROWS,
+    ap.add_argument("--workload", default="2d8192", choices=["2d8192"] + ROWS + ["3d256-mixed", "3d256-fp64"],
                     help="with --only-solve: which workload to time (profiling)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, kernel, mixed or CPU legs); used for profiler launch lists")

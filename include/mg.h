@@ -170,6 +170,16 @@ mg_status mg_op_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int
 mg_status mg_op_residual(int d, int n, mg_prec prec, const void *u, const void *bh, int b_unscaled,
                          void *rh_out, void *stream);
 
+/* The outer step of the FP32-in-FP64 refinement: the scaled residual
+ * rh = bh - h^2 A u (Sec. 1, Eq. (1.3)) of FP64 u and bh, evaluated in FP64
+ * in the order of mg_op_residual and rounded once to FP32 (round to nearest,
+ * ties to even) into rh32_out, the right-hand side of the FP32 cycle. u, bh:
+ * double, rh32_out: float, all device arrays of n^d points (interior
+ * layout). If rnorm2_out (HOST) is non-NULL it receives sum(rh^2) of the
+ * FP64 residual, summed in FP64; this synchronises. */
+mg_status mg_op_residual_refine(int d, int n, const double *u, const double *bh, int b_unscaled, float *rh32_out,
+                                double *rnorm2_out, void *stream);
+
 /* Coarse right-hand side bh_c = 4 R (bh - h^2 A u), full weighting R
  * (Sec. 4); bh_c has ((n-1)/2)^d points. */
 mg_status mg_op_residual_restrict(int d, int n, mg_prec prec, const void *u, const void *bh, int b_unscaled,

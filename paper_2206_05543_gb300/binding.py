@@ -36,6 +36,7 @@ SIGNATURES = {
     "mg_destroy": (None, [_P]),
     "mg_op_sweep": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _DP, _P]),
     "mg_op_residual": (_I, [_I, _I, _I, _P, _P, _I, _P, _P]),
+    "mg_op_residual_refine": (_I, [_I, _I, _P, _P, _I, _P, _P, _P]),
     "mg_op_residual_restrict": (_I, [_I, _I, _I, _P, _P, _I, _P, _P]),
     "mg_op_prolong_correct": (_I, [_I, _I, _I, _P, _P, _P]),
     "mg_op_coarse_solve": (_I, [_I, _I, _P, _P, _P]),
@@ -336,6 +337,23 @@ def op_residual(u, bh, b_unscaled: bool = False, stream=None):
                                 _dev_ptr(bh, bh.dtype, bh.shape, "bh"), int(b_unscaled),
                                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "mg_op_residual")
     return out
+
+
+def op_residual_refine(u, bh, b_unscaled: bool = False, want_norm: bool = False, stream=None):
+    """Outer refinement residual: FP64 u, bh -> FP32 rh (one rounding) and,
+    if want_norm, sum(rh^2) of the FP64 residual. Returns (rh32, norm2|None)."""
+    torch = _torch()
+    d, n = _level(bh)
+    if bh.dtype != torch.float64:
+        raise TypeError("op_residual_refine takes float64 u and bh")
+    out = torch.empty(bh.shape, dtype=torch.float32, device=bh.device)
+    nrm = ctypes.c_double(0.0)
+    _check(lib().mg_op_residual_refine(d, n, _dev_ptr(u, bh.dtype, bh.shape, "u"),
+                                       _dev_ptr(bh, bh.dtype, bh.shape, "bh"), int(b_unscaled),
+                                       ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.byref(nrm) if want_norm else None, _stream_ptr(stream)),
+           "mg_op_residual_refine")
+    return out, (nrm.value if want_norm else None)
 
 
 def op_residual_restrict(u, bh, b_unscaled: bool = False, stream=None):

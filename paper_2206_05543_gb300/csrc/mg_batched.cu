@@ -77,7 +77,7 @@ __global__ void batched_update(const UpdItem *__restrict__ tab, const int *__res
     for (int y = y0; y < y1; ++y) {
         double *ur = it.u + (long long)y * it.n;
         const float *er = it.e + it.off + (long long)y * it.pitch;
-        for (int x = threadIdx.x; x < it.n; x += blockDim.x) ur[x] = __dadd_rn(ur[x], (double)er[x]);
+        for (int x = threadIdx.x; x < it.n; x += blockDim.x) ur[x] = __dadd_rn(ur[x], widen(er[x]));
     }
 }
 

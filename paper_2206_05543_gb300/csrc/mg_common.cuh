@@ -21,6 +21,53 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// IEEE 754 binary64 -> binary32 conversion, round to nearest, ties to even,
+// on the integer pipe: for results in the normal binary32 range the 23 kept
+// fraction bits are the top of the 52, and the 29 dropped bits decide the
+// rounding (above half: up; exactly half: up when the kept part is odd); a
+// carry out of the fraction moves into the exponent, which is the correct
+// result, including the overflow to infinity. Zeros, results that would be
+// subnormal, NaNs and infinities take the hardware conversion. Equal to
+// __double2float_rn bit for bit; on this part the hardware conversion issues
+// on the FP64 pipe, which the FP64 residual kernels saturate.
+__device__ __forceinline__ float narrow_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned e = (hi >> 20) & 0x7ffu;  // biased binary64 exponent
+    if (e - 897u > 253u) return __double2float_rn(x);  // binary32 exponent outside 1..254
+    const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    unsigned r = (hi & 0x80000000u) | ((e - 896u) << 23) | frac;
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
+    return __uint_as_float(r);
+}
+// IEEE 754 binary32 -> binary64 conversion (exact) on the integer pipe:
+// for normal inputs the exponent is rebiased (+896) and the 23 fraction bits
+// move to the top of the 52; zeros, subnormals, infinities and NaNs take the
+// hardware conversion, which on this part issues on the FP64 pipe.
+__device__ __forceinline__ double widen(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e - 1u > 253u) return (double)x;
+    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
+                                            ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// value of an InT result stored as OutT (conversions round to nearest even)
+template <typename OutT, typename InT>
+__device__ __forceinline__ OutT to_out(InT x)
+{
+    if constexpr (sizeof(OutT) < sizeof(InT))
+        return narrow_rn(x);
+    else if constexpr (sizeof(OutT) > sizeof(InT))
+        return widen(x);
+    else
+        return x;
+}
+
 // x * 2^k for a power-of-two scale, done on the exponent field with integer
 // instructions when x and the result are normal numbers (then the product is
 // exact, so the result equals __dmul_rn(x, 2^k) bit for bit); zeros,

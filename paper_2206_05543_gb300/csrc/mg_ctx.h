@@ -44,8 +44,12 @@ struct mg_ctx {
     double *lu = nullptr;
     double *partials = nullptr;
     int npartials = 0;
+    // d_norm2[0]: squared norm of the last residual; the word after it
+    // (d_err) is set by a kernel whose bounded device-side wait gave up. Both
+    // reach the host together (kNormBytes) in pinned h_norm2.
     double *d_norm2 = nullptr;
     double *h_norm2 = nullptr;  // pinned
+    int *d_err = nullptr;
     GraphPair g;
     const void *cap_u = nullptr, *cap_b = nullptr;
     std::vector<void *> owned;  // device allocations to free
@@ -55,6 +59,7 @@ struct mg_ctx {
 
 
 namespace mg {
+constexpr size_t kNormBytes = 2 * sizeof(double);
 mg_status cuda_fail(cudaError_t e);
 void free_adjoint(mg_ctx *c);
 void free_batch(mg_ctx *c);

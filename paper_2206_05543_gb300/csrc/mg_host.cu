@@ -88,7 +88,7 @@ template <typename T>
 __global__ void add_to_f64_kernel(double *__restrict__ u, const T *__restrict__ e, size_t np)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < np; i += (size_t)gridDim.x * blockDim.x)
-        u[i] = __dadd_rn(u[i], (double)e[i]);
+        u[i] = __dadd_rn(u[i], to_out<double>(e[i]));
 }
 
 template <typename T>
@@ -108,7 +108,7 @@ __global__ void add_pl2d_kernel(double *__restrict__ u, const float *__restrict_
         double *ur = u + (long)y * n;
         const float *er = e + g.off + (long)y * g.pitch;
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
-            ur[x] = __dadd_rn(ur[x], (double)er[x]);
+            ur[x] = __dadd_rn(ur[x], widen(er[x]));
     }
 }
 
@@ -279,7 +279,7 @@ struct Recorder {
     {
         if (pl() && c->d == 2)
             return launch_sweep2d_pl((const float *)u, (const float *)b, (float *)out, n, c->c, nullptr, c->s);
-        if (pl()) return launch_sweep3d_pl((const float *)u, (const float *)b, (float *)out, nullptr, n, c->c, c->s);
+        if (pl()) return launch_sweep3d_tma((const float *)u, (const float *)b, (float *)out, n, c->c, c->d_err, c->s);
         return op_sweep<T>(c->d, u, b, unsc, out, n, c->c, nullptr, c->s);
     }
     cudaError_t resrestrict(const T *u, const T *b, bool unsc, T *bc, int n)
@@ -442,7 +442,7 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
             if (e) return e;
             const int np = fused ? sweep_partials(d, n0) : residual_partials(d, n0);
             if ((e = launch_sum_partials(c->partials, np, c->d_norm2, c->s))) return e;
-            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, c->s);
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t { return R.visit(0, false, fused); });
@@ -484,7 +484,7 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
             }
             if (e) return e;
             if ((e = launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s))) return e;
-            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, c->s);
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
@@ -528,6 +528,14 @@ static mg_status launch_graph(mg_ctx *c, cudaGraphExec_t g, unsigned long long n
 static double norm_from_host(mg_ctx *c)
 {
     return std::sqrt(*c->h_norm2) * (double)c->N * (double)c->N;
+}
+
+// a kernel of an earlier replay gave up on a bounded wait (sticky)
+static bool timed_out(const mg_ctx *c)
+{
+    int e;
+    std::memcpy(&e, c->h_norm2 + 1, sizeof e);
+    return e != 0;
 }
 
 static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int nu1, int nu2, int gamma,
@@ -603,7 +611,9 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
         int np = std::max(sweep_partials(d, c->n[0]), residual_partials(d, c->n[0]));
         c->npartials = np;
         MG_TRY(dalloc(c, (void **)&c->partials, (size_t)np * sizeof(double)));
-        MG_TRY(dalloc(c, (void **)&c->d_norm2, sizeof(double)));
+        MG_TRY(dalloc(c, (void **)&c->d_norm2, kNormBytes));
+        MG_TRYC(cudaMemset(c->d_norm2, 0, kNormBytes));
+        c->d_err = (int *)(c->d_norm2 + 1);
         MG_TRY(dalloc(c, (void **)&c->lu, 27 * 27 * sizeof(double)));
         {
             double lu[27 * 27];
@@ -611,7 +621,7 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
             const int m = d == 2 ? 9 : 27;
             MG_TRYC(cudaMemcpy(c->lu, lu, (size_t)m * m * sizeof(double), cudaMemcpyHostToDevice));
         }
-        MG_TRYC(cudaMallocHost((void **)&c->h_norm2, sizeof(double)));
+        MG_TRYC(cudaMallocHost((void **)&c->h_norm2, kNormBytes));
     }
     *out = c;
     return MG_OK;
@@ -668,17 +678,23 @@ static mg_status op_sweep_pl(int d, int n, const double *c, const void *u, const
     float *pu = u ? tmp.make(n, u, s, e) : nullptr;
     float *pb = tmp.make(n, bh, s, e), *po = tmp.make(n, nullptr, s, e);
     double *partials = nullptr;
+    int *err = nullptr, h_err = 0;
     const int np = d == 2 ? sweep2d_pl_blocks(n, sweep2d_pl_H(n)) : 0;
     if (!e && rnorm2) e = cudaMalloc(&partials, (size_t)(np + 1) * sizeof(double));
-    if (!e) e = d == 2 ? launch_sweep2d_pl(pu, pb, po, n, c, partials, s) : launch_sweep3d_pl(pu, pb, po, nullptr, n, c, s);
+    if (!e && d == 3) e = cudaMalloc(&err, sizeof(int));
+    if (!e && d == 3) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (!e) e = d == 2 ? launch_sweep2d_pl(pu, pb, po, n, c, partials, s) : launch_sweep3d_tma(pu, pb, po, n, c, err, s);
     if (!e) e = tmp.pack(po, (float *)out, n, false, s);
     if (!e && rnorm2) {
         e = launch_sum_partials(partials, np, partials + np, s);
         if (!e) e = cudaMemcpyAsync(rnorm2, partials + np, sizeof(double), cudaMemcpyDeviceToHost, s);
     }
+    if (!e && err) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (partials) cudaFree(partials);
-    return e ? cuda_fail(e) : MG_OK;
+    if (err) cudaFree(err);
+    if (e) return cuda_fail(e);
+    return h_err ? MG_ETIMEOUT : MG_OK;
 }
 
 template <typename T>
@@ -749,6 +765,7 @@ mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycl
     if ((st = record(ctx, u, b)) != MG_OK) return st;
     if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
     if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    if (timed_out(ctx)) return MG_ETIMEOUT;
     const double r0 = norm_from_host(ctx);
     double rk = r0;
     int k = 0;
@@ -763,6 +780,7 @@ mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycl
         if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
         if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
         ++k;
+        if (timed_out(ctx)) return MG_ETIMEOUT;
         rk = norm_from_host(ctx);
         if (hist_out) hist_out[k] = rk;
         if (!std::isfinite(rk)) st = MG_ENAN;
@@ -798,9 +816,10 @@ mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *no
                         : op_residual<double, double>(ctx->d, (const double *)u, (const double *)b, true,
                                                       (double *)nullptr, n0, ctx->partials, ctx->s);
     if (!e) e = launch_sum_partials(ctx->partials, residual_partials(ctx->d, n0), ctx->d_norm2, ctx->s);
-    if (!e) e = cudaMemcpyAsync(ctx->h_norm2, ctx->d_norm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+    if (!e) e = cudaMemcpyAsync(ctx->h_norm2, ctx->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, ctx->s);
     if (!e) e = cudaStreamSynchronize(ctx->s);
     if (e) return cuda_fail(e);
+    if (timed_out(ctx)) return MG_ETIMEOUT;
     *norm_out = norm_from_host(ctx);
     return leave(ctx);
 }
@@ -832,6 +851,25 @@ mg_status mg_op_residual(int d, int n, mg_prec prec, const void *u, const void *
                                       nullptr, (cudaStream_t)stream);
     else
         return MG_EINVAL;
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+mg_status mg_op_residual_refine(int d, int n, const double *u, const double *bh, int b_unscaled, float *rh32_out,
+                                double *rnorm2_out, void *stream)
+{
+    if (!valid_level(d, n) || !u || !bh || !rh32_out) return MG_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    double *partials = nullptr;
+    const int np = residual_partials(d, n);
+    cudaError_t e = cudaSuccess;
+    if (rnorm2_out) e = cudaMalloc(&partials, (size_t)(np + 1) * sizeof(double));
+    if (!e) e = op_residual<double, float>(d, u, bh, b_unscaled != 0, rh32_out, n, partials, s);
+    if (!e && rnorm2_out) {
+        e = launch_sum_partials(partials, np, partials + np, s);
+        if (!e) e = cudaMemcpyAsync(rnorm2_out, partials + np, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+    }
+    if (partials) cudaFree(partials);
     return e ? cuda_fail(e) : MG_OK;
 }
 

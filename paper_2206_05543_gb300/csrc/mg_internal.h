@@ -124,9 +124,10 @@ struct Pitch3 {
 };
 Pitch3 pitch3(int n);
 size_t pitch3_floats(int n);
-// u == nullptr: zero start; u64 != nullptr: refinement epilogue u64 += result
-cudaError_t launch_sweep3d_pl(const float *u, const float *b, float *out, double *u64, int n, const double *c,
-                              cudaStream_t s);
+// SPAI sweep with TMA-staged tiles; u == nullptr: zero start. A copy that
+// does not land within about a second sets *err (device int) to nonzero.
+cudaError_t launch_sweep3d_tma(const float *u, const float *b, float *out, int n, const double *c, int *err,
+                               cudaStream_t s);
 cudaError_t launch_resrestrict3d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s);
 cudaError_t launch_prolong3d_pl(const float *e, float *u, int n, cudaStream_t s);
 cudaError_t launch_pack3d(const float *in, float *out, int n, bool to_padded, cudaStream_t s);

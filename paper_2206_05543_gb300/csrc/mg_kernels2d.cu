@@ -77,7 +77,7 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
             r = bb;
         }
         if (!(xin && j >= 0 && j < n)) r = T(0);
-        if (NORM && owner && j >= y0 && j < y1) acc = fma((double)r, (double)r, acc);
+        if (NORM && owner && j >= y0 && j < y1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
         sr[buf][t] = r;
         __syncthreads();
         const T hp = (t >= 1 && t <= kSweepCols) ? radd(sr[buf][t - 1], sr[buf][t + 1]) : T(0);
@@ -273,8 +273,8 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
             InT bb = b[(size_t)j * ld + x];
             if (unscaled) bb = scale2(bb, hk);
             const InT r = radd(rfma(InT(-4), u_cur, bb), s);
-            acc = fma((double)r, (double)r, acc);
-            if (rh_out) rh_out[opitch ? ooff + j * opitch + x : (long)j * ld + x] = (OutT)r;
+            acc = fma(to_out<double>(r), to_out<double>(r), acc);
+            if (rh_out) rh_out[opitch ? ooff + j * opitch + x : (long)j * ld + x] = to_out<OutT>(r);
         }
         u_prev = u_cur;
         u_cur = u_next;

@@ -101,7 +101,7 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
                 r = bb;
             }
             if (!(inside[k] && zz >= 0 && zz < n)) r = T(0);
-            if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma((double)r, (double)r, acc);
+            if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
             r_new[k] = r;
             sr[(zz + 3) % 3][j * kS3 + i] = r;
         }
@@ -288,8 +288,8 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
             InT bb = b[p];
             if (unscaled) bb = scale2(bb, hk);
             const InT r = radd(rfma(InT(-6), u_cur, bb), s);
-            acc = fma((double)r, (double)r, acc);
-            if (rh_out) rh_out[opitch ? ooff + z * oplane + (long)y * opitch + x : (long)p] = (OutT)r;
+            acc = fma(to_out<double>(r), to_out<double>(r), acc);
+            if (rh_out) rh_out[opitch ? ooff + z * oplane + (long)y * opitch + x : (long)p] = to_out<OutT>(r);
             u_prev = u_cur;
             u_cur = u_next;
         }

@@ -108,7 +108,7 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
             if (!(jin && x + k < n)) c4(r, k) = 0.f;
         if ((lt || rt) && !(jin && xh >= 0 && xh < n)) rh = 0.f;
         if (NORM && j >= y0 && j < y1)
-            for (int k = 0; k < 4; ++k) acc = fma((double)c4(r, k), (double)c4(r, k), acc);
+            for (int k = 0; k < 4; ++k) acc = fma(widen(c4(r, k)), widen(c4(r, k)), acc);
         st4(&sr[buf][4 + 4 * t], r);
         if (lt) sr[buf][3] = rh;
         if (rt) sr[buf][kPLCols + 4] = rh;
@@ -131,7 +131,7 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
                 // caller's FP64 solution (compact rows of n doubles)
                 double *ur = u64 + (long)(j - 1) * n + x;
                 for (int k = 0; k < 4; ++k)
-                    if (x + k < n) ur[k] = __dadd_rn(ur[k], (double)c4(o, k));
+                    if (x + k < n) ur[k] = __dadd_rn(ur[k], widen(c4(o, k)));
             } else if (x < n) {
                 st4_valid(O + (long)(j - 1) * P + x, o, x, n);
             }

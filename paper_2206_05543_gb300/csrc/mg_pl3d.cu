@@ -11,143 +11,14 @@
 
 namespace mg {
 
-constexpr int kP3TX = 32;                 // threads along x (4 columns each)
-constexpr int kP3Cols = 4 * kP3TX;        // 128 columns per tile
-constexpr int kP3TY = 14;                 // output rows per tile
-constexpr int kP3Rows = kP3TY + 2;        // residual rows per tile (with halo)
-constexpr int kP3Threads = kP3TX * kP3Rows;  // 512
-constexpr int kP3W = kP3Cols + 8;         // shared row width (4 halo columns each side)
+// x strips of the sweep (mg_tma3d.cu): 128 columns each; rows are padded to
+// whole strips plus the 4-column margins its tiles read on both sides
+constexpr int kP3Cols = 128;
 
 __device__ __forceinline__ float4 ld4g(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4g(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float &e4(float4 &v, int k) { return (&v.x)[k]; }
 __device__ __forceinline__ float ce4(const float4 &v, int k) { return (&v.x)[k]; }
-
-// ---------------------------------------------------------------------------
-// SPAI sweep (formula as sweep3d_kernel): the block computes the residual on
-// 128 columns x 16 rows (output 128 x 14) per plane, marching over z.
-// ACC64: the refinement epilogue, u64 (compact FP64) += result.
-// ---------------------------------------------------------------------------
-template <bool ZERO_U, bool ACC64>
-__global__ void __launch_bounds__(kP3Threads)
-sweep3d_pl_kernel(const float *__restrict__ u, const float *__restrict__ b, float *__restrict__ out,
-                  double *__restrict__ u64, Pitch3 g, int Z, float c0, float c1)
-{
-    __shared__ __align__(16) float su[2][kP3Rows + 2][kP3W];
-    __shared__ __align__(16) float sr[3][kP3Rows][kP3W];
-    const int n = g.n;
-    const int tx = threadIdx.x % kP3TX, ty = threadIdx.x / kP3TX;
-    const int x0 = blockIdx.x * kP3Cols, y0 = blockIdx.y * kP3TY;
-    const int x = x0 + 4 * tx, yr = y0 - 1 + ty;
-    const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
-    const float *U = u + g.off, *Bp = b + g.off;
-    const long P = g.pitch, S = g.plane;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto ok = [&](int y, int z) { return y >= -1 && y <= n && z >= -1 && z <= n; };
-    auto at4 = [&](const float *a, int xx, int y, int z) { return ok(y, z) ? ld4g(a + z * S + y * P + xx) : z4; };
-    auto at1 = [&](const float *a, int xx, int y, int z) { return ok(y, z) ? a[z * S + y * P + xx] : 0.f; };
-    const bool lt = tx == 0, rt = tx == kP3TX - 1;
-    const int xh = lt ? x0 - 1 : x0 + kP3Cols;  // halo column of the edge threads
-    const bool yin = yr >= 0 && yr < n;
-    const bool own_row = ty >= 1 && ty <= kP3TY && yin;
-
-    float4 um = z4, uc = z4, un = z4, rm = z4, rc = z4, bn;
-    float hm = 0.f, hc = 0.f, hn = 0.f, hb, rhm = 0.f, rhc = 0.f;
-    if (!ZERO_U) {
-        um = at4(U, x, yr, z0 - 2);
-        uc = at4(U, x, yr, z0 - 1);
-        if (lt || rt) {
-            hm = at1(U, xh, yr, z0 - 2);
-            hc = at1(U, xh, yr, z0 - 1);
-        }
-    }
-    bn = at4(Bp, x, yr, z0 - 1);
-    hb = (lt || rt) ? at1(Bp, xh, yr, z0 - 1) : 0.f;
-    (void)rhm;
-    (void)rhc;
-    for (int zz = z0 - 1; zz <= z1; ++zz) {
-        const int buf = zz & 1;
-        const float4 bc = bn;
-        const float hbc = hb;
-        bn = at4(Bp, x, yr, zz + 1);
-        if (lt || rt) hb = at1(Bp, xh, yr, zz + 1);
-        const bool zin = zz >= 0 && zz < n;
-        float4 r;
-        float rh = 0.f;
-        if (!ZERO_U) {
-            un = at4(U, x, yr, zz + 1);
-            if (lt || rt) hn = at1(U, xh, yr, zz + 1);
-            float(*s)[kP3W] = su[buf];
-            st4g(&s[ty + 1][4 + 4 * tx], uc);
-            if (lt) st4g(&s[ty + 1][0], at4(U, x0 - 4, yr, zz));
-            if (rt) st4g(&s[ty + 1][kP3Cols + 4], at4(U, x0 + kP3Cols, yr, zz));
-            if (ty == 0 || ty == kP3Rows - 1) {  // the two extra rows y0 - 2 and y0 + 15
-                const int er = ty == 0 ? 0 : kP3Rows + 1, ey = ty == 0 ? y0 - 2 : y0 + kP3Rows - 1;
-                st4g(&s[er][4 + 4 * tx], at4(U, x, ey, zz));
-                if (lt) st4g(&s[er][0], at4(U, x0 - 4, ey, zz));
-                if (rt) st4g(&s[er][kP3Cols + 4], at4(U, x0 + kP3Cols, ey, zz));
-            }
-            __syncthreads();
-            const float *row = &s[ty + 1][4 + 4 * tx], *rs = &s[ty][4 + 4 * tx], *rn = &s[ty + 2][4 + 4 * tx];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float ss = radd(radd(radd(row[k - 1], row[k + 1]), radd(rs[k], rn[k])), radd(e4(um, k), e4(un, k)));
-                e4(r, k) = radd(rfma(-6.f, e4(uc, k), ce4(bc, k)), ss);
-            }
-            if (lt || rt) {
-                const int c = lt ? 3 : kP3Cols + 4;
-                const float ss = radd(radd(radd(s[ty + 1][c - 1], s[ty + 1][c + 1]), radd(s[ty][c], s[ty + 2][c])),
-                                      radd(hm, hn));
-                rh = radd(rfma(-6.f, hc, hbc), ss);
-            }
-        } else {
-            r = bc;
-            rh = hbc;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (!(zin && yin && x + k < n)) e4(r, k) = 0.f;
-        if ((lt || rt) && !(zin && yin && xh >= 0 && xh < n)) rh = 0.f;
-        float(*q)[kP3W] = sr[(zz + 3) % 3];
-        st4g(&q[ty][4 + 4 * tx], r);
-        if (lt) q[ty][3] = rh;
-        if (rt) q[ty][kP3Cols + 4] = rh;
-        __syncthreads();
-        if (zz - 1 >= z0 && own_row) {
-            float(*p)[kP3W] = sr[(zz + 2) % 3];  // plane zz - 1
-            const float *row = &p[ty][4 + 4 * tx], *rs = &p[ty - 1][4 + 4 * tx], *rn = &p[ty + 1][4 + 4 * tx];
-            float4 o;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float E = radd(radd(radd(row[k - 1], row[k + 1]), radd(rs[k], rn[k])), radd(e4(rm, k), e4(r, k)));
-                const float base = ZERO_U ? rmul(c0, e4(rc, k)) : rfma(c0, e4(rc, k), e4(um, k));
-                e4(o, k) = rfma(c1, E, base);
-            }
-            if (ACC64) {
-                double *ur = u64 + ((long)(zz - 1) * n + yr) * n + x;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (x + k < n) ur[k] = __dadd_rn(ur[k], (double)e4(o, k));
-            } else {
-                float *dst = out + g.off + (long)(zz - 1) * S + (long)yr * P + x;
-                if (x + 3 < n) {
-                    st4g(dst, o);
-                } else {
-                    for (int k = 0; k < 4; ++k)
-                        if (x + k < n) dst[k] = e4(o, k);
-                }
-            }
-        }
-        rm = rc;
-        rc = r;
-        if (!ZERO_U) {
-            um = uc;
-            uc = un;
-            hm = hc;
-            hc = hn;
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Residual + full weighting (formula as resrestrict3d_kernel): 16 x 16 coarse
@@ -307,7 +178,7 @@ __global__ void add_pl3d_kernel(double *__restrict__ u, const float *__restrict_
         double *ur = u + r * n;
         const float *er = e + g.off + z * g.plane + y * g.pitch;
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
-            ur[x] = __dadd_rn(ur[x], (double)er[x]);
+            ur[x] = __dadd_rn(ur[x], widen(er[x]));
     }
 }
 
@@ -330,24 +201,6 @@ size_t pitch3_floats(int n)
 {
     const Pitch3 g = pitch3(n);
     return (size_t)(n + 2) * g.plane + 64;
-}
-
-cudaError_t launch_sweep3d_pl(const float *u, const float *b, float *out, double *u64, int n, const double *c,
-                              cudaStream_t s)
-{
-    const Pitch3 g = pitch3(n);
-    const int bx = (n + kP3Cols - 1) / kP3Cols, by = (n + kP3TY - 1) / kP3TY;
-    const int Z = chunk_rows(bx * by, n, 3 * num_sms(), 4, 128);
-    const dim3 grid(bx, by, (n + Z - 1) / Z);
-    const float c0 = (float)c[0], c1 = (float)c[1];
-    if (u64)
-        sweep3d_pl_kernel<false, true><<<grid, kP3Threads, 0, s>>>(u, b, nullptr, u64, g, Z, c0, c1);
-    else if (u)
-        sweep3d_pl_kernel<false, false><<<grid, kP3Threads, 0, s>>>(u, b, out, nullptr, g, Z, c0, c1);
-    else
-        sweep3d_pl_kernel<true, false><<<grid, kP3Threads, 0, s>>>(u, b, out, nullptr, g, Z, c0, c1);
-    count_launch(1);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_resrestrict3d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s)

@@ -1,0 +1,344 @@
+// mg_tma3d.cu -- 3D FP32 SPAI sweep with TMA-staged planes (padded layout).
+//
+// A z-marching 3D sweep in which every thread loads its own u and b values
+// keeps too few bytes in flight to cover HBM latency. Here one thread issues
+// tensor-memory-accelerator copies (cp.async.bulk.tensor, completion counted
+// by mbarriers) of whole u and b tiles (halo included) into rings of shared
+// memory slots kAhead planes ahead of the computation, so the copy engine
+// keeps HBM busy while the block computes. Out-of-range rows and planes of a
+// box are filled with zeros by the hardware: the Dirichlet ghost value.
+//
+// Per plane zz a block
+//   A. forms the scaled residual of plane zz (u planes zz-1..zz+1, b plane zz)
+//      and stores it in a two-plane shared ring,
+//   B. synchronises (u plane zz-1 and b plane zz are dead from here on),
+//   C. refills those two slots with copies of planes kAhead+1 further on,
+//   D. applies the SPAI stencil to the residual of plane zz-1 and writes it,
+//   E. waits for the planes the next step reads, and synchronises.
+// Every wait is bounded by a clock limit; on expiry the block sets an error
+// word (the host reports MG_ETIMEOUT), waits, again bounded, for its copies
+// still in flight, and returns.
+//
+// Formula and rounding order: those of the compact 3D sweep (Sec. 3.2,
+// u' = u + c0 r + c1 (sum of the six face neighbours of r)), so results are
+// bit-identical to it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+namespace {
+
+constexpr int kTX = 32;                   // threads along x, 4 columns each
+constexpr int kTCols = 4 * kTX;           // 128 output columns
+constexpr int kTTY = 14;                  // output rows
+constexpr int kTRows = kTTY + 2;          // residual rows (16)
+constexpr int kTThreads = kTX * kTRows;   // 512 consumer threads (+ one helper warp)
+constexpr int kTW = kTCols + 8;           // tile width: 4 extra columns each side (136)
+constexpr int kURows = kTRows + 2;        // u rows (18)
+constexpr int kAhead = 2;                 // planes of prefetch beyond the next step
+constexpr int kUSlots = 3 + kAhead, kBSlots = 1 + kAhead;
+constexpr int kUBoxBytes = kURows * kTW * 4, kBBoxBytes = kTRows * kTW * 4;
+constexpr int kUSlotBytes = (kUBoxBytes + 127) / 128 * 128;
+constexpr int kBSlotBytes = (kBBoxBytes + 127) / 128 * 128;
+constexpr int kRSlotBytes = kBSlotBytes;  // residual plane: kTRows x kTW
+constexpr int kSmemBytes = kUSlots * kUSlotBytes + kBSlots * kBSlotBytes + 2 * kRSlotBytes + 128;
+constexpr long long kWaitCycles = 1LL << 31;  // about one second
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ float4 ld4s(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float &f4(float4 &v, int k) { return (&v.x)[k]; }
+__device__ __forceinline__ float cf4(const float4 &v, int k) { return (&v.x)[k]; }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// false when the phase did not complete within kWaitCycles
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// The tensor maps view a padded level array (see pitch3) as a pitch x (n+2) x
+// (n+2) box starting at element (-4, -1, -1): element (x, y, z) has tensor
+// coordinates (x + 4, y + 1, z + 1). A u tile of block (x0, y0) covers
+// columns x0-4 .. x0+131 and rows y0-2 .. y0+15; a b tile rows y0-1 .. y0+14.
+//
+// Warps 0..15 (consumers) own residual row ty = warp, four columns per lane.
+// Warp 16 (helper) computes the 32 residuals of the two halo columns
+// (lane & 15 = row, lane >> 4 = side), and its lane 0 drives the copies.
+template <bool ZERO_U>
+__global__ void __launch_bounds__(kTThreads + 32, 2)
+sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant__ CUtensorMap tb,
+                   float *__restrict__ out, Pitch3 g, int Z, float c0, float c1, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte alignment by indexing (not by integer casts), so that the
+    // compiler still sees shared-memory pointers
+    unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float *const su = (float *)base;
+    float *const sb = (float *)(base + kUSlots * kUSlotBytes);
+    float *const sr = (float *)(base + kUSlots * kUSlotBytes + kBSlots * kBSlotBytes);
+    __shared__ __align__(8) unsigned long long bars[kUSlots + kBSlots];
+    __shared__ int s_fail;
+    constexpr int kUF = kUSlotBytes / 4, kBF = kBSlotBytes / 4, kRF = kRSlotBytes / 4;
+
+    const int n = g.n, t = threadIdx.x;
+    const bool helper = t >= kTThreads;
+    const int x0 = blockIdx.x * kTCols, y0 = blockIdx.y * kTTY;
+    const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
+    // consumer: row ty, columns x..x+3; helper: row ty, halo column x
+    const int lane = t & 31;
+    const int ty = helper ? (lane & 15) : t / kTX;
+    const int tx = helper ? 0 : t % kTX;
+    const int yr = y0 - 1 + ty;
+    const bool yin = yr >= 0 && yr < n;
+    const int x = helper ? ((lane >> 4) ? x0 + kTCols : x0 - 1) : x0 + 4 * tx;
+    const int col = helper ? ((lane >> 4) ? kTCols + 4 : 3) : 4 + 4 * tx;  // tile column of x
+    const int ib = ty * kTW + col;        // in a b / residual tile
+    const int iu = (ty + 1) * kTW + col;  // in a u tile
+    unsigned xmask = 0;                   // bit k: column x + k is an interior point of row yr
+    for (int k = 0; k < (helper ? 1 : 4); ++k)
+        if (yin && x + k >= 0 && x + k < n) xmask |= 1u << k;
+    const bool own_row = !helper && ty >= 1 && ty <= kTTY && yin;
+    const bool producer = helper && lane == 0;
+
+    // ring offsets (floats) of u planes zz-1, zz, zz+1 and of b plane zz;
+    // plane p sits in slot (p - first) % slots, its k-th fill has parity k & 1
+    const int ufirst = z0 - 2, bfirst = z0 - 1, ulast = z1 + 1, blast = z1;
+    int om = 0, oc = kUF, op = 2 * kUF, ob = 0;
+    auto ubar = [&](int p) { return smem_u32(&bars[(p - ufirst) % kUSlots]); };
+    auto bbar = [&](int p) { return smem_u32(&bars[kUSlots + (p - bfirst) % kBSlots]); };
+    auto upar = [&](int p) { return (unsigned)(((p - ufirst) / kUSlots) & 1); };
+    auto bpar = [&](int p) { return (unsigned)(((p - bfirst) / kBSlots) & 1); };
+    // producer state: planes issued and planes whose copy has landed
+    int u_issued = ufirst - 1, u_done = ufirst - 1, b_issued = bfirst - 1, b_done = bfirst - 1;
+    auto issue_u = [&](int p) {
+        mbar_expect(ubar(p), kUBoxBytes);
+        tma_load_3d(smem_u32(su + ((p - ufirst) % kUSlots) * kUF), &tu, x0, y0 - 1, p + 1, ubar(p));
+        u_issued = p;
+    };
+    auto issue_b = [&](int p) {
+        mbar_expect(bbar(p), kBBoxBytes);
+        tma_load_3d(smem_u32(sb + ((p - bfirst) % kBSlots) * kBF), &tb, x0, y0, p + 1, bbar(p));
+        b_issued = p;
+    };
+    auto wait_u = [&](int p) {
+        if (!mbar_wait(ubar(p), upar(p))) return false;
+        u_done = p;
+        return true;
+    };
+    auto wait_b = [&](int p) {
+        if (!mbar_wait(bbar(p), bpar(p))) return false;
+        b_done = p;
+        return true;
+    };
+
+    if (producer) {
+        for (int i = 0; i < kUSlots + kBSlots; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bool ok = true;
+        if (!ZERO_U)
+            for (int p = ufirst; p <= min(z0 + kAhead, ulast); ++p) issue_u(p);
+        for (int p = bfirst; p <= min(z0 - 1 + kAhead, blast); ++p) issue_b(p);
+        if (!ZERO_U)
+            for (int p = ufirst; ok && p <= z0; ++p) ok = wait_u(p);
+        ok = ok && wait_b(bfirst);
+        s_fail = ok ? 0 : 1;
+    }
+    __syncthreads();
+
+    long di = g.off + (long)(z0 - 2) * g.plane + (long)yr * g.pitch + x;  // (x, yr, zz-1) at step zz
+    float4 rm = make_float4(0.f, 0.f, 0.f, 0.f), rc = rm;
+    for (int zz = z0 - 1; zz <= z1 && !s_fail; ++zz) {
+        // A. scaled residual of plane zz (zero outside the interior)
+        const unsigned m = (zz >= 0 && zz < n) ? xmask : 0u;
+        const float *bp = sb + ob;
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f), um4 = r;
+        if (helper) {
+            float rh;
+            if (!ZERO_U) {
+                const float *uc = su + oc + iu;
+                rh = radd(rfma(-6.f, uc[0], bp[ib]),
+                          radd(radd(radd(uc[-1], uc[1]), radd(uc[-kTW], uc[kTW])), radd(su[om + iu], su[op + iu])));
+            } else {
+                rh = bp[ib];
+            }
+            sr[(zz & 1) * kRF + ib] = (m & 1u) ? rh : 0.f;
+        } else {
+            if (!ZERO_U) {
+                const float *uc = su + oc + iu;
+                const float4 b4 = ld4s(bp + ib), c4 = ld4s(uc);
+                const float4 s4 = ld4s(uc - kTW), n4 = ld4s(uc + kTW), u4 = ld4s(su + op + iu);
+                um4 = ld4s(su + om + iu);
+                const float w[6] = {uc[-1], c4.x, c4.y, c4.z, c4.w, uc[4]};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float ss = radd(radd(radd(w[k], w[k + 2]), radd(cf4(s4, k), cf4(n4, k))),
+                                          radd(cf4(um4, k), cf4(u4, k)));
+                    f4(r, k) = radd(rfma(-6.f, w[k + 1], cf4(b4, k)), ss);
+                }
+            } else {
+                r = ld4s(bp + ib);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (!((m >> k) & 1u)) f4(r, k) = 0.f;
+            *reinterpret_cast<float4 *>(sr + (zz & 1) * kRF + ib) = r;
+        }
+        // B.
+        __syncthreads();
+        // C. refill the slots of u plane zz-1 and b plane zz
+        if (producer) {
+            if (!ZERO_U && zz + 2 + kAhead <= ulast) issue_u(zz + 2 + kAhead);
+            if (zz + 1 + kAhead <= blast) issue_b(zz + 1 + kAhead);
+        }
+        // D. SPAI update of plane zz-1
+        if (zz > z0 && own_row) {
+            const float *p = sr + ((zz - 1) & 1) * kRF + ib;
+            const float4 pc = ld4s(p), ps = ld4s(p - kTW), pn = ld4s(p + kTW);
+            const float w[6] = {p[-1], pc.x, pc.y, pc.z, pc.w, p[4]};
+            float4 o;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float E = radd(radd(radd(w[k], w[k + 2]), radd(cf4(ps, k), cf4(pn, k))),
+                                     radd(cf4(rm, k), cf4(r, k)));
+                const float b0 = ZERO_U ? rmul(c0, cf4(rc, k)) : rfma(c0, cf4(rc, k), cf4(um4, k));
+                f4(o, k) = rfma(c1, E, b0);
+            }
+            float *dst = out + di;
+            if (x + 3 < n) {
+                *reinterpret_cast<float4 *>(dst) = o;
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (x + k < n) dst[k] = f4(o, k);
+            }
+        }
+        rm = rc;
+        rc = r;
+        di += g.plane;
+        om = oc;
+        oc = op;
+        op = op + kUF == kUSlots * kUF ? 0 : op + kUF;
+        ob = ob + kBF == kBSlots * kBF ? 0 : ob + kBF;
+        // E. planes of the next step
+        if (producer && zz < z1) {
+            bool ok = ZERO_U || wait_u(zz + 2);
+            ok = ok && wait_b(zz + 1);
+            if (!ok) s_fail = 1;
+        }
+        __syncthreads();
+    }
+    if (producer && s_fail) {
+        atomicOr(err, 1);
+        // shared memory must not be released while a copy may still land in it
+        for (int p = u_done + 1; p <= u_issued; ++p) mbar_wait(ubar(p), upar(p));
+        for (int p = b_done + 1; p <= b_issued; ++p) mbar_wait(bbar(p), bpar(p));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// tensor map over a padded 3D level array, box kTW x rows x 1
+bool make_map(CUtensorMap *map, const float *base, const Pitch3 &g, int rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn || ((uintptr_t)base & 15)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.n + 2), (cuuint64_t)(g.n + 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kTW, (cuuint32_t)rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_sweep3d_tma(const float *u, const float *b, float *out, int n, const double *c, int *err,
+                               cudaStream_t s)
+{
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(sweep3d_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(sweep3d_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBytes);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (!err) return cudaErrorInvalidValue;
+    const Pitch3 g = pitch3(n);
+    CUtensorMap tu, tb;
+    if (!make_map(&tb, b, g, kTRows)) return cudaErrorInvalidValue;
+    if (u) {
+        if (!make_map(&tu, u, g, kURows)) return cudaErrorInvalidValue;
+    } else {
+        tu = tb;
+    }
+    const int bx = (n + kTCols - 1) / kTCols, by = (n + kTTY - 1) / kTTY;
+    // one wave at two blocks per SM; chunks of at least four planes
+    int chunks = std::max(1, 2 * num_sms() / (bx * by));
+    chunks = std::min(chunks, std::max(1, n / 4));
+    const int Z = (n + chunks - 1) / chunks;
+    const dim3 grid(bx, by, (n + Z - 1) / Z);
+    const float c0 = (float)c[0], c1 = (float)c[1];
+    if (u)
+        sweep3d_tma_kernel<false><<<grid, kTThreads + 32, kSmemBytes, s>>>(tu, tb, out, g, Z, c0, c1, err);
+    else
+        sweep3d_tma_kernel<true><<<grid, kTThreads + 32, kSmemBytes, s>>>(tu, tb, out, g, Z, c0, c1, err);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace mg

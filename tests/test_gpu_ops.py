@@ -9,6 +9,8 @@ arithmetic: every output is a sum of at most ~25 rounded terms, so
 |out32 - out64| <= 32 * 2^-24 * S where S bounds the magnitude of the terms
 (plus the rounding of the FP32 inputs themselves, which the oracle sees).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -88,6 +90,62 @@ def test_sweep3d_fp64_bitwise(n, name):
     assert nrm == pytest.approx(float(np.sum(rh * rh)), rel=1e-13)
     out0, _ = binding.op_sweep(None, dev(h2 * b), w)
     assert np.array_equal(host(out0), oracle.sweep(np.zeros_like(u), h2 * b, w))
+
+
+@pytest.mark.parametrize("d,n", [(2, 3), (2, 15), (2, 255), (2, 1023), (3, 3), (3, 15), (3, 63), (3, 127)])
+def test_residual_refine_rounds_the_fp64_residual_once(d, n):
+    """Outer refinement step: the FP64 residual, rounded to FP32 (numpy's
+    float64 -> float32 cast is IEEE round to nearest even), bit for bit; its
+    squared norm summed in FP64 within 1e-12 relative of the exact sum."""
+    u, b = rand((n,) * d, 27), rand((n,) * d, 28)
+    h2 = 1.0 / (n + 1) ** 2
+    ref = oracle.residual_scaled(u, h2 * b)
+    for unscaled, bb in ((True, b), (False, h2 * b)):
+        rh32, nrm2 = binding.op_residual_refine(dev(u), dev(bb), b_unscaled=unscaled, want_norm=True)
+        torch.cuda.synchronize()
+        got = rh32.cpu().numpy()
+        assert got.dtype == np.float32
+        assert np.array_equal(got.view(np.uint32), ref.astype(np.float32).view(np.uint32))
+        exact = math.fsum((ref * ref).ravel())
+        assert abs(nrm2 - exact) <= 1e-12 * exact
+
+
+def _narrowing_cases(count, seed):
+    """float64 bit patterns that stress binary64 -> binary32 rounding: exact
+    ties (odd and even kept part), values just above/below a tie, results at
+    the edges of the binary32 exponent range (subnormal, smallest normal,
+    largest finite, overflow), zeros and infinities."""
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 2 ** 63, count, dtype=np.uint64) | (rng.integers(0, 2, count, dtype=np.uint64) << 63)
+    k = np.arange(count) % 8
+    low29 = np.uint64((1 << 29) - 1)
+    half = np.uint64(1 << 28)
+    bits = np.where(k == 0, (bits & ~low29) | half, bits)                 # exact ties
+    bits = np.where(k == 1, (bits & ~low29) | (half + np.uint64(1)), bits)  # just above
+    bits = np.where(k == 2, (bits & ~low29) | (half - np.uint64(1)), bits)  # just below
+    exp = rng.integers(860, 1160, count).astype(np.uint64)  # around binary32's range 897..1150
+    sign_frac = bits & np.uint64(0x800FFFFFFFFFFFFF)
+    bits = np.where(k >= 3, sign_frac | (exp << np.uint64(52)), bits)
+    bits = np.where(k == 3, (bits & ~low29) | half, bits)                 # ties near the range edges
+    x = bits.view(np.float64).copy()
+    x[np.isnan(x)] = 1.5
+    x[:8] = [0.0, -0.0, np.inf, -np.inf, 3.4028235677973366e38, 3.4028235677973362e38, 1.1754943508222875e-38,
+             1.401298464324817e-45]
+    return x
+
+
+@pytest.mark.parametrize("d,n", [(2, 255), (3, 63)])
+def test_residual_refine_narrowing_is_ieee_round_to_nearest_even(d, n):
+    """With u = 0 the residual is bh itself (a zero neighbour sum added to
+    it; -0 becomes +0), so the FP32 output is the rounding of arbitrary
+    doubles: compared bit for bit with numpy's IEEE conversion."""
+    x = _narrowing_cases(n ** d, 5).reshape((n,) * d)
+    rh32, _ = binding.op_residual_refine(dev(np.zeros_like(x)), dev(x))
+    torch.cuda.synchronize()
+    expect = np.where(x == 0.0, 0.0, x)
+    with np.errstate(over="ignore"):
+        expect32 = expect.astype(np.float32)
+    assert np.array_equal(rh32.cpu().numpy().view(np.uint32), expect32.view(np.uint32))
 
 
 @pytest.mark.parametrize("d,n", [(2, 3), (2, 15), (2, 255), (2, 1023), (3, 3), (3, 15), (3, 63)])
