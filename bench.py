@@ -284,7 +284,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         info = one_solve()
-    assert info.converged, info.status
+        assert info.converged, info.status
 
     def barrier():
         if world > 1:
