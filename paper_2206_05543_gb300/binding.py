@@ -42,6 +42,7 @@ SIGNATURES = {
     "mg_op_coarse_solve": (_I, [_I, _I, _P, _P, _P]),
     "mg_op_sweep_norm_noalloc": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _P, _P]),
     "mg_set_coeffs": (_I, [_P, _DP, _I]),
+    "mg_set_refinement_cycles": (_I, [_P, _I]),
     "mg_setup_batched": (_I, [_I, _I, _IP, _DP, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
     "mg_solve_batched": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _IP, _DP]),
     "mg_vcycles_adjoint": (_I, [_P, _I, _P, _P, _P, _DP]),
@@ -185,6 +186,11 @@ class Solver:
 
     def _args(self, u, b):
         return (_dev_ptr(u, self.dtype, self.shape, "u"), _dev_ptr(b, self.dtype, self.shape, "b"))
+
+    def set_refinement_cycles(self, cycles: int):
+        """fp32_ir only: FP32 cycles per refinement iteration (default 1)."""
+        _check(lib().mg_set_refinement_cycles(self._ctx, int(cycles)), "mg_set_refinement_cycles")
+        self.refinement_cycles = int(cycles)
 
     def set_coeffs(self, coeffs):
         arr, nc = _coeff_array(coeffs)

@@ -30,6 +30,7 @@ struct GraphPair {
 
 struct mg_ctx {
     int d = 2, N = 0, L = 0, nu1 = 1, nu2 = 1, gamma = 1, lt = 0, dev = 0;
+    int inner = 1;  // FP32 cycles per refinement iteration (MG_FP32_IR)
     mg_prec prec = MG_FP64;
     double c[3] = {0, 0, 0};
     int ncoef = 0;

@@ -285,7 +285,7 @@ struct Recorder {
     cudaError_t resrestrict(const T *u, const T *b, bool unsc, T *bc, int n)
     {
         if (pl() && c->d == 2) return launch_resrestrict2d_pl((const float *)u, (const float *)b, (float *)bc, n, c->s);
-        if (pl()) return launch_resrestrict3d_pl((const float *)u, (const float *)b, (float *)bc, n, c->s);
+        if (pl()) return launch_resrestrict3d_tma((const float *)u, (const float *)b, (float *)bc, n, c->d_err, c->s);
         return op_resrestrict<T>(c->d, u, b, unsc, bc, n, c->s);
     }
     cudaError_t prolong(const T *e, T *u, int n)
@@ -488,8 +488,12 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
-            R.acc64 = (double *)u;
-            cudaError_t e = R.visit(0, true, false);
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < c->inner && !e; ++k) {
+                // only the last cycle of the iteration may fuse the FP64 update
+                R.acc64 = k == c->inner - 1 ? (double *)u : nullptr;
+                e = R.visit(0, k == 0, false);
+            }
             if (e || R.fused_update) return e;
             if (c->pl && d == 2) return launch_add_pl2d((double *)u, (const float *)c->A[0], n0, c->s);
             if (c->pl) return launch_add_pl3d((double *)u, (const float *)c->A[0], n0, c->s);
@@ -804,6 +808,16 @@ mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs)
     return MG_OK;
 }
 
+mg_status mg_set_refinement_cycles(mg_ctx *ctx, int cycles)
+{
+    if (!ctx || ctx->batch || ctx->prec != MG_FP32_IR || cycles < 1 || cycles > 8) return MG_EINVAL;
+    if (cudaSetDevice(ctx->dev) != cudaSuccess || cudaStreamSynchronize(ctx->s) != cudaSuccess)
+        return cuda_fail(cudaGetLastError());
+    ctx->inner = cycles;
+    free_graphs(ctx);
+    return MG_OK;
+}
+
 mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out)
 {
     if (!ctx || !u || !b || !norm_out || ctx->batch) return MG_EINVAL;
@@ -886,9 +900,15 @@ mg_status mg_op_residual_restrict(int d, int n, mg_prec prec, const void *u, con
         e = cudaSuccess;
         const cudaStream_t s = (cudaStream_t)stream;
         float *pu = tmp.make(n, u, s, e), *pb = tmp.make(n, bh, s, e), *pc = tmp.make((n - 1) / 2, nullptr, s, e);
-        if (!e) e = d == 2 ? launch_resrestrict2d_pl(pu, pb, pc, n, s) : launch_resrestrict3d_pl(pu, pb, pc, n, s);
+        int *err = nullptr, h_err = 0;
+        if (!e && d == 3) e = cudaMalloc(&err, sizeof(int));
+        if (!e && d == 3) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+        if (!e) e = d == 2 ? launch_resrestrict2d_pl(pu, pb, pc, n, s) : launch_resrestrict3d_tma(pu, pb, pc, n, err, s);
         if (!e) e = tmp.pack(pc, (float *)bh_coarse_out, (n - 1) / 2, false, s);
+        if (!e && err) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
+        if (err) cudaFree(err);
+        if (!e && h_err) return MG_ETIMEOUT;
     } else if (prec == MG_FP32_IR)
         e = op_resrestrict<float>(d, (const float *)u, (const float *)bh, b_unscaled != 0, (float *)bh_coarse_out,
                                   n, (cudaStream_t)stream);

@@ -129,6 +129,8 @@ size_t pitch3_floats(int n);
 cudaError_t launch_sweep3d_tma(const float *u, const float *b, float *out, int n, const double *c, int *err,
                                cudaStream_t s);
 cudaError_t launch_resrestrict3d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s);
+// TMA-staged variant of the residual + full weighting above (*err as for the sweep)
+cudaError_t launch_resrestrict3d_tma(const float *u, const float *b, float *bc, int n, int *err, cudaStream_t s);
 cudaError_t launch_prolong3d_pl(const float *e, float *u, int n, cudaStream_t s);
 cudaError_t launch_pack3d(const float *in, float *out, int n, bool to_padded, cudaStream_t s);
 cudaError_t launch_add_pl3d(double *u, const float *e, int n, cudaStream_t s);

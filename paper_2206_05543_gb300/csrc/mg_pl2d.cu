@@ -74,10 +74,18 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
     bn = row4(Bp, y0 - 1, x);
     if (lt || rt) hb = row1(Bp, y0 - 1, xh);
     double acc = 0.0;
+    // refinement epilogue: the FP64 solution row j is loaded at step j and
+    // updated at step j + 1, so its latency overlaps one step of work
+    double u64c[4] = {0.0, 0.0, 0.0, 0.0}, u64n[4] = {0.0, 0.0, 0.0, 0.0};
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
         const float4 bc = bn;
         const float hbc = hb;
+        if (ACC64 && j >= y0 && j < y1) {
+            const double *ur = u64 + (long)j * n + x;
+            for (int k = 0; k < 4; ++k)
+                if (x + k < n) u64n[k] = ur[k];
+        }
         bn = row4(Bp, j + 1, x);  // prefetch
         if (lt || rt) hb = row1(Bp, j + 1, xh);
         float4 r;
@@ -131,7 +139,7 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
                 // caller's FP64 solution (compact rows of n doubles)
                 double *ur = u64 + (long)(j - 1) * n + x;
                 for (int k = 0; k < 4; ++k)
-                    if (x + k < n) ur[k] = __dadd_rn(ur[k], widen(c4(o, k)));
+                    if (x + k < n) ur[k] = __dadd_rn(u64c[k], widen(c4(o, k)));
             } else if (x < n) {
                 st4_valid(O + (long)(j - 1) * P + x, o, x, n);
             }
@@ -146,6 +154,8 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
             hp_ = hc;
             hc = hn;
         }
+        if (ACC64)
+            for (int k = 0; k < 4; ++k) u64c[k] = u64n[k];
     }
     if (NORM) block_sum_store<kPLThreads>(acc, partial);
 }

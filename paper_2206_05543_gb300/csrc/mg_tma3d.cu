@@ -273,6 +273,142 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
     }
 }
 
+// ---------------------------------------------------------------------------
+// Residual + full weighting on TMA-staged planes (formula and order as
+// resrestrict3d_kernel): a block owns 16 x 16 coarse columns, i.e. a 33 x 33
+// fine residual patch per fine plane. u boxes (40 columns from 2 ic0 - 4,
+// 35 rows from 2 jc0 - 1) and b boxes (40 columns, 33 rows from 2 jc0) of
+// each fine plane arrive in rings kAhead planes ahead, as in the sweep. Per
+// fine plane f: residual patch (all warps) -> barrier (u plane f-1 and b
+// plane f are dead: refill) -> x-pass -> barrier -> y-pass, z-combination
+// and output of every second plane -> wait for the next planes -> barrier.
+// ---------------------------------------------------------------------------
+constexpr int kRQ = 16;                 // coarse tile edge
+constexpr int kRF = 2 * kRQ + 1;        // 33 fine residual points per row
+constexpr int kRW = 40;                 // box width: fine columns 2 ic0 - 4 .. 2 ic0 + 35
+constexpr int kRUR = kRF + 2;           // 35 u rows
+constexpr int kRCons = kRQ * kRQ;       // 256 threads own one coarse column each
+constexpr int kRThreads = kRCons + 32;  // + helper warp
+constexpr int kRUSlots = 3 + kAhead, kRBSlots = 1 + kAhead;
+constexpr int kRUBox = kRUR * kRW * 4, kRBBox = kRF * kRW * 4;
+constexpr int kRUSlotBytes = (kRUBox + 127) / 128 * 128, kRBSlotBytes = (kRBBox + 127) / 128 * 128;
+constexpr int kRSmemBytes = kRUSlots * kRUSlotBytes + kRBSlots * kRBSlotBytes + 128;
+
+__global__ void __launch_bounds__(kRThreads)
+resrestrict3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant__ CUtensorMap tb,
+                         float *__restrict__ bc, Pitch3 g, Pitch3 gc, int Zc, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float *const su = (float *)base;
+    float *const sb = (float *)(base + kRUSlots * kRUSlotBytes);
+    __shared__ float sr[kRF][kRF + 1];
+    __shared__ float st1[kRF][kRQ + 1];
+    __shared__ __align__(8) unsigned long long bars[kRUSlots + kRBSlots];
+    __shared__ int s_fail;
+    constexpr int kUF = kRUSlotBytes / 4, kBF = kRBSlotBytes / 4;
+
+    const int n = g.n, nc = gc.n, t = threadIdx.x;
+    const bool producer = t == kRCons;
+    const int tic = t % kRQ, tjc = t / kRQ;
+    const int ic0 = blockIdx.x * kRQ, jc0 = blockIdx.y * kRQ;
+    const int ic = ic0 + tic, jc = jc0 + tjc;
+    const int fx0 = 2 * ic0, fy0 = 2 * jc0;
+    const int kc0 = blockIdx.z * Zc, kc1 = min(kc0 + Zc, nc);
+    const int f0 = 2 * kc0, f1 = 2 * kc1;
+    const int ufirst = f0 - 1, bfirst = f0, ulast = f1 + 1, blast = f1;
+    auto ubar = [&](int p) { return smem_u32(&bars[(p - ufirst) % kRUSlots]); };
+    auto bbar = [&](int p) { return smem_u32(&bars[kRUSlots + (p - bfirst) % kRBSlots]); };
+    auto upar = [&](int p) { return (unsigned)(((p - ufirst) / kRUSlots) & 1); };
+    auto bpar = [&](int p) { return (unsigned)(((p - bfirst) / kRBSlots) & 1); };
+    int u_issued = ufirst - 1, u_done = ufirst - 1, b_issued = bfirst - 1, b_done = bfirst - 1;
+    // tensor coordinates (x + 4, y + 1, z + 1); box x starts at fine column fx0 - 4
+    auto issue_u = [&](int p) {
+        mbar_expect(ubar(p), kRUBox);
+        tma_load_3d(smem_u32(su + ((p - ufirst) % kRUSlots) * kUF), &tu, fx0, fy0, p + 1, ubar(p));
+        u_issued = p;
+    };
+    auto issue_b = [&](int p) {
+        mbar_expect(bbar(p), kRBBox);
+        tma_load_3d(smem_u32(sb + ((p - bfirst) % kRBSlots) * kBF), &tb, fx0, fy0 + 1, p + 1, bbar(p));
+        b_issued = p;
+    };
+    auto wait_u = [&](int p) {
+        if (!mbar_wait(ubar(p), upar(p))) return false;
+        u_done = p;
+        return true;
+    };
+    auto wait_b = [&](int p) {
+        if (!mbar_wait(bbar(p), bpar(p))) return false;
+        b_done = p;
+        return true;
+    };
+
+    if (producer) {
+        for (int i = 0; i < kRUSlots + kRBSlots; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int p = ufirst; p <= min(f0 + 1 + kAhead, ulast); ++p) issue_u(p);
+        for (int p = bfirst; p <= min(f0 + kAhead, blast); ++p) issue_b(p);
+        bool ok = true;
+        for (int p = ufirst; ok && p <= f0 + 1; ++p) ok = wait_u(p);
+        ok = ok && wait_b(bfirst);
+        s_fail = ok ? 0 : 1;
+    }
+    __syncthreads();
+
+    float t2a = 0.f, t2b = 0.f;
+    for (int f = f0; f <= f1 && !s_fail; ++f) {
+        const float *um = su + ((f - 1 - ufirst) % kRUSlots) * kUF;
+        const float *uc = su + ((f - ufirst) % kRUSlots) * kUF;
+        const float *up = su + ((f + 1 - ufirst) % kRUSlots) * kUF;
+        const float *bp = sb + ((f - bfirst) % kRBSlots) * kBF;
+        // fine residual patch: point (i, j) = fine (fx0 + i, fy0 + j), u tile
+        // column i + 4, row j + 1; b tile column i + 4, row j
+        for (int q = t; q < kRF * kRF; q += kRThreads) {
+            const int i = q % kRF, j = q / kRF;
+            float r = 0.f;
+            if (fx0 + i < n && fy0 + j < n) {
+                const int iu = (j + 1) * kRW + i + 4;
+                const float s = radd(radd(radd(uc[iu - 1], uc[iu + 1]), radd(uc[iu - kRW], uc[iu + kRW])),
+                                     radd(um[iu], up[iu]));
+                r = radd(rfma(-6.f, uc[iu], bp[j * kRW + i + 4]), s);
+            }
+            sr[j][i] = r;
+        }
+        __syncthreads();
+        if (producer) {
+            if (f + 2 + kAhead <= ulast) issue_u(f + 2 + kAhead);
+            if (f + 1 + kAhead <= blast) issue_b(f + 1 + kAhead);
+        }
+        for (int q = t; q < kRF * kRQ; q += kRThreads) {
+            const int k = q % kRQ, j = q / kRQ;
+            st1[j][k] = rfma(2.f, sr[j][2 * k + 1], radd(sr[j][2 * k], sr[j][2 * k + 2]));
+        }
+        __syncthreads();
+        if (t < kRCons) {
+            const float t2 = rfma(2.f, st1[2 * tjc + 1][tic], radd(st1[2 * tjc][tic], st1[2 * tjc + 2][tic]));
+            if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
+                const int kc = f / 2 - 1;
+                bc[gc.off + (long)kc * gc.plane + (long)jc * gc.pitch + ic] =
+                    scale2<-4>(rfma(2.f, t2b, radd(t2a, t2)));
+            }
+            t2a = t2b;
+            t2b = t2;
+        }
+        if (producer && f < f1) {
+            bool ok = wait_u(f + 2);
+            ok = ok && wait_b(f + 1);
+            if (!ok) s_fail = 1;
+        }
+        __syncthreads();
+    }
+    if (producer && s_fail) {
+        atomicOr(err, 1);
+        for (int p = u_done + 1; p <= u_issued; ++p) mbar_wait(ubar(p), upar(p));
+        for (int p = b_done + 1; p <= b_issued; ++p) mbar_wait(bbar(p), bpar(p));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static std::once_flag once;
@@ -288,14 +424,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// tensor map over a padded 3D level array, box kTW x rows x 1
-bool make_map(CUtensorMap *map, const float *base, const Pitch3 &g, int rows)
+// tensor map over a padded 3D level array, box width x rows x 1
+bool make_map(CUtensorMap *map, const float *base, const Pitch3 &g, int width, int rows)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || ((uintptr_t)base & 15)) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.n + 2), (cuuint64_t)(g.n + 2)};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kTW, (cuuint32_t)rows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -320,9 +456,9 @@ cudaError_t launch_sweep3d_tma(const float *u, const float *b, float *out, int n
     if (!err) return cudaErrorInvalidValue;
     const Pitch3 g = pitch3(n);
     CUtensorMap tu, tb;
-    if (!make_map(&tb, b, g, kTRows)) return cudaErrorInvalidValue;
+    if (!make_map(&tb, b, g, kTW, kTRows)) return cudaErrorInvalidValue;
     if (u) {
-        if (!make_map(&tu, u, g, kURows)) return cudaErrorInvalidValue;
+        if (!make_map(&tu, u, g, kTW, kURows)) return cudaErrorInvalidValue;
     } else {
         tu = tb;
     }
@@ -337,6 +473,36 @@ cudaError_t launch_sweep3d_tma(const float *u, const float *b, float *out, int n
         sweep3d_tma_kernel<false><<<grid, kTThreads + 32, kSmemBytes, s>>>(tu, tb, out, g, Z, c0, c1, err);
     else
         sweep3d_tma_kernel<true><<<grid, kTThreads + 32, kSmemBytes, s>>>(tu, tb, out, g, Z, c0, c1, err);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resrestrict3d_tma(const float *u, const float *b, float *bc, int n, int *err, cudaStream_t s)
+{
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int resident = 1;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(resrestrict3d_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kRSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, resrestrict3d_tma_kernel, kRThreads,
+                                                                     kRSmemBytes);
+        if (resident < 1) resident = 1;
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (!err) return cudaErrorInvalidValue;
+    const Pitch3 g = pitch3(n), gc = pitch3((n - 1) / 2);
+    const int nc = gc.n;
+    CUtensorMap tu, tb;
+    if (!make_map(&tu, u, g, kRW, kRUR) || !make_map(&tb, b, g, kRW, kRF)) return cudaErrorInvalidValue;
+    const int bxy = (nc + kRQ - 1) / kRQ;
+    // at most one wave: z-chunks of coarse planes
+    int chunks = std::max(1, resident * num_sms() / (bxy * bxy));
+    chunks = std::min(chunks, std::max(1, nc / 2));
+    const int Zc = (nc + chunks - 1) / chunks;
+    resrestrict3d_tma_kernel<<<dim3(bxy, bxy, (nc + Zc - 1) / Zc), kRThreads, kRSmemBytes, s>>>(tu, tb, bc, g, gc,
+                                                                                               Zc, err);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -152,6 +152,28 @@ def test_mixed_precision_refinement(d, N, nu, tol_u):
     assert err_mixed <= max(tol_u, 10 * err_fp64)
 
 
+@pytest.mark.parametrize("d,N,nu", [(2, 256, 1), (3, 64, 2)])
+def test_refinement_with_several_cycles_per_iteration(d, N, nu):
+    """Two and three FP32 cycles per refinement iteration: still the FP64
+    tolerance (oracle residual), and the iteration count drops to about the
+    single-cycle count divided by the cycles per iteration."""
+    b = inputs.uniform(d, N, 9)
+    its = {}
+    for m in (1, 2, 3):
+        with Solver(d, N, nu1=nu, nu2=nu, precision="fp32_ir") as s:
+            if m > 1:
+                s.set_refinement_cycles(m)
+            info = s.solve(dev(b), tol=1e-10, max_cycles=60)
+            u = host(info.u)
+        assert info.converged, m
+        assert oracle.residual_norm(u, b) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
+        its[m] = info.cycles
+    assert its[2] <= (its[1] + 1) // 2 + 1 and its[3] <= (its[1] + 2) // 3 + 1, its
+    with Solver(d, N, nu1=nu, nu2=nu, precision="fp64") as s:
+        with pytest.raises(MGError):
+            s.set_refinement_cycles(2)
+
+
 @pytest.mark.slow
 def test_config_2d_n8192_two_cycles_bitwise():
     """Full-size 2D workload (N = 8192, 67M unknowns, uniform b seed 0, zero
