@@ -232,6 +232,17 @@ const char *mg_last_cuda_error(void);
  * since the process started; graph replays count every node. */
 unsigned long long mg_kernel_launch_count(void);
 
+/* Test hook for the bounded device-side waits (the TMA-staged 3D FP32
+ * kernels wait on mbarriers for their copies). The next `launches` such
+ * launches make their first copy's barrier expect 16 bytes more than the copy
+ * delivers, so that wait expires after its bound (about one second); the
+ * block then records the expiry, drains its other copies and returns, and
+ * the synchronising call that follows reports MG_ETIMEOUT. Nothing faults,
+ * traps or hangs. A launch armed while a cycle is being recorded into the
+ * context's CUDA graph stays armed in every replay of that graph. 0 disarms;
+ * returns the number of launches still armed before the call. */
+int mg_test_arm_wait_expiry(int launches);
+
 #ifdef __cplusplus
 }
 #endif

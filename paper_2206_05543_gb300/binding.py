@@ -49,6 +49,7 @@ SIGNATURES = {
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_cuda_error": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (_U, []),
+    "mg_test_arm_wait_expiry": (_I, [_I]),
 }
 
 
@@ -121,6 +122,12 @@ def _dev_ptr(t, dtype, shape, name):
 
 def kernel_launch_count() -> int:
     return int(lib().mg_kernel_launch_count())
+
+
+def arm_wait_expiry(launches: int) -> int:
+    """Test hook: the next `launches` TMA-staged kernels let their first
+    bounded wait expire (the call reports MG_ETIMEOUT). 0 disarms."""
+    return int(lib().mg_test_arm_wait_expiry(int(launches)))
 
 
 class SolveInfo:

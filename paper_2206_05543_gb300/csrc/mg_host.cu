@@ -400,10 +400,14 @@ struct Recorder {
         e = prolong(A(l + 1), buf[cur], n);
         if (e) return e;
         for (int s = 0; s < c->nu2; ++s) {
-            if (l == 0 && acc64 && pl() && c->d == 2 && s == c->nu2 - 1) {
+            if (l == 0 && acc64 && pl() && s == c->nu2 - 1) {
                 // refinement: the last finest sweep adds its result to the FP64 u
                 fused_update = true;
-                return launch_sweep2d_pl_acc64((const float *)buf[cur], (const float *)BH(l), acc64, n, c->c, c->s);
+                if (c->d == 2)
+                    return launch_sweep2d_pl_acc64((const float *)buf[cur], (const float *)BH(l), acc64, n, c->c,
+                                                   c->s);
+                return launch_sweep3d_tma_acc64((const float *)buf[cur], (const float *)BH(l), acc64, n, c->c,
+                                                c->d_err, c->s);
             }
             e = sweep(buf[cur], BH(l), unsc(l), buf[1 - cur], n);
             if (e) return e;

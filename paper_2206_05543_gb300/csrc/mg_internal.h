@@ -128,8 +128,10 @@ size_t pitch3_floats(int n);
 // does not land within about a second sets *err (device int) to nonzero.
 cudaError_t launch_sweep3d_tma(const float *u, const float *b, float *out, int n, const double *c, int *err,
                                cudaStream_t s);
-cudaError_t launch_resrestrict3d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s);
-// TMA-staged variant of the residual + full weighting above (*err as for the sweep)
+// the same sweep with the refinement epilogue u64 (compact FP64) += result
+cudaError_t launch_sweep3d_tma_acc64(const float *u, const float *b, double *u64, int n, const double *c, int *err,
+                                     cudaStream_t s);
+// residual + full weighting on TMA-staged planes (*err as for the sweep)
 cudaError_t launch_resrestrict3d_tma(const float *u, const float *b, float *bc, int n, int *err, cudaStream_t s);
 cudaError_t launch_prolong3d_pl(const float *e, float *u, int n, cudaStream_t s);
 cudaError_t launch_pack3d(const float *in, float *out, int n, bool to_padded, cudaStream_t s);

@@ -21,82 +21,6 @@ __device__ __forceinline__ float &e4(float4 &v, int k) { return (&v.x)[k]; }
 __device__ __forceinline__ float ce4(const float4 &v, int k) { return (&v.x)[k]; }
 
 // ---------------------------------------------------------------------------
-// Residual + full weighting (formula as resrestrict3d_kernel): 16 x 16 coarse
-// columns per block, fine residual patch 33 x 33 per fine plane from a ring of
-// three u planes (patch rows loaded as aligned float4 from column 2 ic0 - 4).
-// ---------------------------------------------------------------------------
-constexpr int kQ = 16;                  // coarse tile edge
-constexpr int kQF = 2 * kQ + 1;         // 33 fine residual points per row
-constexpr int kQU = 40;                 // u patch row width (10 float4, columns 2 ic0 - 4 ..)
-constexpr int kQR = kQF + 2;            // 35 u patch rows
-constexpr int kQThreads = kQ * kQ;
-
-__global__ void __launch_bounds__(kQThreads)
-resrestrict3d_pl_kernel(const float *__restrict__ u, const float *__restrict__ b, float *__restrict__ bc, Pitch3 g,
-                        Pitch3 gc, int Zc)
-{
-    __shared__ __align__(16) float su[3][kQR][kQU];
-    __shared__ float sr[kQF][kQF + 1];
-    __shared__ float st1[kQF][kQ + 1];
-    const int n = g.n, nc = gc.n, t = threadIdx.x;
-    const int tic = t % kQ, tjc = t / kQ;
-    const int ic0 = blockIdx.x * kQ, jc0 = blockIdx.y * kQ;
-    const int ic = ic0 + tic, jc = jc0 + tjc;
-    const int fx0 = 2 * ic0, fy0 = 2 * jc0;
-    const int kc0 = blockIdx.z * Zc, kc1 = min(kc0 + Zc, nc);
-    const int f0 = 2 * kc0, f1 = 2 * kc1;
-    const float *U = u + g.off, *Bp = b + g.off;
-    const long P = g.pitch, S = g.plane;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    // u patch: rows fy0 - 1 .. fy0 + 33, columns fx0 - 4 .. fx0 + 35
-    auto load_plane = [&](int slot, int fz) {
-        for (int q = t; q < kQR * (kQU / 4); q += kQThreads) {
-            const int r = q / (kQU / 4), c4 = q % (kQU / 4);
-            const int y = fy0 - 1 + r;
-            float4 v = z4;
-            if (y <= n && fz >= -1 && fz <= n) v = ld4g(U + fz * S + y * P + fx0 - 4 + 4 * c4);
-            st4g(&su[slot][r][4 * c4], v);
-        }
-    };
-    load_plane((f0 - 1 + 3) % 3, f0 - 1);
-    load_plane(f0 % 3, f0);
-    float t2a = 0.f, t2b = 0.f;
-    for (int f = f0; f <= f1; ++f) {
-        load_plane((f + 1) % 3, f + 1);
-        __syncthreads();
-        const int sm = (f + 2) % 3, sc = f % 3, sp = (f + 1) % 3;
-        for (int q = t; q < kQF * kQF; q += kQThreads) {
-            const int i = q % kQF, j = q / kQF;
-            const int x = fx0 + i, y = fy0 + j;
-            float r = 0.f;
-            if (x < n && y < n) {
-                const int cx = i + 4, ry = j + 1;  // patch coordinates
-                const float bb = Bp[(long)f * S + (long)y * P + x];
-                const float s = radd(radd(radd(su[sc][ry][cx - 1], su[sc][ry][cx + 1]),
-                                          radd(su[sc][ry - 1][cx], su[sc][ry + 1][cx])),
-                                     radd(su[sm][ry][cx], su[sp][ry][cx]));
-                r = radd(rfma(-6.f, su[sc][ry][cx], bb), s);
-            }
-            sr[j][i] = r;
-        }
-        __syncthreads();
-        for (int q = t; q < kQF * kQ; q += kQThreads) {
-            const int k = q % kQ, j = q / kQ;
-            st1[j][k] = rfma(2.f, sr[j][2 * k + 1], radd(sr[j][2 * k], sr[j][2 * k + 2]));
-        }
-        __syncthreads();
-        const float t2 = rfma(2.f, st1[2 * tjc + 1][tic], radd(st1[2 * tjc][tic], st1[2 * tjc + 2][tic]));
-        if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
-            const int kc = f / 2 - 1;
-            bc[gc.off + (long)kc * gc.plane + (long)jc * gc.pitch + ic] = scale2<-4>(rfma(2.f, t2b, radd(t2a, t2)));
-        }
-        t2a = t2b;
-        t2b = t2;
-        __syncthreads();  // the ring slot of plane f - 1 is reloaded next
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Trilinear interpolation + correction (formula as prolong3d_kernel): thread
 // per 4 fine x-columns of one fine row, marching over coarse planes.
 // ---------------------------------------------------------------------------
@@ -201,17 +125,6 @@ size_t pitch3_floats(int n)
 {
     const Pitch3 g = pitch3(n);
     return (size_t)(n + 2) * g.plane + 64;
-}
-
-cudaError_t launch_resrestrict3d_pl(const float *u, const float *b, float *bc, int n, cudaStream_t s)
-{
-    const Pitch3 g = pitch3(n), gc = pitch3((n - 1) / 2);
-    const int nc = gc.n;
-    const int bxy = (nc + kQ - 1) / kQ;
-    const int Zc = chunk_rows(bxy * bxy, nc, 8 * num_sms(), 2, 32);
-    resrestrict3d_pl_kernel<<<dim3(bxy, bxy, (nc + Zc - 1) / Zc), kQThreads, 0, s>>>(u, b, bc, g, gc, Zc);
-    count_launch(1);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_prolong3d_pl(const float *e, float *u, int n, cudaStream_t s)
