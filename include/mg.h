@@ -105,13 +105,16 @@ void mg_destroy(mg_ctx *ctx);
  * mg_setup); the recorded cycle is re-recorded on the next call. */
 mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs);
 
-/* MG_FP32_IR contexts: the number of FP32 cycles per refinement iteration
- * (1..8; default 1). Each iteration still forms r = b - A u in FP64 once,
- * rounds it to FP32, runs `cycles` FP32 cycles on A e = r from e = 0 (the
- * later ones starting from the current e) and adds e to u in FP64; more
- * cycles per iteration mean fewer FP64 residuals per solve (the residual
- * reduction per iteration is about the cycle's contraction to that power).
- * MG_EINVAL for other precisions; re-recorded on the next call. */
+/* MG_FP32_IR contexts and batched contexts: the number of FP32 cycles per
+ * refinement iteration (1..8; default 1). Each iteration still forms
+ * r = b - A u in FP64 once, rounds it to FP32, runs `cycles` FP32 cycles on
+ * A e = r from e = 0 (the later ones starting from the current e) and adds e
+ * to u in FP64; more cycles per iteration mean fewer FP64 residuals per
+ * solve (the residual reduction per iteration is about the cycle's
+ * contraction to that power). MG_EINVAL for other precisions, and for
+ * batched contexts with cycles > 1 unless nu1 + nu2 is even and every
+ * N >= 32. Single-problem contexts re-record on the next call; batched
+ * contexts re-record here (synchronises). */
 mg_status mg_set_refinement_cycles(mg_ctx *ctx, int cycles);
 
 /* ---------------------------------------------------------------------- */

@@ -284,6 +284,12 @@ class BatchedSolver:
     def __exit__(self, *exc):
         self.close()
 
+    def set_refinement_cycles(self, cycles: int):
+        """FP32 cycles per refinement iteration (default 1; >1 needs nu1 + nu2
+        even and every N >= 32)."""
+        _check(lib().mg_set_refinement_cycles(self._ctx, int(cycles)), "mg_set_refinement_cycles")
+        self.refinement_cycles = int(cycles)
+
     def solve(self, bs, us=None, tol: float = 1e-10, max_cycles: int = 100):
         """Returns (us, status, cycles per problem, relres per problem)."""
         torch = _torch()

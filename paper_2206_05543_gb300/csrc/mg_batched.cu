@@ -131,6 +131,9 @@ struct BatchSize {
     std::vector<int> probs, lev;
     std::vector<BItem<float> *> pre, post;
     BItem<float> *rr = nullptr, *pro = nullptr;
+    // first pre-sweep of the later cycles of a refinement iteration: finest
+    // levels from the previous cycle's result, coarse levels from zero
+    BItem<float> *again = nullptr;
     int H = 16, Hrr = 8, Hpro = 8;
 };
 
@@ -251,7 +254,7 @@ mg_status autotune(mg_ctx *c, BatchWork *w)
         static const int sweep_c[] = {4, 8, 16, 32, 64};
         static const int rr_c[] = {2, 4, 8, 16, 32};
         tune("sweep", sweep_c, 5, S.H, [&](int H) {
-            launch_sweep2d_pl_batched(S.pre[0], np, w->active, S.n, H, true, c->c, c->s);
+            launch_sweep2d_pl_batched(S.pre[0], np, w->active, S.n, H, 1, c->c, c->s);
         });
         tune("restrict", rr_c, 5, S.Hrr, [&](int H) {
             launch_resrestrict2d_pl_batched(S.rr, np, w->active, S.n, H, c->s);
@@ -268,15 +271,20 @@ mg_status autotune(mg_ctx *c, BatchWork *w)
     return MG_OK;
 }
 
-cudaError_t record_rest(mg_ctx *c, BatchWork *w)
+cudaError_t record_cycle(mg_ctx *c, BatchWork *w, bool first)
 {
     cudaError_t e;
     const int nu1 = c->nu1, nu2 = c->nu2;
     // descend
     for (BatchSize &S : w->sizes) {
         const int np = (int)S.probs.size();
-        for (int k = 0; k < nu1; ++k)
-            if ((e = launch_sweep2d_pl_batched(S.pre[k], np, w->active, S.n, S.H, k == 0, c->c, c->s))) return e;
+        for (int k = 0; k < nu1; ++k) {
+            if (k == 0 && !first)
+                e = launch_sweep2d_pl_batched(S.again, np, w->active, S.n, S.H, 2, c->c, c->s);
+            else
+                e = launch_sweep2d_pl_batched(S.pre[k], np, w->active, S.n, S.H, k == 0 ? 1 : 0, c->c, c->s);
+            if (e) return e;
+        }
         if (nu1 == 0) {
             // no pre-sweep: the level's value is zero
             for (size_t j = 0; j < S.probs.size(); ++j) {
@@ -297,8 +305,16 @@ cudaError_t record_rest(mg_ctx *c, BatchWork *w)
         const int np = (int)S.probs.size();
         if ((e = launch_prolong2d_pl_batched(S.pro, np, w->active, S.n, S.Hpro, c->s))) return e;
         for (int k = 0; k < nu2; ++k)
-            if ((e = launch_sweep2d_pl_batched(S.post[k], np, w->active, S.n, S.H, false, c->c, c->s))) return e;
+            if ((e = launch_sweep2d_pl_batched(S.post[k], np, w->active, S.n, S.H, 0, c->c, c->s))) return e;
     }
+    return cudaSuccess;
+}
+
+cudaError_t record_rest(mg_ctx *c, BatchWork *w)
+{
+    cudaError_t e;
+    for (int k = 0; k < c->inner; ++k)
+        if ((e = record_cycle(c, w, k == 0))) return e;
     // u_i += e_i in FP64
     batched_update<<<dim3(w->upd_chunks, w->count), 256, 0, c->s>>>(w->upd, w->active);
     count_launch(1);
@@ -323,6 +339,25 @@ cudaError_t record_pre(mg_ctx *c, BatchWork *w)
 }  // namespace
 
 namespace mg {
+mg_status batch_set_inner(mg_ctx *c, int inner)
+{
+    BatchWork *w = c->batch;
+    if (!w || inner < 1 || inner > 8) return MG_EINVAL;
+    if (inner > 1) {
+        // later cycles continue level 0 in place of the first pre-sweep's
+        // input: it must be the buffer the cycle ends in, and not a tail level
+        if ((c->nu1 + c->nu2) % 2) return MG_EINVAL;
+        for (int p = 0; p < w->count; ++p)
+            if (w->lt[p] == 0) return MG_EINVAL;
+    }
+    if (cudaSetDevice(c->dev) != cudaSuccess || cudaStreamSynchronize(c->s) != cudaSuccess)
+        return cuda_fail(cudaGetLastError());
+    if (w->rest) cudaGraphExecDestroy(w->rest);
+    w->rest = nullptr;
+    c->inner = inner;
+    return capture_graph(c, &w->rest, &w->rest_nodes, [&]() { return record_rest(c, w); });
+}
+
 void free_batch(mg_ctx *c)
 {
     BatchWork *w = c->batch;
@@ -449,11 +484,13 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             for (int k = 0; k < nu1; ++k) pre.push_back((BItem<float> *)a.take(tb));
             for (int k = 0; k < nu2; ++k) post.push_back((BItem<float> *)a.take(tb));
             BItem<float> *rr = (BItem<float> *)a.take(tb), *pro = (BItem<float> *)a.take(tb);
+            BItem<float> *again = (BItem<float> *)a.take(tb);
             if (real) {
                 S.pre = pre;
                 S.post = post;
                 S.rr = rr;
                 S.pro = pro;
+                S.again = again;
             }
         }
         for (BatchGroup &G : w->groups) {
@@ -517,6 +554,14 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             }
             up(S.pre[k], tab.data(), np * sizeof(BItem<float>));
         }
+        // later cycles of an iteration: level 0 continues from the previous
+        // cycle's result (buffer A when nu1 + nu2 is even), coarse levels from zero
+        for (size_t j = 0; j < np; ++j) {
+            const int p = S.probs[j], l = S.lev[j];
+            float *buf[2] = {w->A[p][l], w->B[p][l]};
+            tab[j] = BItem<float>{l == 0 ? result_buf(w, p, 0, nu1 + nu2) : nullptr, w->BH[p][l], buf[1], p, 0};
+        }
+        up(S.again, tab.data(), np * sizeof(BItem<float>));
         for (size_t j = 0; j < np; ++j) {
             const int p = S.probs[j], l = S.lev[j];
             float *buf[2] = {w->A[p][l], w->B[p][l]};

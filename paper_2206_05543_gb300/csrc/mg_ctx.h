@@ -64,6 +64,8 @@ constexpr size_t kNormBytes = 2 * sizeof(double);
 mg_status cuda_fail(cudaError_t e);
 void free_adjoint(mg_ctx *c);
 void free_batch(mg_ctx *c);
+// batched contexts: FP32 cycles per refinement iteration (re-records the cycle graph)
+mg_status batch_set_inner(mg_ctx *c, int inner);
 // Record the work issued by body() on the context's stream into a CUDA graph;
 // *nodes receives the number of kernels it launches per replay.
 mg_status capture_graph(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nodes,

@@ -814,7 +814,8 @@ mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs)
 
 mg_status mg_set_refinement_cycles(mg_ctx *ctx, int cycles)
 {
-    if (!ctx || ctx->batch || ctx->prec != MG_FP32_IR || cycles < 1 || cycles > 8) return MG_EINVAL;
+    if (ctx && ctx->batch) return batch_set_inner(ctx, cycles);
+    if (!ctx || ctx->prec != MG_FP32_IR || cycles < 1 || cycles > 8) return MG_EINVAL;
     if (cudaSetDevice(ctx->dev) != cudaSuccess || cudaStreamSynchronize(ctx->s) != cudaSuccess)
         return cuda_fail(cudaGetLastError());
     ctx->inner = cycles;

@@ -92,7 +92,8 @@ template <typename OutT>
 cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s,
                                       long opitch = 0, long ooff = 0);
 int residual2d_batched_tiles(int n);
-cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, bool zero_u,
+// mode 0: every item from its u; 1: from zero; 2: per item (u == nullptr: from zero)
+cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, int mode,
                                       const double *c, cudaStream_t s);
 cudaError_t launch_resrestrict2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int Hc,
                                             cudaStream_t s);

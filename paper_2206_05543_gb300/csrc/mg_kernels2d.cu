@@ -52,27 +52,40 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
         return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : T(0);
     };
 
-    T u_prev = T(0), u_cur = T(0), u_next = T(0);
+    // One barrier per row: at step j the u row j + 1 is written to the other
+    // half of the double buffer (read at step j + 1) next to the residual row
+    // j, and every global load is issued one step before its use.
+    T u_prev = T(0), u_cur = T(0), u_next = T(0), u_nn = T(0), h_next = T(0), h_nn = T(0);
     if (!ZERO_U) {
         u_prev = get(u, y0 - 2, x);
         u_cur = get(u, y0 - 1, x);
+        u_next = get(u, y0, x);
+        su[(y0 - 1) & 1][t + 1] = u_cur;
+        if (t == 0) su[(y0 - 1) & 1][0] = get(u, y0 - 1, x - 1);
+        if (t == kSweepThreads - 1) su[(y0 - 1) & 1][kSweepThreads + 1] = get(u, y0 - 1, x + 1);
+        if (t == 0) h_next = get(u, y0, x - 1);
+        if (t == kSweepThreads - 1) h_next = get(u, y0, x + 1);
+        __syncthreads();
     }
+    T b_cur = get(b, y0 - 1, x);
     T r1 = T(0), r2 = T(0), hp1 = T(0), hp2 = T(0);
     double acc = 0.0;
 
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
-        T bb = get(b, j, x);
+        T bb = b_cur;
+        b_cur = get(b, j + 1, x);  // next step's right-hand side
         if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
         T r;
         if (!ZERO_U) {
-            u_next = get(u, j + 1, x);
-            su[buf][t + 1] = u_cur;
-            if (t == 0) su[buf][0] = get(u, j, x - 1);
-            if (t == kSweepThreads - 1) su[buf][kSweepThreads + 1] = get(u, j, x + 1);
-            __syncthreads();
+            u_nn = get(u, j + 2, x);
+            if (t == 0) h_nn = get(u, j + 2, x - 1);
+            if (t == kSweepThreads - 1) h_nn = get(u, j + 2, x + 1);
             const T s = radd(radd(su[buf][t], su[buf][t + 2]), radd(u_prev, u_next));
             r = radd(rfma(T(-4), u_cur, bb), s);
+            su[1 - buf][t + 1] = u_next;
+            if (t == 0) su[1 - buf][0] = h_next;
+            if (t == kSweepThreads - 1) su[1 - buf][kSweepThreads + 1] = h_next;
         } else {
             r = bb;
         }
@@ -94,6 +107,8 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
         if (!ZERO_U) {
             u_prev = u_cur;
             u_cur = u_next;
+            u_next = u_nn;
+            h_next = h_nn;
         }
     }
     if (NORM) block_sum_store<kSweepThreads>(acc, partial);

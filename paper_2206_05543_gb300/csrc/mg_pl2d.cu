@@ -334,7 +334,8 @@ prolong2d_pl_kernel(const float *__restrict__ e, float *__restrict__ u, Pitch2 g
 // Batched forms (persistent loops over (problem, tile) items; see
 // mg_kernels2d.cu). All problems of one launch share the level size n.
 // ---------------------------------------------------------------------------
-template <bool ZERO_U>
+// MODE 0: every item from its u; 1: every item from zero; 2: per item (u == nullptr: from zero)
+template <int MODE>
 __global__ void __launch_bounds__(kPLThreads)
 sweep2d_pl_batched(const BItem<float> *__restrict__ tab, int nprob, const int *__restrict__ active, Pitch2 g, int H,
                    int bx, int by, float c0, float c1, float c2)
@@ -343,7 +344,12 @@ sweep2d_pl_batched(const BItem<float> *__restrict__ tab, int nprob, const int *_
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int j = it / per, r = it - j * per;
         const BItem<float> e = tab[j];
-        if (active[e.problem]) sweep2d_pl_tile<ZERO_U, false>(e.u, e.b, e.out, g, H, c0, c1, c2, r % bx, r / bx, nullptr);
+        if (active[e.problem]) {
+            if (MODE == 1 || (MODE == 2 && !e.u))
+                sweep2d_pl_tile<true, false>(e.u, e.b, e.out, g, H, c0, c1, c2, r % bx, r / bx, nullptr);
+            else
+                sweep2d_pl_tile<false, false>(e.u, e.b, e.out, g, H, c0, c1, c2, r % bx, r / bx, nullptr);
+        }
         __syncthreads();
     }
 }
@@ -475,19 +481,22 @@ static int pl_persistent_grid(const void *fn, long items)
     return (int)std::max<long>(1, std::min<long>(items, (long)per_sm * num_sms()));
 }
 
-cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, bool zero_u,
+cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, int mode,
                                       const double *c, cudaStream_t s)
 {
     const Pitch2 g = pitch2(n);
     const int bx = (n + kPLCols - 1) / kPLCols, by = (n + H - 1) / H;
     const long items = (long)nprob * bx * by;
     const float c0 = (float)c[0], c1 = (float)c[1], c2 = (float)c[2];
-    if (zero_u)
-        sweep2d_pl_batched<true><<<pl_persistent_grid((const void *)sweep2d_pl_batched<true>, items), kPLThreads, 0, s>>>(
+    if (mode == 1)
+        sweep2d_pl_batched<1><<<pl_persistent_grid((const void *)sweep2d_pl_batched<1>, items), kPLThreads, 0, s>>>(
+            tab, nprob, active, g, H, bx, by, c0, c1, c2);
+    else if (mode == 2)
+        sweep2d_pl_batched<2><<<pl_persistent_grid((const void *)sweep2d_pl_batched<2>, items), kPLThreads, 0, s>>>(
             tab, nprob, active, g, H, bx, by, c0, c1, c2);
     else
-        sweep2d_pl_batched<false><<<pl_persistent_grid((const void *)sweep2d_pl_batched<false>, items), kPLThreads, 0,
-                                    s>>>(tab, nprob, active, g, H, bx, by, c0, c1, c2);
+        sweep2d_pl_batched<0><<<pl_persistent_grid((const void *)sweep2d_pl_batched<0>, items), kPLThreads, 0, s>>>(
+            tab, nprob, active, g, H, bx, by, c0, c1, c2);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2206_05543_gb300.binding import MG_ENOCONV, MG_OK, BatchedSolver, Solver  # noqa: E402
+from paper_2206_05543_gb300.binding import MG_ENOCONV, MG_OK, BatchedSolver, MGError, Solver  # noqa: E402
 
 
 def _dev(a):
@@ -69,3 +69,30 @@ def test_batched_masking_and_edge_cases():
         # solving again with new buffers re-uploads the pointer tables
         us2, st2, cyc2, _ = bsolver.solve([_dev(b) for b in bs], tol=1e-10)
         assert st2 == MG_OK and cyc2[1] == 0 and min(cyc2[0], cyc2[2]) >= 8
+
+
+def test_batched_two_cycles_per_iteration_equals_single_problem_solves():
+    """Two FP32 cycles per refinement iteration: every problem's iterate equals
+    the one-problem solve with the same setting, bit for bit."""
+    Ns = [64, 256, 32, 128, 64, 512]
+    bs = [inputs.uniform(2, N, 200 + i) for i, N in enumerate(Ns)]
+    with BatchedSolver(Ns) as bsolver:
+        bsolver.set_refinement_cycles(2)
+        us, st, cyc, rel = bsolver.solve([_dev(b) for b in bs], tol=1e-10)
+        got = [u.cpu().numpy() for u in us]
+    assert st == MG_OK
+    for i, (N, b) in enumerate(zip(Ns, bs)):
+        with Solver(2, N, precision="fp32_ir") as s:
+            s.set_refinement_cycles(2)
+            info = s.solve(_dev(b), tol=1e-10)
+        assert info.cycles == cyc[i], (i, N)
+        assert np.array_equal(got[i], info.u.cpu().numpy()), (i, N)
+        assert oracle.residual_norm(got[i], b) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
+    assert max(cyc) <= 7
+
+
+def test_batched_several_cycles_needs_no_tail_finest_level():
+    with BatchedSolver([64, 16]) as bsolver:
+        with pytest.raises(MGError):
+            bsolver.set_refinement_cycles(2)
+        bsolver.set_refinement_cycles(1)
