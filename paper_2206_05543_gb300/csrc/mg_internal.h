@@ -80,14 +80,6 @@ struct BRes {  // FP64 residual of one problem's caller arrays
     double *partials;  // residual2d_batched_tiles(n) partial sums
     int problem, pad;
 };
-template <typename T>
-cudaError_t launch_sweep2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int H, bool zero_u,
-                                   const double *c, cudaStream_t s);
-template <typename T>
-cudaError_t launch_resrestrict2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc,
-                                         cudaStream_t s);
-template <typename T>
-cudaError_t launch_prolong2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc, cudaStream_t s);
 template <typename OutT>
 cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s,
                                       long opitch = 0, long ooff = 0);

@@ -28,94 +28,133 @@ namespace mg {
 //   u' = fma(c2, C, fma(c1, E, fma(c0, rh_p, u_p)))
 // The pairs are shared between points: hp(q) = rh(q - x) + rh(q + x) gives
 // E = hp(p) + (rh_S + rh_N) and C = hp(p - y) + hp(p + y).
-// Block: 256 threads, thread t owns column x = 254*bx - 1 + t; threads 1..254
-// write, threads 0 and 255 supply the halo residuals. Rows [y0, y0 + H).
+// Block: two adjacent columns per thread (two independent FP64 chains):
+// 128 threads cover the 256 columns X0 .. X0 + 255 of a strip,
+// X0 = 254 bx - 1; columns 1 .. 254 of the strip are written, 0 and 255
+// supply halo residuals. Rows [y0, y0 + H). One barrier per row: at step j
+// the u row j + 1 goes to the other half of the double buffer next to the
+// residual row j, and every global load is issued one step before its use.
 // ZERO_U: the input is u = 0 (first sweep on a coarse level): rh = bh.
 // NORM: accumulate the squared residual of the input over owned points.
 // ---------------------------------------------------------------------------
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out,
-                                             int n, int H, T c0, T c1, T c2, int hk, int tbx, int tby,
-                                             double *__restrict__ partial)
+                                              int n, int H, T c0, T c1, T c2, int hk, int tbx, int tby,
+                                              double *__restrict__ partial)
 {
-    __shared__ T su[2][kSweepThreads + 2];
-    __shared__ T sr[2][kSweepThreads];
+    constexpr int NT = kSweepThreads / 2;
+    __shared__ T su[2][kSweepThreads + 2];  // [c + 1]: column X0 + c, c in -1 .. 256
+    __shared__ T sr[2][kSweepThreads + 2];
     const int t = threadIdx.x;
-    const int x = tbx * kSweepCols - 1 + t;
-    const int y0 = tby * H;
-    const int y1 = min(y0 + H, n);
-    const bool xin = x >= 0 && x < n;
-    const bool owner = t >= 1 && t <= kSweepCols && xin;
+    const int X0 = tbx * kSweepCols - 1;
+    const int xa = X0 + 2 * t, xb = xa + 1;
+    const int y0 = tby * H, y1 = min(y0 + H, n);
+    const bool ina = xa >= 0 && xa < n, inb = xb >= 0 && xb < n;
+    const bool owna = t >= 1 && ina, ownb = t <= NT - 2 && inb;
+    const bool lt = t == 0, rt = t == NT - 1;
     const size_t ld = (size_t)n;
-
     auto get = [&](const T *a, int yy, int xx) -> T {
         return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : T(0);
     };
-
-    // One barrier per row: at step j the u row j + 1 is written to the other
-    // half of the double buffer (read at step j + 1) next to the residual row
-    // j, and every global load is issued one step before its use.
-    T u_prev = T(0), u_cur = T(0), u_next = T(0), u_nn = T(0), h_next = T(0), h_nn = T(0);
+    T ap = T(0), ac = T(0), an = T(0), ann = T(0), bp = T(0), bc = T(0), bn = T(0), bnn = T(0);
+    T hn = T(0), hnn = T(0);  // halo column of the edge threads, rows j + 1, j + 2
     if (!ZERO_U) {
-        u_prev = get(u, y0 - 2, x);
-        u_cur = get(u, y0 - 1, x);
-        u_next = get(u, y0, x);
-        su[(y0 - 1) & 1][t + 1] = u_cur;
-        if (t == 0) su[(y0 - 1) & 1][0] = get(u, y0 - 1, x - 1);
-        if (t == kSweepThreads - 1) su[(y0 - 1) & 1][kSweepThreads + 1] = get(u, y0 - 1, x + 1);
-        if (t == 0) h_next = get(u, y0, x - 1);
-        if (t == kSweepThreads - 1) h_next = get(u, y0, x + 1);
+        ap = get(u, y0 - 2, xa);
+        bp = get(u, y0 - 2, xb);
+        ac = get(u, y0 - 1, xa);
+        bc = get(u, y0 - 1, xb);
+        an = get(u, y0, xa);
+        bn = get(u, y0, xb);
+        const int buf0 = (y0 - 1) & 1;
+        su[buf0][2 * t + 1] = ac;
+        su[buf0][2 * t + 2] = bc;
+        if (lt) su[buf0][0] = get(u, y0 - 1, xa - 1);
+        if (rt) su[buf0][kSweepThreads + 1] = get(u, y0 - 1, xb + 1);
+        if (lt) hn = get(u, y0, xa - 1);
+        if (rt) hn = get(u, y0, xb + 1);
         __syncthreads();
     }
-    T b_cur = get(b, y0 - 1, x);
-    T r1 = T(0), r2 = T(0), hp1 = T(0), hp2 = T(0);
+    T ba_cur = get(b, y0 - 1, xa), bb_cur = get(b, y0 - 1, xb);
+    T ra1 = T(0), ra2 = T(0), rb1 = T(0), rb2 = T(0), pa1 = T(0), pa2 = T(0), pb1 = T(0), pb2 = T(0);
     double acc = 0.0;
-
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
-        T bb = b_cur;
-        b_cur = get(b, j + 1, x);  // next step's right-hand side
-        if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
-        T r;
+        T fa = ba_cur, fb = bb_cur;
+        ba_cur = get(b, j + 1, xa);
+        bb_cur = get(b, j + 1, xb);
+        if (UNSCALED_B) {
+            fa = scale2(fa, hk);
+            fb = scale2(fb, hk);
+        }
+        T ra, rb;
         if (!ZERO_U) {
-            u_nn = get(u, j + 2, x);
-            if (t == 0) h_nn = get(u, j + 2, x - 1);
-            if (t == kSweepThreads - 1) h_nn = get(u, j + 2, x + 1);
-            const T s = radd(radd(su[buf][t], su[buf][t + 2]), radd(u_prev, u_next));
-            r = radd(rfma(T(-4), u_cur, bb), s);
-            su[1 - buf][t + 1] = u_next;
-            if (t == 0) su[1 - buf][0] = h_next;
-            if (t == kSweepThreads - 1) su[1 - buf][kSweepThreads + 1] = h_next;
+            ann = get(u, j + 2, xa);
+            bnn = get(u, j + 2, xb);
+            if (lt) hnn = get(u, j + 2, xa - 1);
+            if (rt) hnn = get(u, j + 2, xb + 1);
+            const T sa = radd(radd(su[buf][2 * t], bc), radd(ap, an));
+            const T sb = radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn));
+            ra = radd(rfma(T(-4), ac, fa), sa);
+            rb = radd(rfma(T(-4), bc, fb), sb);
+            su[1 - buf][2 * t + 1] = an;
+            su[1 - buf][2 * t + 2] = bn;
+            if (lt) su[1 - buf][0] = hn;
+            if (rt) su[1 - buf][kSweepThreads + 1] = hn;
         } else {
-            r = bb;
+            ra = fa;
+            rb = fb;
         }
-        if (!(xin && j >= 0 && j < n)) r = T(0);
-        if (NORM && owner && j >= y0 && j < y1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
-        sr[buf][t] = r;
+        const bool jin = j >= 0 && j < n;
+        if (!(ina && jin)) ra = T(0);
+        if (!(inb && jin)) rb = T(0);
+        if (NORM && j >= y0 && j < y1) {
+            if (owna) acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
+            if (ownb) acc = fma(to_out<double>(rb), to_out<double>(rb), acc);
+        }
+        sr[buf][2 * t + 1] = ra;
+        sr[buf][2 * t + 2] = rb;
         __syncthreads();
-        const T hp = (t >= 1 && t <= kSweepCols) ? radd(sr[buf][t - 1], sr[buf][t + 1]) : T(0);
-        if (owner && j - 1 >= y0) {  // output row j - 1
-            const T E = radd(hp1, radd(r2, r));
-            const T C = radd(hp2, hp);
-            const T base = ZERO_U ? rmul(c0, r1) : rfma(c0, r1, u_prev);
-            out[(size_t)(j - 1) * ld + x] = rfma(c2, C, rfma(c1, E, base));
+        const T pa = lt ? T(0) : radd(sr[buf][2 * t], rb);
+        const T pb = rt ? T(0) : radd(ra, sr[buf][2 * t + 3]);
+        if (j - 1 >= y0) {  // output row j - 1
+            if (owna) {
+                const T E = radd(pa1, radd(ra2, ra));
+                const T C = radd(pa2, pa);
+                const T base = ZERO_U ? rmul(c0, ra1) : rfma(c0, ra1, ap);
+                out[(size_t)(j - 1) * ld + xa] = rfma(c2, C, rfma(c1, E, base));
+            }
+            if (ownb) {
+                const T E = radd(pb1, radd(rb2, rb));
+                const T C = radd(pb2, pb);
+                const T base = ZERO_U ? rmul(c0, rb1) : rfma(c0, rb1, bp);
+                out[(size_t)(j - 1) * ld + xb] = rfma(c2, C, rfma(c1, E, base));
+            }
         }
-        r2 = r1;
-        r1 = r;
-        hp2 = hp1;
-        hp1 = hp;
+        ra2 = ra1;
+        ra1 = ra;
+        rb2 = rb1;
+        rb1 = rb;
+        pa2 = pa1;
+        pa1 = pa;
+        pb2 = pb1;
+        pb1 = pb;
         if (!ZERO_U) {
-            u_prev = u_cur;
-            u_cur = u_next;
-            u_next = u_nn;
-            h_next = h_nn;
+            ap = ac;
+            ac = an;
+            an = ann;
+            bp = bc;
+            bc = bn;
+            bn = bnn;
+            hn = hnn;
         }
     }
-    if (NORM) block_sum_store<kSweepThreads>(acc, partial);
+    if (NORM) block_sum_store<NT>(acc, partial);
 }
 
+// 128 threads, two columns each; the occupancy bound (10 blocks per SM)
+// keeps the register count at 48, measured fastest for the FP64 form
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads / 2, 10)
 sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int H,
                T c0, T c1, T c2, int hk, double *__restrict__ partials)
 {
@@ -307,63 +346,11 @@ residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 }
 
 // ---------------------------------------------------------------------------
-// Batched forms: one launch covers the same-size level of many problems.
-// The launch is persistent: gridDim.x blocks loop over (problem, tile) items;
-// items of problems whose flag in `active` is 0 are skipped (a converged
-// problem costs nothing). All problems in one launch share n, so the item ->
-// (problem, tile) map is a division.
+// Batched FP64 residual (the refinement step of mg_batched.cu): one launch
+// covers the same-size finest level of many problems. The launch is
+// persistent: gridDim.x blocks loop over (problem, tile) items; items of
+// problems whose flag in `active` is 0 are skipped.
 // ---------------------------------------------------------------------------
-template <typename T, bool ZERO_U>
-__global__ void __launch_bounds__(kSweepThreads)
-sweep2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int H,
-                int bx, int by, T c0, T c1, T c2, int hk)
-{
-    const int per = bx * by, total = nprob * per;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int j = it / per, r = it - j * per;
-        const BItem<T> e = tab[j];
-        if (active[e.problem]) {
-            if (e.flags & 1)
-                sweep2d_tile<T, ZERO_U, true, false>(e.u, e.b, e.out, n, H, c0, c1, c2, hk, r % bx, r / bx, nullptr);
-            else
-                sweep2d_tile<T, ZERO_U, false, false>(e.u, e.b, e.out, n, H, c0, c1, c2, hk, r % bx, r / bx, nullptr);
-        }
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kRestrictThreads)
-resrestrict2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int Hc,
-                      int bx, int by, int hk)
-{
-    const int per = bx * by, total = nprob * per;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int j = it / per, r = it - j * per;
-        const BItem<T> e = tab[j];
-        if (active[e.problem]) {
-            if (e.flags & 1)
-                resrestrict2d_tile<T, true>(e.u, e.b, e.out, n, Hc, hk, r % bx, r / bx);
-            else
-                resrestrict2d_tile<T, false>(e.u, e.b, e.out, n, Hc, hk, r % bx, r / bx);
-        }
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kProlongThreads)
-prolong2d_batched(const BItem<T> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int Hc, int bx,
-                  int by)
-{
-    const int per = bx * by, total = nprob * per;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int j = it / per, r = it - j * per;
-        const BItem<T> e = tab[j];
-        if (active[e.problem]) prolong2d_tile<T>(e.u, e.out, n, Hc, r % bx, r / bx);  // u: coarse e, out: fine u
-    }
-}
-
 // FP64 residual of the caller's arrays, written as OutT, with one partial sum
 // per tile at the item's partial offset.
 template <typename OutT>
@@ -404,7 +391,7 @@ cudaError_t launch_sweep2d(const T *u, const T *b, bool unscaled, T *out, int n,
     const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]);
 #define MG_SWEEP(ZU, UB, NRM) \
-    sweep2d_kernel<T, ZU, UB, NRM><<<grid, kSweepThreads, 0, s>>>(u, b, out, n, g.H, c0, c1, c2, hk, partials)
+    sweep2d_kernel<T, ZU, UB, NRM><<<grid, kSweepThreads / 2, 0, s>>>(u, b, out, n, g.H, c0, c1, c2, hk, partials)
     const bool z = u == nullptr, nrm = partials != nullptr;
     if (z) {
         if (unscaled) {
@@ -478,50 +465,6 @@ static int persistent_grid(const void *fn, int threads, long items)
     return (int)std::max<long>(1, std::min<long>(items, (long)per_sm * num_sms()));
 }
 
-template <typename T>
-cudaError_t launch_sweep2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int H, bool zero_u,
-                                   const double *c, cudaStream_t s)
-{
-    const int bx = (n + kSweepCols - 1) / kSweepCols, by = (n + H - 1) / H;
-    const long items = (long)nprob * bx * by;
-    const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]);
-    const int hk = h2_exponent(n);
-    if (zero_u) {
-        const int g = persistent_grid((const void *)sweep2d_batched<T, true>, kSweepThreads, items);
-        sweep2d_batched<T, true><<<g, kSweepThreads, 0, s>>>(tab, nprob, active, n, H, bx, by, c0, c1, c2, hk);
-    } else {
-        const int g = persistent_grid((const void *)sweep2d_batched<T, false>, kSweepThreads, items);
-        sweep2d_batched<T, false><<<g, kSweepThreads, 0, s>>>(tab, nprob, active, n, H, bx, by, c0, c1, c2, hk);
-    }
-    count_launch(1);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_resrestrict2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc,
-                                         cudaStream_t s)
-{
-    const int nc = (n - 1) / 2;
-    const int bx = (nc + kRestrictCols - 1) / kRestrictCols, by = (nc + Hc - 1) / Hc;
-    const long items = (long)nprob * bx * by;
-    const int g = persistent_grid((const void *)resrestrict2d_batched<T>, kRestrictThreads, items);
-    resrestrict2d_batched<T><<<g, kRestrictThreads, 0, s>>>(tab, nprob, active, n, Hc, bx, by, h2_exponent(n));
-    count_launch(1);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_prolong2d_batched(const BItem<T> *tab, int nprob, const int *active, int n, int Hc, cudaStream_t s)
-{
-    const int nc = (n - 1) / 2;
-    const int bx = (nc + 1 + kProlongThreads - 1) / kProlongThreads, by = (nc + 1 + Hc - 1) / Hc;
-    const long items = (long)nprob * bx * by;
-    const int g = persistent_grid((const void *)prolong2d_batched<T>, kProlongThreads, items);
-    prolong2d_batched<T><<<g, kProlongThreads, 0, s>>>(tab, nprob, active, n, Hc, bx, by);
-    count_launch(1);
-    return cudaGetLastError();
-}
-
 int residual2d_batched_tiles(int n)
 {
     const Grid2 g = sweep2d_grid(n);
@@ -541,16 +484,6 @@ cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const in
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sweep2d_batched<float>(const BItem<float> *, int, const int *, int, int, bool,
-                                                   const double *, cudaStream_t);
-template cudaError_t launch_sweep2d_batched<double>(const BItem<double> *, int, const int *, int, int, bool,
-                                                    const double *, cudaStream_t);
-template cudaError_t launch_resrestrict2d_batched<float>(const BItem<float> *, int, const int *, int, int,
-                                                         cudaStream_t);
-template cudaError_t launch_resrestrict2d_batched<double>(const BItem<double> *, int, const int *, int, int,
-                                                          cudaStream_t);
-template cudaError_t launch_prolong2d_batched<float>(const BItem<float> *, int, const int *, int, int, cudaStream_t);
-template cudaError_t launch_prolong2d_batched<double>(const BItem<double> *, int, const int *, int, int, cudaStream_t);
 template cudaError_t launch_residual2d_batched<float>(const BRes<float> *, int, const int *, int, cudaStream_t, long,
                                                       long);
 template cudaError_t launch_residual2d_batched<double>(const BRes<double> *, int, const int *, int, cudaStream_t, long,
