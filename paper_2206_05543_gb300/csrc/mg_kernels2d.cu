@@ -190,18 +190,27 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
     const bool in0 = fx < n, in1 = fx + 1 < n;
 
     const int f0 = 2 * jc0, f1 = 2 * jc1;  // fine rows f0 .. f1 feed coarse rows jc0 .. jc1-1
+    // one barrier per fine row: the u row f + 1 goes to the other half of the
+    // double buffer at step f; global loads are issued one step before use
+    const bool lt = t == 0, rt = t == kRestrictThreads - 1;
     T ua_prev = get(u, f0 - 1, fx), ub_prev = get(u, f0 - 1, fx + 1);
     T ua = get(u, f0, fx), ub = get(u, f0, fx + 1);
+    T ua_next = get(u, f0 + 1, fx), ub_next = get(u, f0 + 1, fx + 1);
+    T h_next = lt ? get(u, f0 + 1, fx - 1) : rt ? get(u, f0 + 1, fx + 2) : T(0);
+    su[f0 & 1][2 * t + 1] = ua;
+    su[f0 & 1][2 * t + 2] = ub;
+    if (lt) su[f0 & 1][0] = get(u, f0, fx - 1);
+    if (rt) su[f0 & 1][2 * kRestrictThreads + 1] = get(u, f0, fx + 2);
+    T ba_next = get(b, f0, fx), bb_next = get(b, f0, fx + 1);
+    __syncthreads();
     T t1 = T(0), t2 = T(0);  // x-pass of fine rows f-1, f-2
     for (int f = f0; f <= f1; ++f) {
         const int buf = f & 1;
-        const T ua_next = get(u, f + 1, fx), ub_next = get(u, f + 1, fx + 1);
-        su[buf][2 * t + 1] = ua;
-        su[buf][2 * t + 2] = ub;
-        if (t == 0) su[buf][0] = get(u, f, fx - 1);
-        if (t == kRestrictThreads - 1) su[buf][2 * kRestrictThreads + 1] = get(u, f, fx + 2);
-        __syncthreads();
-        T ba = get(b, f, fx), bb = get(b, f, fx + 1);
+        T ba = ba_next, bb = bb_next;
+        ba_next = get(b, f + 1, fx);
+        bb_next = get(b, f + 1, fx + 1);
+        const T ua_nn = get(u, f + 2, fx), ub_nn = get(u, f + 2, fx + 1);
+        const T h_nn = lt ? get(u, f + 2, fx - 1) : rt ? get(u, f + 2, fx + 2) : T(0);
         if (UNSCALED_B) {
             ba = scale2(ba, hk);
             bb = scale2(bb, hk);
@@ -213,7 +222,11 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
         if (!in0 || f >= n) ra = T(0);
         if (!in1 || f >= n) rb = T(0);
         sr[buf][t] = ra;
-        if (t == kRestrictThreads - 1) sr[buf][kRestrictThreads] = T(0);  // never read by a writer
+        if (rt) sr[buf][kRestrictThreads] = T(0);  // never read by a writer
+        su[1 - buf][2 * t + 1] = ua_next;
+        su[1 - buf][2 * t + 2] = ub_next;
+        if (lt) su[1 - buf][0] = h_next;
+        if (rt) su[1 - buf][2 * kRestrictThreads + 1] = h_next;
         __syncthreads();
         const T tx = rfma(T(2), rb, radd(ra, sr[buf][t + 1]));
         if (f >= f0 + 2 && (f & 1) == 0 && t < kRestrictCols && ic < nc) {
@@ -227,11 +240,15 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
         ub_prev = ub;
         ua = ua_next;
         ub = ub_next;
+        ua_next = ua_nn;
+        ub_next = ub_nn;
+        h_next = h_nn;
     }
 }
 
+// at most 6 blocks per SM (measured fastest for the FP64 form)
 template <typename T, bool UNSCALED_B>
-__global__ void __launch_bounds__(kRestrictThreads)
+__global__ void __launch_bounds__(kRestrictThreads, 6)
 resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
                      int Hc, int hk)
 {
@@ -294,8 +311,9 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
 // ---------------------------------------------------------------------------
 // FP64 residual for iterative refinement: rh = fma(-4, u, h^2 b) + s exactly
 // as in the sweep, written as OutT (the cycle's precision) together with one
-// partial sum of rh^2 per block. Same marching layout as the sweep (threads
-// 0 and 255 only supply the u halo).
+// partial sum of rh^2 per block. Same layout as the sweep: 128 threads, two
+// adjacent columns each (columns 1 .. 254 of the strip are written), one
+// barrier per row, loads one step ahead.
 // ---------------------------------------------------------------------------
 template <typename InT, typename OutT>
 __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const InT *__restrict__ b,
@@ -303,41 +321,70 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
                                                 int tbx, int tby, double *__restrict__ partial, long opitch = 0,
                                                 long ooff = 0)
 {
-    __shared__ InT su[2][kSweepThreads + 2];
+    constexpr int NT = kSweepThreads / 2;
+    __shared__ InT su[2][kSweepThreads + 2];  // [c + 1]: column X0 + c, c in -1 .. 256
     const int t = threadIdx.x;
-    const int x = tbx * kSweepCols - 1 + t;
+    const int X0 = tbx * kSweepCols - 1;
+    const int xa = X0 + 2 * t, xb = xa + 1;
     const int y0 = tby * H;
     const int y1 = min(y0 + H, n);
-    const bool owner = t >= 1 && t <= kSweepCols && x < n;
+    const bool owna = t >= 1 && xa < n, ownb = t <= NT - 2 && xb < n;
+    const bool lt = t == 0, rt = t == NT - 1;
     const size_t ld = (size_t)n;
     auto get = [&](const InT *a, int yy, int xx) -> InT {
         return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : InT(0);
     };
-    InT u_prev = get(u, y0 - 1, x), u_cur = get(u, y0, x);
+    InT ap = get(u, y0 - 1, xa), bp = get(u, y0 - 1, xb);
+    InT ac = get(u, y0, xa), bc = get(u, y0, xb);
+    InT an = get(u, y0 + 1, xa), bn = get(u, y0 + 1, xb);
+    InT hn = lt ? get(u, y0 + 1, xa - 1) : rt ? get(u, y0 + 1, xb + 1) : InT(0);
+    su[y0 & 1][2 * t + 1] = ac;
+    su[y0 & 1][2 * t + 2] = bc;
+    if (lt) su[y0 & 1][0] = get(u, y0, xa - 1);
+    if (rt) su[y0 & 1][kSweepThreads + 1] = get(u, y0, xb + 1);
+    InT fa_next = get(b, y0, xa), fb_next = get(b, y0, xb);
+    __syncthreads();
     double acc = 0.0;
     for (int j = y0; j < y1; ++j) {
         const int buf = j & 1;
-        const InT u_next = get(u, j + 1, x);
-        su[buf][t + 1] = u_cur;
-        if (t == 0) su[buf][0] = get(u, j, x - 1);
-        if (t == kSweepThreads - 1) su[buf][kSweepThreads + 1] = get(u, j, x + 1);
-        __syncthreads();
-        if (owner) {
-            const InT s = radd(radd(su[buf][t], su[buf][t + 2]), radd(u_prev, u_next));
-            InT bb = b[(size_t)j * ld + x];
-            if (unscaled) bb = scale2(bb, hk);
-            const InT r = radd(rfma(InT(-4), u_cur, bb), s);
-            acc = fma(to_out<double>(r), to_out<double>(r), acc);
-            if (rh_out) rh_out[opitch ? ooff + j * opitch + x : (long)j * ld + x] = to_out<OutT>(r);
+        InT fa = fa_next, fb = fb_next;
+        fa_next = get(b, j + 1, xa);
+        fb_next = get(b, j + 1, xb);
+        const InT ann = get(u, j + 2, xa), bnn = get(u, j + 2, xb);
+        const InT hnn = lt ? get(u, j + 2, xa - 1) : rt ? get(u, j + 2, xb + 1) : InT(0);
+        if (unscaled) {
+            fa = scale2(fa, hk);
+            fb = scale2(fb, hk);
         }
-        u_prev = u_cur;
-        u_cur = u_next;
+        const InT ra = radd(rfma(InT(-4), ac, fa), radd(radd(su[buf][2 * t], bc), radd(ap, an)));
+        const InT rb = radd(rfma(InT(-4), bc, fb), radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn)));
+        if (owna) {
+            acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
+            if (rh_out) rh_out[opitch ? ooff + j * opitch + xa : (long)j * ld + xa] = to_out<OutT>(ra);
+        }
+        if (ownb) {
+            acc = fma(to_out<double>(rb), to_out<double>(rb), acc);
+            if (rh_out) rh_out[opitch ? ooff + j * opitch + xb : (long)j * ld + xb] = to_out<OutT>(rb);
+        }
+        su[1 - buf][2 * t + 1] = an;
+        su[1 - buf][2 * t + 2] = bn;
+        if (lt) su[1 - buf][0] = hn;
+        if (rt) su[1 - buf][kSweepThreads + 1] = hn;
+        __syncthreads();
+        ap = ac;
+        ac = an;
+        an = ann;
+        bp = bc;
+        bc = bn;
+        bn = bnn;
+        hn = hnn;
     }
-    if (partial) block_sum_store<kSweepThreads>(acc, partial);
+    if (partial) block_sum_store<NT>(acc, partial);
 }
 
+// at most 12 blocks per SM (measured fastest for the FP64 form)
 template <typename InT, typename OutT>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads / 2, 12)
 residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
                   int n, int H, int hk, bool unscaled, double *__restrict__ partials, long opitch, long ooff)
 {
@@ -354,7 +401,7 @@ residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 // FP64 residual of the caller's arrays, written as OutT, with one partial sum
 // per tile at the item's partial offset.
 template <typename OutT>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads / 2, 12)
 residual2d_batched(const BRes<OutT> *__restrict__ tab, int nprob, const int *__restrict__ active, int n, int H,
                    int bx, int by, int hk, long opitch, long ooff)
 {
@@ -444,7 +491,7 @@ cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *r
                               cudaStream_t s, long out_pitch, long out_off)
 {
     const Grid2 g = sweep2d_grid(n);
-    residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads, 0, s>>>(u, b, rh, n, g.H, h2_exponent(n),
+    residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads / 2, 0, s>>>(u, b, rh, n, g.H, h2_exponent(n),
                                                                            unscaled, partials, out_pitch, out_off);
     count_launch(1);
     return cudaGetLastError();
@@ -477,8 +524,8 @@ cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const in
 {
     const Grid2 g = sweep2d_grid(n);
     const long items = (long)nprob * g.bx * g.by;
-    const int grid = persistent_grid((const void *)residual2d_batched<OutT>, kSweepThreads, items);
-    residual2d_batched<OutT><<<grid, kSweepThreads, 0, s>>>(tab, nprob, active, n, g.H, g.bx, g.by, h2_exponent(n),
+    const int grid = persistent_grid((const void *)residual2d_batched<OutT>, kSweepThreads / 2, items);
+    residual2d_batched<OutT><<<grid, kSweepThreads / 2, 0, s>>>(tab, nprob, active, n, g.H, g.bx, g.by, h2_exponent(n),
                                                             opitch, ooff);
     count_launch(1);
     return cudaGetLastError();
