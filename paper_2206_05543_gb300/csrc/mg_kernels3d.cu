@@ -32,15 +32,20 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 //   u' = fma(c1, E, fma(c0, rh_p, u_p))
 // (W/E = x-1/x+1, S/N = y-1/y+1, D/U = z-1/z+1). A block computes rh on a
 // 32x32 tile (output tile 30x30 plus its halo), thread t holding the tile
-// points t, t+256, t+512, t+768 with their z-windows in registers.
+// points t, t+256, t+512, t+768 with their z-windows in registers. One
+// barrier per plane: at step zz the u plane zz + 1 goes to the other half of
+// the double buffer next to the residual plane zz, the update of plane zz - 1
+// reads the residual plane written one step earlier, and every global load
+// is issued one step before its use.
 // ---------------------------------------------------------------------------
+// at most 4 blocks per SM (64 registers; measured fastest for the FP64 form)
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__global__ void __launch_bounds__(kS3Threads)
+__global__ void __launch_bounds__(kS3Threads, 4)
 sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int Z,
                T c0, T c1, int hk, double *__restrict__ partials)
 {
     __shared__ T su[2][kS3U * kS3U];
-    __shared__ T sr[3][kS3 * kS3];  // three planes: the output reads the previous one
+    __shared__ T sr[2][kS3 * kS3];
     const int t = threadIdx.x;
     const int ex0 = blockIdx.x * kS3Out - 1, ey0 = blockIdx.y * kS3Out - 1;
     const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
@@ -48,7 +53,7 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 
     int px[kS3Pts], py[kS3Pts];
     bool inside[kS3Pts], own[kS3Pts];
-    T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], r_m1[kS3Pts], r_0[kS3Pts];
+    T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], b_next[kS3Pts], r_m1[kS3Pts], r_0[kS3Pts];
 #pragma unroll
     for (int k = 0; k < kS3Pts; ++k) {
         const int i = (t + k * kS3Threads) % kS3, j = (t + k * kS3Threads) / kS3;
@@ -58,38 +63,51 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
         own[k] = inside[k] && i >= 1 && i <= kS3Out && j >= 1 && j <= kS3Out;
         u_prev[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0 - 2);
         u_cur[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0 - 1);
-        u_next[k] = T(0);
+        u_next[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0);
+        b_next[k] = get3(b, n, px[k], py[k], z0 - 1);
         r_m1[k] = T(0);
         r_0[k] = T(0);
+    }
+    // the one-point ring around the 32x32 tile: 4 * 33 = 132 points, one per
+    // thread t < 132 (tile-relative (ri, rj) in [-1, 32])
+    const bool ring = !ZERO_U && t < 4 * (kS3 + 1);
+    int ri = 0, rj = 0;
+    if (ring) {
+        const int side = t / (kS3 + 1), q = t % (kS3 + 1);
+        if (side == 0) { ri = q - 1; rj = -1; }
+        else if (side == 1) { ri = kS3; rj = q - 1; }
+        else if (side == 2) { ri = q; rj = kS3; }
+        else { ri = -1; rj = q; }
+    }
+    T ring_next = T(0);
+    if (!ZERO_U) {
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) {
+            const int i = px[k] - ex0, j = py[k] - ey0;
+            su[(z0 - 1) & 1][(j + 1) * kS3U + (i + 1)] = u_cur[k];
+        }
+        if (ring) {
+            su[(z0 - 1) & 1][(rj + 1) * kS3U + (ri + 1)] = get3(u, n, ex0 + ri, ey0 + rj, z0 - 1);
+            ring_next = get3(u, n, ex0 + ri, ey0 + rj, z0);
+        }
+        __syncthreads();
     }
     double acc = 0.0;
 
     for (int zz = z0 - 1; zz <= z1; ++zz) {  // residual plane zz, output plane zz - 1
         const int buf = zz & 1;
+        T r_new[kS3Pts], u_nn[kS3Pts];
+        T ring_nn = T(0);
         if (!ZERO_U) {
 #pragma unroll
-            for (int k = 0; k < kS3Pts; ++k) {
-                u_next[k] = get3(u, n, px[k], py[k], zz + 1);
-                const int i = px[k] - ex0, j = py[k] - ey0;
-                su[buf][(j + 1) * kS3U + (i + 1)] = u_cur[k];
-            }
-            // the one-point ring around the 32x32 tile: 4 * 33 = 132 points
-            if (t < 4 * (kS3 + 1)) {
-                const int side = t / (kS3 + 1), q = t % (kS3 + 1);
-                int i, j;  // tile-relative, in [-1, 32]
-                if (side == 0) { i = q - 1; j = -1; }
-                else if (side == 1) { i = kS3; j = q - 1; }
-                else if (side == 2) { i = q; j = kS3; }
-                else { i = -1; j = q; }
-                su[buf][(j + 1) * kS3U + (i + 1)] = get3(u, n, ex0 + i, ey0 + j, zz);
-            }
-            __syncthreads();
+            for (int k = 0; k < kS3Pts; ++k) u_nn[k] = get3(u, n, px[k], py[k], zz + 2);
+            if (ring) ring_nn = get3(u, n, ex0 + ri, ey0 + rj, zz + 2);
         }
-        T r_new[kS3Pts];
 #pragma unroll
         for (int k = 0; k < kS3Pts; ++k) {
             const int i = px[k] - ex0, j = py[k] - ey0;
-            T bb = get3(b, n, px[k], py[k], zz);
+            T bb = b_next[k];
+            b_next[k] = get3(b, n, px[k], py[k], zz + 1);
             if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
             T r;
             if (!ZERO_U) {
@@ -97,17 +115,18 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
                 const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kS3U], row[kS3U])),
                                  radd(u_prev[k], u_next[k]));
                 r = radd(rfma(T(-6), u_cur[k], bb), s);
+                su[1 - buf][(j + 1) * kS3U + (i + 1)] = u_next[k];
             } else {
                 r = bb;
             }
             if (!(inside[k] && zz >= 0 && zz < n)) r = T(0);
             if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
             r_new[k] = r;
-            sr[(zz + 3) % 3][j * kS3 + i] = r;
+            sr[buf][j * kS3 + i] = r;
         }
-        __syncthreads();
+        if (ring) su[1 - buf][(rj + 1) * kS3U + (ri + 1)] = ring_next;
         if (zz - 1 >= z0) {
-            const T *rp = sr[(zz + 2) % 3];  // plane zz - 1
+            const T *rp = sr[1 - buf];  // plane zz - 1, written at the previous step
 #pragma unroll
             for (int k = 0; k < kS3Pts; ++k) {
                 if (!own[k]) continue;
@@ -119,6 +138,7 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
                 out[(size_t)(zz - 1) * plane + (size_t)py[k] * n + px[k]] = rfma(c1, E, base);
             }
         }
+        __syncthreads();
 #pragma unroll
         for (int k = 0; k < kS3Pts; ++k) {
             r_m1[k] = r_0[k];
@@ -126,8 +146,10 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
             if (!ZERO_U) {
                 u_prev[k] = u_cur[k];
                 u_cur[k] = u_next[k];
+                u_next[k] = u_nn[k];
             }
         }
+        ring_next = ring_nn;
     }
     if (NORM) block_sum_store<kS3Threads>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
 }
@@ -141,14 +163,16 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 //   bh_c = 0.0625 v        (= 4 R rh, R = (1,2,1)/4 per axis)
 // Block: 16x16 coarse columns; per fine plane the residual on the 33x33 fine
 // patch is formed in shared memory from a ring of three u planes.
+// (The load of a plane into the ring happens one step after its global read.)
 // ---------------------------------------------------------------------------
 constexpr int kR3 = 16;              // coarse tile edge
 constexpr int kR3F = 2 * kR3 + 1;    // fine residual patch edge (33)
 constexpr int kR3U = kR3F + 2;       // u patch edge incl. halo (35)
 constexpr int kR3Threads = kR3 * kR3;
 
+// at most 4 blocks per SM (64 registers; measured fastest for the FP64 form)
 template <typename T, bool UNSCALED_B>
-__global__ void __launch_bounds__(kR3Threads)
+__global__ void __launch_bounds__(kR3Threads, 4)
 resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n, int Zc,
                      int hk)
 {
@@ -165,26 +189,60 @@ resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
     const int f0 = 2 * kc0, f1 = 2 * kc1;
     const size_t plane = (size_t)n * n;
 
-    auto load_plane = [&](int slot, int fz) {
-        for (int q = t; q < kR3U * kR3U; q += kR3Threads) {
-            const int i = q % kR3U - 1, j = q / kR3U - 1;
-            su[slot][q] = get3(u, n, fx0 + i, fy0 + j, fz);
+    // each thread moves the same (at most 5) points of every u plane and b
+    // plane; the copies of plane f + 2 (u) and f + 1 (b) are loaded into
+    // registers at step f, so their latency overlaps a step of work
+    constexpr int kLU = (kR3U * kR3U + kR3Threads - 1) / kR3Threads;
+    constexpr int kLB = (kR3F * kR3F + kR3Threads - 1) / kR3Threads;
+    T upre[kLU], bpre[kLB];
+    auto fetch_u = [&](int fz) {
+#pragma unroll
+        for (int k = 0; k < kLU; ++k) {
+            const int q = t + k * kR3Threads;
+            upre[k] = q < kR3U * kR3U ? get3(u, n, fx0 + q % kR3U - 1, fy0 + q / kR3U - 1, fz) : T(0);
         }
     };
-    load_plane((f0 - 1 + 3) % 3, f0 - 1);
-    load_plane(f0 % 3, f0);
+    auto store_u = [&](int slot) {
+#pragma unroll
+        for (int k = 0; k < kLU; ++k) {
+            const int q = t + k * kR3Threads;
+            if (q < kR3U * kR3U) su[slot][q] = upre[k];
+        }
+    };
+    auto fetch_b = [&](int fz) {
+#pragma unroll
+        for (int k = 0; k < kLB; ++k) {
+            const int q = t + k * kR3Threads;
+            const int x = fx0 + q % kR3F, y = fy0 + q / kR3F;
+            bpre[k] = (q < kR3F * kR3F && x < n && y < n && fz < n) ? b[(size_t)fz * plane + (size_t)y * n + x] : T(0);
+        }
+    };
+    fetch_u(f0 - 1);
+    store_u((f0 - 1 + 3) % 3);
+    fetch_u(f0);
+    store_u(f0 % 3);
+    fetch_u(f0 + 1);
+    fetch_b(f0);
     T t2a = T(0), t2b = T(0);  // y-pass of fine planes f-2, f-1
     for (int f = f0; f <= f1; ++f) {
-        load_plane((f + 1) % 3, f + 1);
+        store_u((f + 1) % 3);
+        T bb_k[kLB];
+#pragma unroll
+        for (int k = 0; k < kLB; ++k) bb_k[k] = bpre[k];
+        fetch_u(f + 2);
+        fetch_b(f + 1);
         __syncthreads();
         const T *um = su[(f + 2) % 3], *uc = su[f % 3], *up = su[(f + 1) % 3];
-        for (int q = t; q < kR3F * kR3F; q += kR3Threads) {
+#pragma unroll
+        for (int k = 0; k < kLB; ++k) {
+            const int q = t + k * kR3Threads;
+            if (q >= kR3F * kR3F) break;
             const int i = q % kR3F, j = q / kR3F;
             const int x = fx0 + i, y = fy0 + j;
             const int p = (j + 1) * kR3U + (i + 1);
             T r = T(0);
             if (x < n && y < n && f < n) {
-                T bb = b[(size_t)f * plane + (size_t)y * n + x];
+                T bb = bb_k[k];
                 if (UNSCALED_B) bb = scale2(bb, hk);
                 const T s = radd(radd(radd(uc[p - 1], uc[p + 1]), radd(uc[p - kR3U], uc[p + kR3U])),
                                  radd(um[p], up[p]));
