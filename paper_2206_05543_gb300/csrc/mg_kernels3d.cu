@@ -321,39 +321,93 @@ prolong3d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Zc)
 
 // ---------------------------------------------------------------------------
 // Scaled residual rh = fma(-6, u, bh) + s (as in the sweep), InT arithmetic,
-// written as OutT, with one squared partial sum per block. Thread per (x, y)
-// column of a 32x8 tile; in-plane neighbours from global memory (L1).
+// written as OutT, with one squared partial sum per block. A block owns a
+// 64 x 8 tile of (x, y) columns, thread t the two adjacent columns
+// 2 (t % 32), 2 (t % 32) + 1 of row t / 32, and marches along z; the
+// in-plane neighbours come from a double-buffered shared plane (tile plus a
+// one-point ring), one barrier per plane, every global load one plane ahead.
 // ---------------------------------------------------------------------------
+constexpr int kQX = 64, kQY = 8, kQThreads = 256, kQW = kQX + 2;
+constexpr int kQRing = 2 * kQX + 2 * kQY;  // 144 ring points, one per thread t < 144
+
+// at most 6 blocks per SM (42 registers; measured fastest for the FP64 form)
 template <typename InT, typename OutT>
-__global__ void __launch_bounds__(kP3X * kP3Y)
+__global__ void __launch_bounds__(kQThreads, 6)
 residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out, int n,
                   int Z, int hk, bool unscaled, double *__restrict__ partials, long opitch, long oplane, long ooff)
 {
-    const int x = blockIdx.x * kP3X + threadIdx.x % kP3X;
-    const int y = blockIdx.y * kP3Y + threadIdx.x / kP3X;
+    __shared__ InT su[2][(kQY + 2) * kQW];  // [(j + 1) * kQW + i + 1]: tile point (i, j), i in -1 .. 64
+    const int t = threadIdx.x;
+    const int tx = t % (kQX / 2), ty = t / (kQX / 2);
+    const int X0 = blockIdx.x * kQX, Y0 = blockIdx.y * kQY;
+    const int xa = X0 + 2 * tx, xb = xa + 1, y = Y0 + ty;
     const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
-    const bool in = x < n && y < n;
-    const size_t plane = (size_t)n * n;
+    const bool owna = xa < n && y < n, ownb = xb < n && y < n;
+    const int ia = (ty + 1) * kQW + 2 * tx + 1;  // shared index of column xa
+    // ring point of this thread (tile-relative (ri, rj))
+    const bool ring = t < kQRing;
+    int ri = 0, rj = 0;
+    if (t < kQX) { ri = t; rj = -1; }
+    else if (t < 2 * kQX) { ri = t - kQX; rj = kQY; }
+    else if (t < 2 * kQX + kQY) { ri = -1; rj = t - 2 * kQX; }
+    else { ri = kQX; rj = t - 2 * kQX - kQY; }
+    const int ir = (rj + 1) * kQW + ri + 1;
+
+    InT ap = get3(u, n, xa, y, z0 - 1), bp = get3(u, n, xb, y, z0 - 1);
+    InT ac = get3(u, n, xa, y, z0), bc = get3(u, n, xb, y, z0);
+    InT an = get3(u, n, xa, y, z0 + 1), bn = get3(u, n, xb, y, z0 + 1);
+    InT fa_next = get3(b, n, xa, y, z0), fb_next = get3(b, n, xb, y, z0);
+    InT ring_next = InT(0);
+    su[z0 & 1][ia] = ac;
+    su[z0 & 1][ia + 1] = bc;
+    if (ring) {
+        su[z0 & 1][ir] = get3(u, n, X0 + ri, Y0 + rj, z0);
+        ring_next = get3(u, n, X0 + ri, Y0 + rj, z0 + 1);
+    }
+    __syncthreads();
     double acc = 0.0;
-    if (in) {
-        InT u_prev = get3(u, n, x, y, z0 - 1), u_cur = get3(u, n, x, y, z0);
-        for (int z = z0; z < z1; ++z) {
-            const InT u_next = get3(u, n, x, y, z + 1);
-            const InT s = radd(radd(radd(get3(u, n, x - 1, y, z), get3(u, n, x + 1, y, z)),
-                                    radd(get3(u, n, x, y - 1, z), get3(u, n, x, y + 1, z))),
-                               radd(u_prev, u_next));
-            const size_t p = (size_t)z * plane + (size_t)y * n + x;
-            InT bb = b[p];
-            if (unscaled) bb = scale2(bb, hk);
-            const InT r = radd(rfma(InT(-6), u_cur, bb), s);
-            acc = fma(to_out<double>(r), to_out<double>(r), acc);
-            if (rh_out) rh_out[opitch ? ooff + z * oplane + (long)y * opitch + x : (long)p] = to_out<OutT>(r);
-            u_prev = u_cur;
-            u_cur = u_next;
+    for (int z = z0; z < z1; ++z) {
+        const int buf = z & 1;
+        InT fa = fa_next, fb = fb_next;
+        fa_next = get3(b, n, xa, y, z + 1);
+        fb_next = get3(b, n, xb, y, z + 1);
+        const InT ann = get3(u, n, xa, y, z + 2), bnn = get3(u, n, xb, y, z + 2);
+        const InT ring_nn = ring ? get3(u, n, X0 + ri, Y0 + rj, z + 2) : InT(0);
+        if (unscaled) {
+            fa = scale2(fa, hk);
+            fb = scale2(fb, hk);
         }
+        const InT *P = su[buf];
+        const InT sa = radd(radd(radd(P[ia - 1], bc), radd(P[ia - kQW], P[ia + kQW])), radd(ap, an));
+        const InT sb = radd(radd(radd(ac, P[ia + 2]), radd(P[ia + 1 - kQW], P[ia + 1 + kQW])), radd(bp, bn));
+        const InT ra = radd(rfma(InT(-6), ac, fa), sa);
+        const InT rb = radd(rfma(InT(-6), bc, fb), sb);
+        if (owna) {
+            acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
+            if (rh_out)
+                rh_out[opitch ? ooff + z * oplane + (long)y * opitch + xa : ((long)z * n + y) * n + xa] =
+                    to_out<OutT>(ra);
+        }
+        if (ownb) {
+            acc = fma(to_out<double>(rb), to_out<double>(rb), acc);
+            if (rh_out)
+                rh_out[opitch ? ooff + z * oplane + (long)y * opitch + xb : ((long)z * n + y) * n + xb] =
+                    to_out<OutT>(rb);
+        }
+        su[1 - buf][ia] = an;
+        su[1 - buf][ia + 1] = bn;
+        if (ring) su[1 - buf][ir] = ring_next;
+        __syncthreads();
+        ap = ac;
+        ac = an;
+        an = ann;
+        bp = bc;
+        bc = bn;
+        bn = bnn;
+        ring_next = ring_nn;
     }
     if (partials)
-        block_sum_store<kP3X * kP3Y>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
+        block_sum_store<kQThreads>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,8 +425,8 @@ Grid3 sweep3d_grid(int n)
 Grid3 residual3d_grid(int n)
 {
     Grid3 g;
-    g.bx = (n + kP3X - 1) / kP3X;
-    g.by = (n + kP3Y - 1) / kP3Y;
+    g.bx = (n + kQX - 1) / kQX;
+    g.by = (n + kQY - 1) / kQY;
     g.Z = chunk_rows(g.bx * g.by, n, 8 * num_sms(), 4, 64);
     g.bz = (n + g.Z - 1) / g.Z;
     return g;
@@ -440,7 +494,7 @@ cudaError_t launch_residual3d(const InT *u, const InT *b, bool unscaled, OutT *r
                               cudaStream_t s, long out_pitch, long out_plane, long out_off)
 {
     const Grid3 g = residual3d_grid(n);
-    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kP3X * kP3Y, 0, s>>>(
+    residual3d_kernel<InT, OutT><<<dim3(g.bx, g.by, g.bz), kQThreads, 0, s>>>(
         u, b, rh, n, g.Z, h2_exponent(n), unscaled, partials, out_pitch, out_plane, out_off);
     count_launch(1);
     return cudaGetLastError();
