@@ -294,24 +294,39 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
 
 // ---------------------------------------------------------------------------
 // Residual + full weighting on TMA-staged planes (formula and order as
-// resrestrict3d_kernel): a block owns 16 x 16 coarse columns, i.e. a 33 x 33
-// fine residual patch per fine plane. u boxes (40 columns from 2 ic0 - 4,
-// 35 rows from 2 jc0 - 1) and b boxes (40 columns, 33 rows from 2 jc0) of
-// each fine plane arrive in rings kAhead planes ahead, as in the sweep. Per
-// fine plane f: residual patch (all warps) -> barrier (u plane f-1 and b
-// plane f are dead: refill) -> x-pass -> barrier -> y-pass, z-combination
-// and output of every second plane -> wait for the next planes -> barrier.
+// resrestrict3d_kernel), as a warp pipeline without block barriers. A block
+// owns 32 x 16 coarse columns. Consumer warp w (of 8) owns coarse rows
+// jc0 + 2w, jc0 + 2w + 1 and lane l the coarse column ic = ic0 + l; per
+// fine plane f the warp walks its 5 fine rows y = 2 (jc0 + 2w) + r with a
+// rolling window of u rows in registers: lane l forms the residuals at fine
+// columns 2ic + 1 and 2ic + 2, takes the one at 2ic from lane l - 1 by a
+// shuffle (lane 0 computes it), does the x pass, the y pass every second row
+// and the z pass every second plane, all in registers. The helper warp's lane
+// 0 fills rings of u planes (72 x 35 boxes from fine column 2 ic0 - 4, row
+// 2 jc0 - 1) and b planes (72 x 33 from row 2 jc0), one plane ahead of
+// the consumers' next step, through "full" mbarriers
+// (expect_tx); each consumer warp releases a slot through an "empty"
+// mbarrier (one arrival per warp) once it has read it. Every wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr int kRQ = 16;                 // coarse tile edge
-constexpr int kRF = 2 * kRQ + 1;        // 33 fine residual points per row
-constexpr int kRW = 40;                 // box width: fine columns 2 ic0 - 4 .. 2 ic0 + 35
-constexpr int kRUR = kRF + 2;           // 35 u rows
-constexpr int kRCons = kRQ * kRQ;       // 256 threads own one coarse column each
-constexpr int kRThreads = kRCons + 32;  // + helper warp
-constexpr int kRUSlots = 3 + kAhead, kRBSlots = 1 + kAhead;
-constexpr int kRUBox = kRUR * kRW * 4, kRBBox = kRF * kRW * 4;
+constexpr int kRX = 32;                  // coarse columns per block (one per lane)
+constexpr int kRWarps = 8;               // consumer warps
+constexpr int kRRows = 2;                // coarse rows per consumer warp
+constexpr int kRY = kRWarps * kRRows;    // 16 coarse rows per block
+constexpr int kRW = 72;                  // box width: fine columns 2 ic0 - 4 .. 2 ic0 + 67
+constexpr int kRUR = 2 * kRY + 3;        // 35 u rows: fine rows 2 jc0 - 1 .. 2 jc0 + 33
+constexpr int kRBR = 2 * kRY + 1;        // 33 b rows: fine rows 2 jc0 .. 2 jc0 + 32
+constexpr int kRThreads = 32 * (kRWarps + 1);
+// one plane of prefetch (smaller rings: three blocks per SM; measured faster)
+constexpr int kRUSlots = 4, kRBSlots = 2;
+constexpr int kRUBox = kRUR * kRW * 4, kRBBox = kRBR * kRW * 4;
 constexpr int kRUSlotBytes = (kRUBox + 127) / 128 * 128, kRBSlotBytes = (kRBBox + 127) / 128 * 128;
 constexpr int kRSmemBytes = kRUSlots * kRUSlotBytes + kRBSlots * kRBSlotBytes + 128;
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ float2 ld2s(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 
 __global__ void __launch_bounds__(kRThreads)
 resrestrict3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant__ CUtensorMap tb,
@@ -321,110 +336,150 @@ resrestrict3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_co
     unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     float *const su = (float *)base;
     float *const sb = (float *)(base + kRUSlots * kRUSlotBytes);
-    __shared__ float sr[kRF][kRF + 1];
-    __shared__ float st1[kRF][kRQ + 1];
-    __shared__ __align__(8) unsigned long long bars[kRUSlots + kRBSlots];
-    __shared__ int s_fail;
-    constexpr int kUF = kRUSlotBytes / 4, kBF = kRBSlotBytes / 4;
+    // full[0 .. kRUSlots + kRBSlots), then empty[same]
+    __shared__ __align__(8) unsigned long long bars[2 * (kRUSlots + kRBSlots)];
+    __shared__ volatile int s_fail;
+    constexpr int kUF = kRUSlotBytes / 4, kBF = kRBSlotBytes / 4, kNB = kRUSlots + kRBSlots;
 
-    const int n = g.n, nc = gc.n, t = threadIdx.x;
-    const bool producer = t == kRCons;
-    const int tic = t % kRQ, tjc = t / kRQ;
-    const int ic0 = blockIdx.x * kRQ, jc0 = blockIdx.y * kRQ;
-    const int ic = ic0 + tic, jc = jc0 + tjc;
+    const int n = g.n, nc = gc.n, t = threadIdx.x, warp = t / 32, lane = t % 32;
+    const int ic0 = blockIdx.x * kRX, jc0 = blockIdx.y * kRY;
     const int fx0 = 2 * ic0, fy0 = 2 * jc0;
     const int kc0 = blockIdx.z * Zc, kc1 = min(kc0 + Zc, nc);
     const int f0 = 2 * kc0, f1 = 2 * kc1;
-    const int ufirst = f0 - 1, bfirst = f0, ulast = f1 + 1, blast = f1;
-    auto ubar = [&](int p) { return smem_u32(&bars[(p - ufirst) % kRUSlots]); };
-    auto bbar = [&](int p) { return smem_u32(&bars[kRUSlots + (p - bfirst) % kRBSlots]); };
+    const int ufirst = f0 - 1, bfirst = f0, blast = f1;  // u planes f0 - 1 .. f1 + 1
+    auto uslot = [&](int p) { return (p - ufirst) % kRUSlots; };
+    auto bslot = [&](int p) { return (p - bfirst) % kRBSlots; };
     auto upar = [&](int p) { return (unsigned)(((p - ufirst) / kRUSlots) & 1); };
     auto bpar = [&](int p) { return (unsigned)(((p - bfirst) / kRBSlots) & 1); };
-    int u_issued = ufirst - 1, u_done = ufirst - 1, b_issued = bfirst - 1, b_done = bfirst - 1;
-    // tensor coordinates (x + 4, y + 1, z + 1); box x starts at fine column fx0 - 4
-    auto issue_u = [&](int p) {
-        mbar_expect(ubar(p), kRUBox + (p == ufirst ? inject : 0));
-        tma_load_3d(smem_u32(su + ((p - ufirst) % kRUSlots) * kUF), &tu, fx0, fy0, p + 1, ubar(p));
-        u_issued = p;
-    };
-    auto issue_b = [&](int p) {
-        mbar_expect(bbar(p), kRBBox);
-        tma_load_3d(smem_u32(sb + ((p - bfirst) % kRBSlots) * kBF), &tb, fx0, fy0 + 1, p + 1, bbar(p));
-        b_issued = p;
-    };
-    auto wait_u = [&](int p) {
-        if (!mbar_wait(ubar(p), upar(p))) return false;
-        u_done = p;
-        return true;
-    };
-    auto wait_b = [&](int p) {
-        if (!mbar_wait(bbar(p), bpar(p))) return false;
-        b_done = p;
-        return true;
-    };
+    auto full_u = [&](int p) { return smem_u32(&bars[uslot(p)]); };
+    auto full_b = [&](int p) { return smem_u32(&bars[kRUSlots + bslot(p)]); };
+    auto empty_u = [&](int p) { return smem_u32(&bars[kNB + uslot(p)]); };
+    auto empty_b = [&](int p) { return smem_u32(&bars[kNB + kRUSlots + bslot(p)]); };
 
-    if (producer) {
-        for (int i = 0; i < kRUSlots + kRBSlots; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    if (t == 0) {
+        for (int i = 0; i < kNB; ++i) {
+            mbar_init(smem_u32(&bars[i]), 1);
+            mbar_init(smem_u32(&bars[kNB + i]), kRWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int p = ufirst; p <= min(f0 + 1 + kAhead, ulast); ++p) issue_u(p);
-        for (int p = bfirst; p <= min(f0 + kAhead, blast); ++p) issue_b(p);
-        bool ok = true;
-        for (int p = ufirst; ok && p <= f0 + 1; ++p) ok = wait_u(p);
-        ok = ok && wait_b(bfirst);
-        s_fail = ok ? 0 : 1;
+        s_fail = 0;
     }
-    __syncthreads();
+    __syncthreads();  // the only block barrier: barriers initialised
 
-    float t2a = 0.f, t2b = 0.f;
-    for (int f = f0; f <= f1 && !s_fail; ++f) {
-        const float *um = su + ((f - 1 - ufirst) % kRUSlots) * kUF;
-        const float *uc = su + ((f - ufirst) % kRUSlots) * kUF;
-        const float *up = su + ((f + 1 - ufirst) % kRUSlots) * kUF;
-        const float *bp = sb + ((f - bfirst) % kRBSlots) * kBF;
-        // fine residual patch: point (i, j) = fine (fx0 + i, fy0 + j), u tile
-        // column i + 4, row j + 1; b tile column i + 4, row j
-        for (int q = t; q < kRF * kRF; q += kRThreads) {
-            const int i = q % kRF, j = q / kRF;
-            float r = 0.f;
-            if (fx0 + i < n && fy0 + j < n) {
-                const int iu = (j + 1) * kRW + i + 4;
-                const float s = radd(radd(radd(uc[iu - 1], uc[iu + 1]), radd(uc[iu - kRW], uc[iu + kRW])),
-                                     radd(um[iu], up[iu]));
-                r = radd(rfma(-6.f, uc[iu], bp[j * kRW + i + 4]), s);
-            }
-            sr[j][i] = r;
+    if (warp == kRWarps) {
+        // ---------------- producer (one thread) ----------------
+        if (lane != 0) return;
+        int u_last = ufirst - 1, b_last = bfirst - 1;  // last plane issued
+        bool ok = true;
+        // a slot is refilled once every consumer warp has released its previous plane
+        auto issue_u = [&](int p) {
+            if (p - kRUSlots >= ufirst && !mbar_wait(empty_u(p), upar(p - kRUSlots))) return false;
+            mbar_expect(full_u(p), kRUBox + (p == ufirst ? inject : 0));
+            tma_load_3d(smem_u32(su + uslot(p) * kUF), &tu, fx0, fy0, p + 1, full_u(p));
+            u_last = p;
+            return true;
+        };
+        auto issue_b = [&](int p) {
+            if (p - kRBSlots >= bfirst && !mbar_wait(empty_b(p), bpar(p - kRBSlots))) return false;
+            mbar_expect(full_b(p), kRBBox);
+            tma_load_3d(smem_u32(sb + bslot(p) * kBF), &tb, fx0, fy0 + 1, p + 1, full_b(p));
+            b_last = p;
+            return true;
+        };
+        ok = issue_u(ufirst) && issue_u(ufirst + 1);
+        for (int q = bfirst; ok && q <= blast; ++q) {
+            ok = issue_u(q + 1) && issue_b(q);  // consumer step q reads u(q - 1 .. q + 1), b(q)
+            if (s_fail) ok = false;
         }
-        __syncthreads();
-        if (producer) {
-            if (f + 2 + kAhead <= ulast) issue_u(f + 2 + kAhead);
-            if (f + 1 + kAhead <= blast) issue_b(f + 1 + kAhead);
+        if (!ok) {
+            s_fail = 1;
+            atomicOr(err, 1);
         }
-        for (int q = t; q < kRF * kRQ; q += kRThreads) {
-            const int k = q % kRQ, j = q / kRQ;
-            st1[j][k] = rfma(2.f, sr[j][2 * k + 1], radd(sr[j][2 * k], sr[j][2 * k + 2]));
-        }
-        __syncthreads();
-        if (t < kRCons) {
-            const float t2 = rfma(2.f, st1[2 * tjc + 1][tic], radd(st1[2 * tjc][tic], st1[2 * tjc + 2][tic]));
-            if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
-                const int kc = f / 2 - 1;
-                bc[gc.off + (long)kc * gc.plane + (long)jc * gc.pitch + ic] =
-                    scale2<-4>(rfma(2.f, t2b, radd(t2a, t2)));
-            }
-            t2a = t2b;
-            t2b = t2;
-        }
-        if (producer && f < f1) {
-            bool ok = wait_u(f + 2);
-            ok = ok && wait_b(f + 1);
-            if (!ok) s_fail = 1;
-        }
-        __syncthreads();
+        // before the block ends every issued copy must have landed (bounded)
+        for (int p = max(ufirst, u_last - kRUSlots + 1); p <= u_last; ++p) mbar_wait(full_u(p), upar(p));
+        for (int p = max(bfirst, b_last - kRBSlots + 1); p <= b_last; ++p) mbar_wait(full_b(p), bpar(p));
+        return;
     }
-    if (producer && s_fail) {
+
+    // ---------------- consumers ----------------
+    const int l = lane;
+    const int ic = ic0 + l;
+    const int cu = 2 * l + 4;       // box column of fine 2 ic
+    const int X0 = fx0 + 2 * l;     // fine 2 ic
+    const int ry0 = 2 * kRRows * warp;  // first fine row of this warp relative to fy0
+    float t2a[kRRows], t2b[kRRows];
+#pragma unroll
+    for (int m = 0; m < kRRows; ++m) t2a[m] = t2b[m] = 0.f;
+    bool ok = true;
+    auto wait_full = [&](unsigned bar, unsigned par) {
+        if (!mbar_wait(bar, par)) {
+            s_fail = 1;
+            atomicOr(err, 1);
+            return false;
+        }
+        return true;
+    };
+    ok = wait_full(full_u(ufirst), upar(ufirst)) && wait_full(full_u(ufirst + 1), upar(ufirst + 1));
+    for (int f = f0; ok && f <= f1; ++f) {
+        ok = wait_full(full_u(f + 1), upar(f + 1)) && wait_full(full_b(f), bpar(f));
+        if (!ok || s_fail) break;
+        const float *um = su + uslot(f - 1) * kUF, *uc = su + uslot(f) * kUF, *up = su + uslot(f + 1) * kUF;
+        const float *bp = sb + bslot(f) * kBF;
+        // rolling rows (box row = fine row - (fy0 - 1)): columns 2ic .. 2ic + 3
+        float2 pA = ld2s(uc + (ry0) * kRW + cu), pB = ld2s(uc + (ry0) * kRW + cu + 2);          // y - 1
+        float2 cA = ld2s(uc + (ry0 + 1) * kRW + cu), cB = ld2s(uc + (ry0 + 1) * kRW + cu + 2);  // y
+        float tq1 = 0.f, tq2 = 0.f;  // x passes of rows y - 1, y - 2
+#pragma unroll
+        for (int r = 0; r <= 2 * kRRows; ++r) {
+            const int row = ry0 + 1 + r;  // box row of fine row y
+            const float2 nA = ld2s(uc + (row + 1) * kRW + cu), nB = ld2s(uc + (row + 1) * kRW + cu + 2);
+            const int y = fy0 + ry0 + r;
+            const bool yin = y < n;
+            const float *zm = um + row * kRW + cu, *zp = up + row * kRW + cu;
+            const float *bb = bp + (row - 1) * kRW + cu;
+            // fine 2ic + 1 (box column cu + 1) and 2ic + 2 (cu + 2)
+            const float s1 = radd(radd(radd(cA.x, cB.x), radd(pA.y, nA.y)), radd(zm[1], zp[1]));
+            float r1 = radd(rfma(-6.f, cA.y, bb[1]), s1);
+            const float s2 = radd(radd(radd(cA.y, cB.y), radd(pB.x, nB.x)), radd(zm[2], zp[2]));
+            float r2 = radd(rfma(-6.f, cB.x, bb[2]), s2);
+            if (!(yin && X0 + 1 < n)) r1 = 0.f;
+            if (!(yin && X0 + 2 < n)) r2 = 0.f;
+            float r0 = __shfl_up_sync(0xffffffffu, r2, 1);
+            if (l == 0) {  // fine 2 ic0 (box column 4)
+                const float w = uc[row * kRW + cu - 1];
+                const float s0 = radd(radd(radd(w, cA.y), radd(pA.x, nA.x)), radd(zm[0], zp[0]));
+                r0 = radd(rfma(-6.f, cA.x, bb[0]), s0);
+                if (!(yin && X0 < n)) r0 = 0.f;
+            }
+            const float tx = rfma(2.f, r1, radd(r0, r2));
+            if (r >= 2 && (r & 1) == 0) {  // coarse row m = r / 2 - 1 of this warp
+                const int m = r / 2 - 1;
+                const float t2 = rfma(2.f, tq1, radd(tq2, tx));
+                const int jc = jc0 + kRRows * warp + m;
+                if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
+                    const int kc = f / 2 - 1;
+                    bc[gc.off + (long)kc * gc.plane + (long)jc * gc.pitch + ic] =
+                        scale2<-4>(rfma(2.f, t2b[m], radd(t2a[m], t2)));
+                }
+                t2a[m] = t2b[m];
+                t2b[m] = t2;
+            }
+            tq2 = tq1;
+            tq1 = tx;
+            pA = cA;
+            pB = cB;
+            cA = nA;
+            cB = nB;
+        }
+        __syncwarp();
+        if (l == 0) {  // this warp is done with u(f - 1) and b(f)
+            mbar_arrive(empty_u(f - 1));
+            mbar_arrive(empty_b(f));
+        }
+    }
+    if (!ok) {
+        s_fail = 1;
         atomicOr(err, 1);
-        for (int p = u_done + 1; p <= u_issued; ++p) mbar_wait(ubar(p), upar(p));
-        for (int p = b_done + 1; p <= b_issued; ++p) mbar_wait(bbar(p), bpar(p));
     }
 }
 
@@ -546,18 +601,19 @@ cudaError_t launch_resrestrict3d_tma(const float *u, const float *b, float *bc, 
     const Pitch3 g = pitch3(n), gc = pitch3((n - 1) / 2);
     const int nc = gc.n;
     CUtensorMap tu, tb;
-    if (!make_map(&tu, u, g, kRW, kRUR) || !make_map(&tb, b, g, kRW, kRF)) return cudaErrorInvalidValue;
-    const int bxy = (nc + kRQ - 1) / kRQ;
+    if (!make_map(&tu, u, g, kRW, kRUR) || !make_map(&tb, b, g, kRW, kRBR)) return cudaErrorInvalidValue;
+    const int bx = (nc + kRX - 1) / kRX, by = (nc + kRY - 1) / kRY;
     // at most one wave: z-chunks of coarse planes
-    int chunks = std::max(1, resident * num_sms() / (bxy * bxy));
+    int chunks = std::max(1, resident * num_sms() / (bx * by));
     chunks = std::min(chunks, std::max(1, nc / 2));
     const int Zc = (nc + chunks - 1) / chunks;
     const int inject = take_armed() ? 16 : 0;
-    resrestrict3d_tma_kernel<<<dim3(bxy, bxy, (nc + Zc - 1) / Zc), kRThreads, kRSmemBytes, s>>>(tu, tb, bc, g, gc,
-                                                                                               Zc, err, inject);
+    resrestrict3d_tma_kernel<<<dim3(bx, by, (nc + Zc - 1) / Zc), kRThreads, kRSmemBytes, s>>>(tu, tb, bc, g, gc, Zc,
+                                                                                            err, inject);
     count_launch(1);
     return cudaGetLastError();
 }
+
 
 }  // namespace mg
 
