@@ -52,6 +52,10 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
     const bool ina = xa >= 0 && xa < n, inb = xb >= 0 && xb < n;
     const bool owna = t >= 1 && ina, ownb = t <= NT - 2 && inb;
     const bool lt = t == 0, rt = t == NT - 1;
+    // a warp whose 64 columns all lie at x >= n has only zero residuals: it
+    // skips the FP64 work (the pipe, not the bytes, bounds this kernel) and
+    // only stores the zeros its neighbours read
+    const bool wact = X0 + 2 * (t & ~31) < n;
     const size_t ld = (size_t)n;
     auto get = [&](const T *a, int yy, int xx) -> T {
         return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : T(0);
@@ -86,16 +90,18 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
             fa = scale2(fa, hk);
             fb = scale2(fb, hk);
         }
-        T ra, rb;
+        T ra = T(0), rb = T(0);
         if (!ZERO_U) {
             ann = get(u, j + 2, xa);
             bnn = get(u, j + 2, xb);
             if (lt) hnn = get(u, j + 2, xa - 1);
             if (rt) hnn = get(u, j + 2, xb + 1);
-            const T sa = radd(radd(su[buf][2 * t], bc), radd(ap, an));
-            const T sb = radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn));
-            ra = radd(rfma(T(-4), ac, fa), sa);
-            rb = radd(rfma(T(-4), bc, fb), sb);
+            if (wact) {
+                const T sa = radd(radd(su[buf][2 * t], bc), radd(ap, an));
+                const T sb = radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn));
+                ra = radd(rfma(T(-4), ac, fa), sa);
+                rb = radd(rfma(T(-4), bc, fb), sb);
+            }
             su[1 - buf][2 * t + 1] = an;
             su[1 - buf][2 * t + 2] = bn;
             if (lt) su[1 - buf][0] = hn;
@@ -114,8 +120,8 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
         sr[buf][2 * t + 1] = ra;
         sr[buf][2 * t + 2] = rb;
         __syncthreads();
-        const T pa = lt ? T(0) : radd(sr[buf][2 * t], rb);
-        const T pb = rt ? T(0) : radd(ra, sr[buf][2 * t + 3]);
+        const T pa = (lt || !wact) ? T(0) : radd(sr[buf][2 * t], rb);
+        const T pb = (rt || !wact) ? T(0) : radd(ra, sr[buf][2 * t + 3]);
         if (j - 1 >= y0) {  // output row j - 1
             if (owna) {
                 const T E = radd(pa1, radd(ra2, ra));
@@ -330,6 +336,7 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
     const int y1 = min(y0 + H, n);
     const bool owna = t >= 1 && xa < n, ownb = t <= NT - 2 && xb < n;
     const bool lt = t == 0, rt = t == NT - 1;
+    const bool wact = X0 + 2 * (t & ~31) < n;  // as in the sweep: all-outside warps skip the FP64 work
     const size_t ld = (size_t)n;
     auto get = [&](const InT *a, int yy, int xx) -> InT {
         return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : InT(0);
@@ -356,8 +363,11 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
             fa = scale2(fa, hk);
             fb = scale2(fb, hk);
         }
-        const InT ra = radd(rfma(InT(-4), ac, fa), radd(radd(su[buf][2 * t], bc), radd(ap, an)));
-        const InT rb = radd(rfma(InT(-4), bc, fb), radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn)));
+        InT ra = InT(0), rb = InT(0);
+        if (wact) {
+            ra = radd(rfma(InT(-4), ac, fa), radd(radd(su[buf][2 * t], bc), radd(ap, an)));
+            rb = radd(rfma(InT(-4), bc, fb), radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn)));
+        }
         if (owna) {
             acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
             if (rh_out) rh_out[opitch ? ooff + j * opitch + xa : (long)j * ld + xa] = to_out<OutT>(ra);
