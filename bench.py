@@ -158,9 +158,10 @@ def run_reference(args):
     }), flush=True)
 
 
-def _cpu_baseline_sample():
+def _cpu_baseline_sample(threads: int = 1):
     """The oracle timed on a bounded sample: one V(1,1) cycle of the full
-    problem (about 10-20 s of single-threaded CPU work)."""
+    problem (a few seconds of single-threaded CPU work). threads > 1 spreads
+    the oracle's grid loops over that many host cores (OpenMP)."""
     import numpy as np
 
     import oracle
@@ -169,11 +170,16 @@ def _cpu_baseline_sample():
 
     b = inputs.uniform(D, N, SEED)
     u = np.zeros_like(b)
-    t0 = time.perf_counter()
-    oracle.cycles(b, u, coeffs.default(D), 1)
-    dt = time.perf_counter() - t0
-    return {"value": UNKNOWNS / dt, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 V(1,1) cycle of the full-size problem in {dt:.1f} s (C oracle, 1 thread)"}
+    used = oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        oracle.cycles(b, u, coeffs.default(D), 1)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return {"value": UNKNOWNS / dt, "unit": "DOF/s", "cores": used, "kind": "oracle",
+            "sample": f"1 V(1,1) cycle of the full-size problem in {dt:.2f} s (C oracle, {used} thread"
+                      f"{'' if used == 1 else 's'})"}
 
 
 def make_workload(name, torch):
@@ -444,6 +450,8 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline_sample()
+            # the same oracle with its grid loops on every host core
+            line["cpu_baseline_all_cores"] = _cpu_baseline_sample(_cpu_cores())
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -56,8 +56,11 @@ def build(force: bool = False) -> str:
              or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP only spreads the per-point grid loops over threads (timing);
+        # without it the same source builds single-threaded
+        cmd = ["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(cmd, capture_output=True).returncode != 0:
+            subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,10 +83,18 @@ def lib():
             L.orc_residual_norm.restype = d
             L.orc_cycles.argtypes = [i, i, dp, i, i, i, i, i, dp, dp]
             L.orc_solve.argtypes = [i, i, dp, i, i, i, i, dp, dp, d, i, dp, ip, dp]
+            L.orc_set_threads.argtypes = [i]
+            L.orc_set_threads.restype = i
+            L.orc_set_threads(1)  # single-threaded unless a timing asks otherwise
             for f in (L.orc_cycles, L.orc_solve):
                 f.restype = i
             _lib = L
     return _lib
+
+
+def set_threads(threads: int) -> int:
+    """Threads for the grid loops (timing only; results do not depend on it)."""
+    return int(lib().orc_set_threads(int(threads)))
 
 
 def _p(a: np.ndarray):

@@ -100,6 +100,7 @@ void orc_residual_scaled(int d, int n, int periodic, const double *u,
                          const double *bh, double *rh)
 {
     if (d == 2) {
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < n; ++y)
             for (int x = 0; x < n; ++x) {
                 long p = (long)y * n + x;
@@ -108,6 +109,7 @@ void orc_residual_scaled(int d, int n, int periodic, const double *u,
                 rh[p] = fma(-4.0, u[p], bh[p]) + s;
             }
     } else {
+#pragma omp parallel for schedule(static)
         for (int z = 0; z < n; ++z)
             for (int y = 0; y < n; ++y)
                 for (int x = 0; x < n; ++x) {
@@ -118,6 +120,24 @@ void orc_residual_scaled(int d, int n, int periodic, const double *u,
                     rh[p] = fma(-6.0, u[p], bh[p]) + s;
                 }
     }
+}
+
+/* Timing only: the number of threads the grid loops above use (each point is
+ * computed by one thread in the same order, so results do not depend on it;
+ * norms are summed by one thread). Returns the count in effect, 1 when the
+ * library was built without OpenMP. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int orc_set_threads(int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    return omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------ */
@@ -136,6 +156,7 @@ static void apply_spai(int d, int n, int periodic, const double *c,
                        const double *rh, const double *u, double *out)
 {
     if (d == 2) {
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < n; ++y)
             for (int x = 0; x < n; ++x) {
                 long p = (long)y * n + x;
@@ -146,6 +167,7 @@ static void apply_spai(int d, int n, int periodic, const double *c,
                 out[p] = fma(c[2], C, fma(c[1], E, fma(c[0], rh[p], u[p])));
             }
     } else {
+#pragma omp parallel for schedule(static)
         for (int z = 0; z < n; ++z)
             for (int y = 0; y < n; ++y)
                 for (int x = 0; x < n; ++x) {
@@ -184,6 +206,7 @@ void orc_restrict(int d, int nf, const double *rh, double *bh_c)
 {
     int nc = (nf - 1) / 2;
     if (d == 2) {
+#pragma omp parallel for schedule(static)
         for (int J = 1; J <= nc; ++J)
             for (int I = 1; I <= nc; ++I) {
                 int fx = 2 * I - 1, fy = 2 * J - 1; /* 0-based index of fine point 2I, 2J */
@@ -196,6 +219,7 @@ void orc_restrict(int d, int nf, const double *rh, double *bh_c)
                 bh_c[(long)(J - 1) * nc + (I - 1)] = 0.25 * v;
             }
     } else {
+#pragma omp parallel for schedule(static)
         for (int K = 1; K <= nc; ++K)
             for (int J = 1; J <= nc; ++J)
                 for (int I = 1; I <= nc; ++I) {
@@ -269,12 +293,14 @@ void orc_prolong_add(int d, int nf, const double *e_c, double *u)
 {
     int nc = (nf - 1) / 2;
     if (d == 2) {
+#pragma omp parallel for schedule(static)
         for (int y = 1; y <= nf; ++y)
             for (int x = 1; x <= nf; ++x) {
                 long p = (long)(y - 1) * nf + (x - 1);
                 u[p] = u[p] + interp_xy2(e_c, nc, x, y);
             }
     } else {
+#pragma omp parallel for schedule(static)
         for (int z = 1; z <= nf; ++z)
             for (int y = 1; y <= nf; ++y)
                 for (int x = 1; x <= nf; ++x) {

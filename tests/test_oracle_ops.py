@@ -170,3 +170,20 @@ def test_residual_norm_is_accurately_summed():
     r = b.ravel() - exact.laplacian(2, N) @ u.ravel()
     ref = math.sqrt(math.fsum(r * r))
     assert oracle.residual_norm(u, b) == pytest.approx(ref, rel=1e-14)
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    """The grid loops may run on several threads (timing); every point is
+    still computed by one thread in the same order, so cycles are identical."""
+    import os
+    for d, N in ((2, 64), (3, 16)):
+        b = np.random.default_rng(11).uniform(-1, 1, (N - 1,) * d)
+        c = coeffs.default(d)
+        try:
+            oracle.set_threads(1)
+            one = oracle.cycles(b, np.zeros_like(b), c, 2)
+            oracle.set_threads(max(2, os.cpu_count() or 2))
+            many = oracle.cycles(b, np.zeros_like(b), c, 2)
+        finally:
+            oracle.set_threads(1)
+        assert np.array_equal(one, many)
