@@ -314,16 +314,14 @@ void orc_prolong_add(int d, int nf, const double *e_c, double *u)
 /* coarsest-level solve                                               */
 /* ------------------------------------------------------------------ */
 
-/* Exact solve on the coarsest grid h0 = 1/4 (3^d interior unknowns)
- * [Sec. 4; the solver is not named there]. Gaussian elimination without
- * pivoting (the matrix is symmetric positive definite) on the scaled
- * operator h0^2 A_h0, unknowns in the natural order, applied to the
- * augmented system:
+/* Gaussian elimination without pivoting (the matrix is symmetric positive
+ * definite) on the scaled coarsest operator h0^2 A_h0, unknowns in the
+ * natural order, applied to the augmented system with right-hand side rhs:
  *   for k: for i > k: l = a_ik / a_kk; a_ij -= l a_kj (j > k); y_i -= l y_k
  *   for i = m-1 .. 0: y_i -= a_ij x_j for j = i+1 .. m-1 in increasing j;
  *                     x_i = y_i / a_ii.
  * Products are rounded before each subtraction (no fma). */
-void orc_coarse_solve(int d, const double *bh, double *x)
+static void coarse_eliminate(int d, const double *rhs, double *x)
 {
     const int n = 3;
     const int m = d == 2 ? 9 : 27;
@@ -331,7 +329,7 @@ void orc_coarse_solve(int d, const double *bh, double *x)
     double y[27];
     for (int i = 0; i < m; ++i) {
         for (int j = 0; j < m; ++j) a[i][j] = 0.0;
-        y[i] = bh[i];
+        y[i] = rhs[i];
     }
     for (int i = 0; i < m; ++i) {
         int xi = i % n, yi = (i / n) % n, zi = i / (n * n);
@@ -352,6 +350,27 @@ void orc_coarse_solve(int d, const double *bh, double *x)
         double s = y[i];
         for (int j = i + 1; j < m; ++j) s = s - a[i][j] * x[j];
         x[i] = s / a[i][i];
+    }
+}
+
+/* Exact solve on the coarsest grid h0 = 1/4 (3^d interior unknowns)
+ * [Sec. 4; the solver is not named there]: x = B bh with B the inverse of
+ * h0^2 A_h0, whose column j is the elimination above applied to the unit
+ * vector e_j; the product is summed in increasing j, each product rounded
+ * before the addition:  x_i = (...((0 + B_i0 bh_0) + B_i1 bh_1) ...). */
+void orc_coarse_solve(int d, const double *bh, double *x)
+{
+    const int m = d == 2 ? 9 : 27;
+    double inv[27][27], e[27], col[27];
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < m; ++i) e[i] = i == j ? 1.0 : 0.0;
+        coarse_eliminate(d, e, col);
+        for (int i = 0; i < m; ++i) inv[i][j] = col[i];
+    }
+    for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s = s + inv[i][j] * bh[j];
+        x[i] = s;
     }
 }
 

@@ -176,13 +176,20 @@ adj_interp(const T *__restrict__ e, T *__restrict__ out, int n, T scale)
     }
 }
 
-// acc[j] += sum over blocks of partials[3 b + j] (fixed order)
-__global__ void adj_accumulate(const double *__restrict__ partials, int nblocks, double *__restrict__ acc)
+// acc[j] += sum over blocks of partials[3 b + j]: thread t sums the blocks
+// t, t + 256, ... in that order, then a fixed shuffle/warp tree (the same
+// order every run, independent of timing)
+__global__ void __launch_bounds__(256) adj_accumulate(const double *__restrict__ partials, int nblocks,
+                                                      double *__restrict__ acc)
 {
-    if (threadIdx.x < 3) {
+    __shared__ double tot;
+    for (int j = 0; j < 3; ++j) {
         double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partials[3 * b + threadIdx.x];
-        acc[threadIdx.x] += s;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[3 * b + j];
+        block_sum_store<256>(s, &tot);
+        __syncthreads();
+        if (threadIdx.x == 0) acc[j] += tot;
+        __syncthreads();
     }
 }
 
@@ -293,7 +300,7 @@ struct Adjoint {
         else
             adj_sweep_stage1<T, 3><<<grid, 256, 0, c->s>>>(G, u_in, bh(k, l), l == 0, Tt, nn, T(c->c[0]),
                                                            T(c->c[1]), T(0), hk, w->partials);
-        adj_accumulate<<<1, 32, 0, c->s>>>(w->partials, grid, w->acc);
+        adj_accumulate<<<1, 256, 0, c->s>>>(w->partials, grid, w->acc);
         if (c->d == 2)
             adj_stage2<T, 2><<<grid, 256, 0, c->s>>>(G, Tt, GB, nn);
         else

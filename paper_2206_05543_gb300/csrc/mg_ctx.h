@@ -42,7 +42,7 @@ struct mg_ctx {
     std::vector<void *> A, B, BH, RH;
     size_t esize = 8;
     bool pl = false;  // FP32 levels in the padded layout (refinement, 2D)
-    double *lu = nullptr;
+    double *lu = nullptr;  // exact inverse of the coarsest operator (device)
     double *partials = nullptr;
     int npartials = 0;
     // d_norm2[0]: squared norm of the last residual; the word after it

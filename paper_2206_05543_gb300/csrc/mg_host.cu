@@ -625,7 +625,7 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
         MG_TRY(dalloc(c, (void **)&c->lu, 27 * 27 * sizeof(double)));
         {
             double lu[27 * 27];
-            coarse_lu(d, lu);
+            coarse_inverse(d, lu);
             const int m = d == 2 ? 9 : 27;
             MG_TRYC(cudaMemcpy(c->lu, lu, (size_t)m * m * sizeof(double), cudaMemcpyHostToDevice));
         }
@@ -947,7 +947,7 @@ mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, v
 {
     if ((d != 2 && d != 3) || !bh || !x_out || (prec != MG_FP64 && prec != MG_FP32_IR)) return MG_EINVAL;
     double lu[27 * 27];
-    coarse_lu(d, lu);
+    coarse_inverse(d, lu);
     double *dlu = nullptr;
     cudaError_t e = cudaMalloc(&dlu, sizeof lu);
     if (e) return cuda_fail(e);

@@ -148,7 +148,7 @@ struct TailArgs {
     TailLevel lv[kMaxTailLevels];
     TailOp ops[kMaxTailOps];
     double c[3];
-    const double *lu;  // coarsest LU factors (device)
+    const double *lu;  // exact inverse of the coarsest operator (device, coarse_inverse)
     int d, nops;
 };
 inline TailLevel tail_level(void *u, void *tmp, void *bh, void *rh, int n)
@@ -170,7 +170,8 @@ cudaError_t launch_tail(const TailArgs &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tail_batched(const TailLevel *lv, const TailOp *ops, const int *op_off, const int *op_cnt,
                                 const int *active, int count, int d, const double *c, const double *lu, cudaStream_t s);
-void coarse_lu(int d, double *lu);
+// exact inverse of h0^2 A_h0 (m x m row-major, m = 3^d) for the coarsest solve
+void coarse_inverse(int d, double *inv);
 
 // ---- small helpers (mg_host.cu) -------------------------------------------
 cudaError_t launch_sum_partials(const double *partials, int np, double *out, cudaStream_t s);

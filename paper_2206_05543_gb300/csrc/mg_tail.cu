@@ -124,20 +124,22 @@ __device__ T interp_at(int d, const T *e, const Lay &Lc, int fx, int fy, int fz)
     return scale2<-1>(radd(interp_xy(e, Lc, fx, fy, q - 1), interp_xy(e, Lc, fx, fy, q)));
 }
 
+// Coarsest solve x = B bh with B the exact inverse of h0^2 A_h0 (formed on
+// the host by coarse_inverse): thread i < m forms x_i = sum_j B_ij bh_j in
+// increasing j, each product rounded before the addition. The m dot
+// products run in parallel (a triangular solve on this part is a long
+// dependent FP64 chain).
 template <typename T>
-__device__ void coarse_substitution(int d, const double *lu, const T *bh, T *x, const Lay &L)
+__device__ void coarse_apply(int d, const double *__restrict__ inv, const T *bh, T *x, const Lay &L)
 {
     const int m = d == 2 ? 9 : 27;
-    double y[27], xs[27];
-    for (int i = 0; i < m; ++i) y[i] = (double)bh[lidx(L, i % 3, (i / 3) % 3, i / 9)];
-    for (int i = 0; i < m; ++i)
-        for (int k = 0; k < i; ++k) y[i] = __dsub_rn(y[i], __dmul_rn(lu[i * m + k], y[k]));
-    for (int i = m - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int j = i + 1; j < m; ++j) s = __dsub_rn(s, __dmul_rn(lu[i * m + j], xs[j]));
-        xs[i] = __ddiv_rn(s, lu[i * m + i]);
+    const int i = threadIdx.x;
+    if (i < m) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j)
+            s = __dadd_rn(s, __dmul_rn(__ldg(&inv[i * m + j]), (double)bh[lidx(L, j % 3, (j / 3) % 3, j / 9)]));
+        x[lidx(L, i % 3, (i / 3) % 3, i / 9)] = (T)s;
     }
-    for (int i = 0; i < m; ++i) x[lidx(L, i % 3, (i / 3) % 3, i / 9)] = (T)xs[i];
 }
 
 template <typename T>
@@ -193,7 +195,7 @@ __device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d
                 }
             }
         } else if (kind == TAIL_SOLVE) {
-            if (threadIdx.x == 0) coarse_substitution<T>(d, lu, bh, u, L);
+            coarse_apply<T>(d, lu, bh, u, L);
         } else if (kind == TAIL_PROLONG) {
             const TailLevel &C = lv[l + 1];
             const Lay Lc{C.n, C.pitch, C.plane, C.off};
@@ -254,9 +256,14 @@ template cudaError_t launch_tail<float>(const TailArgs &, cudaStream_t);
 // LU factors of the scaled coarsest operator h0^2 A_h0 (3^d unknowns, natural
 // order), written into lu (m*m, row-major): strict lower part = multipliers,
 // upper part incl. diagonal = U. Host code, compiled without contraction.
-void coarse_lu(int d, double *lu)
+void coarse_inverse(int d, double *inv)
 {
+    // Gaussian elimination without pivoting on h0^2 A_h0 (natural order),
+    // products rounded before each subtraction; column j of the inverse is
+    // the forward substitution (y_i -= l_ik y_k, k increasing) and back
+    // substitution (s -= u_ij x_j, j increasing; x_i = s / u_ii) of e_j.
     const int n = 3, m = d == 2 ? 9 : 27;
+    double lu[27 * 27];
     for (int i = 0; i < m; ++i) {
         const int xi = i % n, yi = (i / n) % n, zi = i / (n * n);
         for (int j = 0; j < m; ++j) {
@@ -271,6 +278,18 @@ void coarse_lu(int d, double *lu)
             for (int j = k + 1; j < m; ++j) lu[i * m + j] = lu[i * m + j] - l * lu[k * m + j];
             lu[i * m + k] = l;
         }
+    for (int c = 0; c < m; ++c) {
+        double y[27], x[27];
+        for (int i = 0; i < m; ++i) y[i] = i == c ? 1.0 : 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k < i; ++k) y[i] = y[i] - lu[i * m + k] * y[k];
+        for (int i = m - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int j = i + 1; j < m; ++j) s = s - lu[i * m + j] * x[j];
+            x[i] = s / lu[i * m + i];
+        }
+        for (int i = 0; i < m; ++i) inv[i * m + c] = x[i];
+    }
 }
 
 }  // namespace mg
