@@ -18,7 +18,6 @@ constexpr int kP3Cols = 128;
 __device__ __forceinline__ float4 ld4g(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4g(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float &e4(float4 &v, int k) { return (&v.x)[k]; }
-__device__ __forceinline__ float ce4(const float4 &v, int k) { return (&v.x)[k]; }
 
 // ---------------------------------------------------------------------------
 // Trilinear interpolation + correction (formula as prolong3d_kernel): thread

@@ -185,7 +185,8 @@ def test_coarse_solve_fp64_bitwise(d):
 # FP32 versions of the same operators (used inside iterative refinement)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("d,n,name", [(2, 63, "m9"), (2, 511, "m9"), (2, 1023, "jacobi"), (3, 31, "m7"), (3, 63, "m7")])
+@pytest.mark.parametrize("d,n,name", [(2, 63, "m9"), (2, 511, "m9"), (2, 1023, "jacobi"), (3, 31, "m7"), (3, 63, "m7"),
+                                      (3, 127, "m7"), (3, 255, "jacobi")])
 def test_sweep_fp32_within_rounding_bound(d, n, name):
     w = _w(d, name)
     u = rand((n,) * d, 14).astype(np.float32).astype(np.float64)
@@ -197,7 +198,7 @@ def test_sweep_fp32_within_rounding_bound(d, n, name):
     np.testing.assert_allclose(host(out), ref, rtol=0, atol=32 * EPS32 * S)
 
 
-@pytest.mark.parametrize("d,n", [(2, 511), (3, 63)])
+@pytest.mark.parametrize("d,n", [(2, 511), (2, 2047), (3, 63), (3, 127), (3, 255)])
 def test_restrict_and_prolong_fp32_within_rounding_bound(d, n):
     u = rand((n,) * d, 16).astype(np.float32).astype(np.float64)
     bh = (rand((n,) * d, 17) / (n + 1) ** 2).astype(np.float32).astype(np.float64)

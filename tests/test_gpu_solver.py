@@ -188,3 +188,66 @@ def test_config_2d_n8192_two_cycles_bitwise():
     assert info.cycles == 2
     np.testing.assert_allclose(info.hist, ref.hist, rtol=1e-12, atol=0)
     assert np.array_equal(got, ref.u)
+
+
+@pytest.mark.slow
+def test_config_3d_n512_full_size():
+    """Full-size 3D workload (N = 512, 133M unknowns, uniform b seed 0): the
+    FP64 sweep in the benchmark's launch configuration equals the oracle at
+    sampled points (corners, faces, tile and chunk edges, random) bit for
+    bit, and the refinement solves (one and two FP32 cycles per iteration)
+    reach an FP64 residual <= 1e-10 ||b||, recomputed by the oracle."""
+    N, n = 512, 511
+    b = inputs.uniform(3, N, 0)
+    w = coeffs.default(3)
+    h2 = 1.0 / N ** 2
+    u = np.random.default_rng(5).uniform(-1, 1, b.shape)
+    out, _ = binding.op_sweep(dev(u), dev(b), w, b_unscaled=True)
+    got = host(out)
+    rng = np.random.default_rng(6)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n // 2, n - 1), (255, 29, 127), (256, 30, 128),
+           (254, 31, 129)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(60)]
+    bh = h2 * b
+    for p in pts:
+        ref = _residual_sweep_point(u, bh, w, p)
+        assert got[p] == ref, (p, got[p], ref)
+    del got, out
+    for m in (1, 2):
+        with Solver(3, N, w, nu1=2, nu2=2, precision="fp32_ir") as s:
+            if m > 1:
+                s.set_refinement_cycles(m)
+            info = s.solve(dev(b), tol=1e-10, max_cycles=40)
+            x = host(info.u)
+        assert info.converged
+        assert oracle.residual_norm(x, b) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
+
+
+def _residual_sweep_point(u, bh, w, p):
+    """One point of the FP64 sweep, in the oracle's operation order, from the
+    oracle's scaled residual of the 3^3 neighbourhood boxes of p and its six
+    neighbours (every value the stencil reads)."""
+    n = u.shape[0]
+
+    def val(a, q):
+        return a[q] if all(0 <= c < n for c in q) else 0.0
+
+    def rh(q):
+        if not all(0 <= c < n for c in q):
+            return 0.0
+        box_u = np.array([[[val(u, (q[0] + dz, q[1] + dy, q[2] + dx)) for dx in (-1, 0, 1)]
+                           for dy in (-1, 0, 1)] for dz in (-1, 0, 1)])
+        box_b = np.zeros((3, 3, 3))
+        box_b[1, 1, 1] = bh[q]
+        # the 3^3 oracle grid's centre point sees exactly q's six neighbours
+        return oracle.residual_scaled(box_u, box_b)[1, 1, 1]
+
+    z, y, x = p
+    E = ((rh((z, y, x - 1)) + rh((z, y, x + 1))) + (rh((z, y - 1, x)) + rh((z, y + 1, x)))) + \
+        (rh((z - 1, y, x)) + rh((z + 1, y, x)))
+    return _fma(w[1], E, _fma(w[0], rh(p), float(u[p])))
+
+
+def _fma(a, b, c):
+    """a * b + c rounded once (exact rational arithmetic, then the nearest double)."""
+    from fractions import Fraction
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
