@@ -74,17 +74,22 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
     bn = row4(Bp, y0 - 1, x);
     if (lt || rt) hb = row1(Bp, y0 - 1, xh);
     double acc = 0.0;
-    // refinement epilogue: the FP64 solution row j is loaded at step j and
-    // updated at step j + 1, so its latency overlaps one step of work
+    // refinement epilogue: each warp stages its 128 FP32 results in shared
+    // memory and lane l updates the FP64 columns xw + l + 32 k (k < 4), so
+    // every FP64 access of the warp covers 256 contiguous bytes; the FP64
+    // row j is loaded at step j and updated at step j + 1
+    __shared__ __align__(16) float sacc[kPLThreads / 32][4 * 32];
+    const int lane = t & 31, wrp = t >> 5;
+    const int xw = xb + 128 * wrp;
     double u64c[4] = {0.0, 0.0, 0.0, 0.0}, u64n[4] = {0.0, 0.0, 0.0, 0.0};
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
         const float4 bc = bn;
         const float hbc = hb;
         if (ACC64 && j >= y0 && j < y1) {
-            const double *ur = u64 + (long)j * n + x;
+            const double *ur = u64 + (long)j * n + xw + lane;
             for (int k = 0; k < 4; ++k)
-                if (x + k < n) u64n[k] = ur[k];
+                if (xw + lane + 32 * k < n) u64n[k] = ur[32 * k];
         }
         bn = row4(Bp, j + 1, x);  // prefetch
         if (lt || rt) hb = row1(Bp, j + 1, xh);
@@ -135,11 +140,14 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
                 c4(o, k) = rfma(c2, C, rfma(c1, E, base));
             }
             if (ACC64) {
-                // refinement epilogue: the correction goes straight into the
-                // caller's FP64 solution (compact rows of n doubles)
-                double *ur = u64 + (long)(j - 1) * n + x;
+                // the correction goes straight into the caller's FP64
+                // solution (compact rows of n doubles)
+                st4(&sacc[wrp][4 * lane], o);
+                __syncwarp();
+                double *ur = u64 + (long)(j - 1) * n + xw + lane;
                 for (int k = 0; k < 4; ++k)
-                    if (x + k < n) ur[k] = __dadd_rn(u64c[k], widen(c4(o, k)));
+                    if (xw + lane + 32 * k < n) ur[32 * k] = __dadd_rn(u64c[k], widen(sacc[wrp][lane + 32 * k]));
+                __syncwarp();
             } else if (x < n) {
                 st4_valid(O + (long)(j - 1) * P + x, o, x, n);
             }

@@ -51,6 +51,7 @@ constexpr int kUSlotBytes = (kUBoxBytes + 127) / 128 * 128;
 constexpr int kBSlotBytes = (kBBoxBytes + 127) / 128 * 128;
 constexpr int kRSlotBytes = kBSlotBytes;  // residual plane: kTRows x kTW
 constexpr int kSmemBytes = kUSlots * kUSlotBytes + kBSlots * kBSlotBytes + 2 * kRSlotBytes + 128;
+constexpr int kAccBytes = kTRows * kTCols * 4;  // ACC64 staging: one 128-float row per consumer warp
 constexpr long long kWaitCycles = 1LL << 31;  // about one second
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -193,12 +194,16 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
 
     long di = g.off + (long)(z0 - 2) * g.plane + (long)yr * g.pitch + x;  // (x, yr, zz-1) at step zz
     float4 rm = make_float4(0.f, 0.f, 0.f, 0.f), rc = rm;
+    // ACC64: each consumer warp stages its 128 results (behind the residual
+    // ring) and lane l updates the FP64 columns x0 + l + 32 k, so that every
+    // FP64 access of the warp covers 256 contiguous bytes
+    float *const sacc = sr + 2 * kRF + (helper ? 0 : ty) * kTCols;
     for (int zz = z0 - 1; zz <= z1 && !s_fail; ++zz) {
         double u64v[4] = {0.0, 0.0, 0.0, 0.0};
         if (ACC64 && zz > z0 && own_row) {
-            const double *ur = u64 + ((long)(zz - 1) * n + yr) * n + x;
+            const double *ur = u64 + ((long)(zz - 1) * n + yr) * n + x0 + lane;
             for (int k = 0; k < 4; ++k)
-                if (x + k < n) u64v[k] = ur[k];
+                if (x0 + lane + 32 * k < n) u64v[k] = ur[32 * k];
         }
         // A. scaled residual of plane zz (zero outside the interior)
         const unsigned m = (zz >= 0 && zz < n) ? xmask : 0u;
@@ -256,9 +261,12 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
                 f4(o, k) = rfma(c1, E, b0);
             }
             if (ACC64) {
-                double *ur = u64 + ((long)(zz - 1) * n + yr) * n + x;
+                *reinterpret_cast<float4 *>(sacc + 4 * lane) = o;
+                __syncwarp();
+                double *ur = u64 + ((long)(zz - 1) * n + yr) * n + x0 + lane;
                 for (int k = 0; k < 4; ++k)
-                    if (x + k < n) ur[k] = __dadd_rn(u64v[k], widen(f4(o, k)));
+                    if (x0 + lane + 32 * k < n) ur[32 * k] = __dadd_rn(u64v[k], widen(sacc[lane + 32 * k]));
+                __syncwarp();
             } else {
                 float *dst = out + di;
                 if (x + 3 < n) {
@@ -538,7 +546,7 @@ static cudaError_t sweep3d_tma_any(const float *u, const float *b, float *out, d
                                             kSmemBytes);
         if (attr_err == cudaSuccess)
             attr_err = cudaFuncSetAttribute(sweep3d_tma_kernel<false, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes + kAccBytes);
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (!err || (u64 && !u)) return cudaErrorInvalidValue;
@@ -559,8 +567,8 @@ static cudaError_t sweep3d_tma_any(const float *u, const float *b, float *out, d
     const float c0 = (float)c[0], c1 = (float)c[1];
     const int inject = take_armed() ? 16 : 0;
     if (u64)
-        sweep3d_tma_kernel<false, true><<<grid, kTThreads + 32, kSmemBytes, s>>>(tu, tb, nullptr, g, Z, c0, c1, err,
-                                                                                 u64, inject);
+        sweep3d_tma_kernel<false, true><<<grid, kTThreads + 32, kSmemBytes + kAccBytes, s>>>(tu, tb, nullptr, g, Z, c0,
+                                                                                             c1, err, u64, inject);
     else if (u)
         sweep3d_tma_kernel<false><<<grid, kTThreads + 32, kSmemBytes, s>>>(tu, tb, out, g, Z, c0, c1, err, nullptr,
                                                                            inject);
