@@ -202,9 +202,14 @@ def make_workload(name, torch):
         if inner > 1:
             s.set_refinement_cycles(inner)
 
+        last = {}
+
         def step():  # V-cycles run
             u.zero_()
-            return s.solve(b, u, tol=TOL, max_cycles=100).cycles * inner
+            info = s.solve(b, u, tol=TOL, max_cycles=100)
+            last.update(u=u, relres=info.relres)
+            return info.cycles * inner
+        step.last = last
         return step, (n_ - 1) ** 2, f"2D N={n_} {prec}{'' if inner == 1 else f' x{inner}'} V(1,1) M9 to 1e-10", s.close
     if name.startswith("3d") and name.endswith(("-fp64", "-mixed", "-mixed2")):
         # 3d512-*: the rows; smaller sizes (3d256-mixed, ...) serve profiling
@@ -216,9 +221,14 @@ def make_workload(name, torch):
         if inner > 1:
             s.set_refinement_cycles(inner)
 
+        last = {}
+
         def step():  # V-cycles run
             u.zero_()
-            return s.solve(b, u, tol=TOL, max_cycles=100).cycles * inner
+            info = s.solve(b, u, tol=TOL, max_cycles=100)
+            last.update(u=u, relres=info.relres)
+            return info.cycles * inner
+        step.last = last
         return step, (n_ - 1) ** 3, f"3D N={n_} {prec}{'' if inner == 1 else f' x{inner}'} V(2,2) M7 to 1e-10", s.close
     if name in ("batch256", "batch256-2"):
         Ns = [int(x) for x in inputs.batch_sizes(256, 0)]
@@ -253,7 +263,10 @@ ROWS = ["2d64", "2d8192-mixed", "2d8192-mixed2", "3d512-fp64", "3d512-mixed", "3
         "adjoint128"]
 
 
-def time_workload(name, torch, warmup=2, steps=3):
+def time_workload(name, torch, warmup=2, steps=3, keep=None):
+    """Best of `steps` timed runs after `warmup`; for solver workloads also the
+    final relative residual (FP64, from the library) and, when `keep` is a
+    dict, the last solution under keep[name] (compared after timing)."""
     step, unknowns, desc, close = make_workload(name, torch)
     for _ in range(warmup):
         step()
@@ -266,9 +279,15 @@ def time_workload(name, torch, warmup=2, steps=3):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    close()
     ms = min(times)
-    return {"workload": desc, "ms": ms, "cycles": cycles, "dof_per_s": unknowns * cycles / (ms * 1e-3)}
+    r = {"workload": desc, "ms": ms, "cycles": cycles, "dof_per_s": unknowns * cycles / (ms * 1e-3)}
+    last = getattr(step, "last", None)
+    if last:
+        r["final_relres"] = last["relres"]
+        if keep is not None:
+            keep[name] = last["u"].clone()
+    close()
+    return r
 
 
 def run_ours(args):
@@ -411,8 +430,18 @@ def run_ours(args):
         with open(tpath) as f:
             traffic = json.load(f).get("sweep2d_fp64_n8191")
 
-    rows = {} if args.no_rows else {w: time_workload(w, torch) for w in ROWS}
-    if rows:
+    rows = {}
+    if not args.no_rows:
+        sols = {}
+        for w in ROWS:
+            rows[w] = time_workload(w, torch, keep=sols if ("-mixed" in w or w == "3d512-fp64") else None)
+            # mixed precision against the plain FP64 solution of the same grid:
+            # ||u_mixed - u_fp64|| / ||u_fp64|| (after timing, on the device)
+            ref = u if w.startswith("2d8192") else sols.get("3d512-fp64")
+            if "-mixed" in w and ref is not None:
+                rows[w]["diff_vs_fp64"] = float(torch.linalg.vector_norm(sols.pop(w) - ref) /
+                                                torch.linalg.vector_norm(ref))
+        sols.clear()
         rows["3d512_mixed_speedup_vs_fp64"] = rows["3d512-fp64"]["ms"] / rows["3d512-mixed"]["ms"]
         rows["3d512_mixed2_speedup_vs_fp64"] = rows["3d512-fp64"]["ms"] / rows["3d512-mixed2"]["ms"]
     if rank == 0:
