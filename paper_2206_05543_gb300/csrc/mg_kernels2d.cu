@@ -434,7 +434,7 @@ Grid2 sweep2d_grid(int n)
 {
     Grid2 g;
     g.bx = (n + kSweepCols - 1) / kSweepCols;
-    g.H = chunk_rows(g.bx, n, 8 * num_sms(), 8, 64);
+    g.H = chunk_rows(g.bx, n, 8 * num_sms(), 2, 64);
     g.by = (n + g.H - 1) / g.H;
     return g;
 }
@@ -473,7 +473,7 @@ cudaError_t launch_resrestrict2d(const T *u, const T *b, bool unscaled, T *bc, i
 {
     const int nc = (n - 1) / 2;
     const int bx = (nc + kRestrictCols - 1) / kRestrictCols;
-    const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 4, 32);
+    const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 1, 32);
     const dim3 grid(bx, (nc + Hc - 1) / Hc);
     const int hk = h2_exponent(n);
     if (unscaled)
@@ -489,7 +489,7 @@ cudaError_t launch_prolong2d(const T *e, T *u, int n, cudaStream_t s)
 {
     const int nc = (n - 1) / 2;
     const int bx = (nc + 1 + kProlongThreads - 1) / kProlongThreads;
-    const int Hc = chunk_rows(bx, nc + 1, 8 * num_sms(), 4, 32);
+    const int Hc = chunk_rows(bx, nc + 1, 8 * num_sms(), 1, 32);
     const dim3 grid(bx, (nc + 1 + Hc - 1) / Hc);
     prolong2d_kernel<T><<<grid, kProlongThreads, 0, s>>>(e, u, n, Hc);
     count_launch(1);

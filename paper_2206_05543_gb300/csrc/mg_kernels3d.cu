@@ -417,7 +417,7 @@ Grid3 sweep3d_grid(int n)
 {
     Grid3 g;
     g.bx = g.by = (n + kS3Out - 1) / kS3Out;
-    g.Z = chunk_rows(g.bx * g.by, n, 4 * num_sms(), 4, 64);
+    g.Z = chunk_rows(g.bx * g.by, n, 4 * num_sms(), 2, 64);
     g.bz = (n + g.Z - 1) / g.Z;
     return g;
 }
@@ -427,7 +427,7 @@ Grid3 residual3d_grid(int n)
     Grid3 g;
     g.bx = (n + kQX - 1) / kQX;
     g.by = (n + kQY - 1) / kQY;
-    g.Z = chunk_rows(g.bx * g.by, n, 8 * num_sms(), 4, 64);
+    g.Z = chunk_rows(g.bx * g.by, n, 8 * num_sms(), 2, 64);
     g.bz = (n + g.Z - 1) / g.Z;
     return g;
 }
@@ -466,7 +466,7 @@ cudaError_t launch_resrestrict3d(const T *u, const T *b, bool unscaled, T *bc, i
 {
     const int nc = (n - 1) / 2;
     const int bxy = (nc + kR3 - 1) / kR3;
-    const int Zc = chunk_rows(bxy * bxy, nc, 8 * num_sms(), 2, 32);
+    const int Zc = chunk_rows(bxy * bxy, nc, 8 * num_sms(), 1, 32);
     const dim3 grid(bxy, bxy, (nc + Zc - 1) / Zc);
     const int hk = h2_exponent(n);
     if (unscaled)
@@ -482,7 +482,7 @@ cudaError_t launch_prolong3d(const T *e, T *u, int n, cudaStream_t s)
 {
     const int nc = (n - 1) / 2;
     const int bx = (n + kP3X - 1) / kP3X, by = (n + kP3Y - 1) / kP3Y;
-    const int Zc = chunk_rows(bx * by, nc + 1, 8 * num_sms(), 2, 32);
+    const int Zc = chunk_rows(bx * by, nc + 1, 8 * num_sms(), 1, 32);
     const dim3 grid(bx, by, (nc + 1 + Zc - 1) / Zc);
     prolong3d_kernel<T><<<grid, kP3X * kP3Y, 0, s>>>(e, u, n, Zc);
     count_launch(1);

@@ -429,7 +429,7 @@ int sweep2d_pl_blocks(int n, int H) { return ((n + kPLCols - 1) / kPLCols) * ((n
 int sweep2d_pl_H(int n)
 {
     const int bx = (n + kPLCols - 1) / kPLCols;
-    return chunk_rows(bx, n, 8 * num_sms(), 8, 64);
+    return chunk_rows(bx, n, 8 * num_sms(), 2, 64);
 }
 
 cudaError_t launch_sweep2d_pl(const float *u, const float *b, float *out, int n, const double *c, double *partials,
@@ -465,7 +465,7 @@ cudaError_t launch_resrestrict2d_pl(const float *u, const float *b, float *bc, i
     const Pitch2 g = pitch2(n), gc = pitch2((n - 1) / 2);
     const int nc = gc.n;
     const int bx = (nc + kPLCols - 1) / kPLCols;
-    const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 4, 32);
+    const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 1, 32);
     resrestrict2d_pl_kernel<<<dim3(bx, (nc + Hc - 1) / Hc), kPLThreads, 0, s>>>(u, b, bc, g, gc, Hc);
     count_launch(1);
     return cudaGetLastError();
@@ -476,7 +476,7 @@ cudaError_t launch_prolong2d_pl(const float *e, float *u, int n, cudaStream_t s)
     const Pitch2 g = pitch2(n), gc = pitch2((n - 1) / 2);
     const int nc = gc.n;
     const int bx = (nc + 1 + kPLCols - 1) / kPLCols;
-    const int Hc = chunk_rows(bx, nc + 1, 8 * num_sms(), 4, 32);
+    const int Hc = chunk_rows(bx, nc + 1, 8 * num_sms(), 1, 32);
     prolong2d_pl_kernel<<<dim3(bx, (nc + 1 + Hc - 1) / Hc), kPLThreads, 0, s>>>(e, u, g, gc, Hc);
     count_launch(1);
     return cudaGetLastError();

@@ -132,7 +132,7 @@ cudaError_t launch_prolong3d_pl(const float *e, float *u, int n, cudaStream_t s)
     const int nc = gc.n;
     const int qxs = (n + 3) / 4;
     const int bx = (qxs + kR3X - 1) / kR3X, by = (n + kR3Y - 1) / kR3Y;
-    const int Zc = chunk_rows(bx * by, nc + 1, 8 * num_sms(), 2, 32);
+    const int Zc = chunk_rows(bx * by, nc + 1, 8 * num_sms(), 1, 32);
     prolong3d_pl_kernel<<<dim3(bx, by, (nc + 1 + Zc - 1) / Zc), kR3X * kR3Y, 0, s>>>(e, u, g, gc, Zc);
     count_launch(1);
     return cudaGetLastError();
