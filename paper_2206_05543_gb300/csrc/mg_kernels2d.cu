@@ -430,6 +430,8 @@ residual2d_batched(const BRes<OutT> *__restrict__ tab, int nprob, const int *__r
 // launchers
 // ---------------------------------------------------------------------------
 
+constexpr int kBatchedResidualRows = 32;
+
 Grid2 sweep2d_grid(int n)
 {
     Grid2 g;
@@ -522,9 +524,20 @@ static int persistent_grid(const void *fn, int threads, long items)
     return (int)std::max<long>(1, std::min<long>(items, (long)per_sm * num_sms()));
 }
 
+// The batch supplies the parallelism, so the batched residual marches tall
+// row chunks (a chunk's prologue costs three rows and a barrier)
+static Grid2 residual2d_batched_grid(int n)
+{
+    Grid2 g;
+    g.bx = (n + kSweepCols - 1) / kSweepCols;
+    g.H = n < kBatchedResidualRows ? n : kBatchedResidualRows;
+    g.by = (n + g.H - 1) / g.H;
+    return g;
+}
+
 int residual2d_batched_tiles(int n)
 {
-    const Grid2 g = sweep2d_grid(n);
+    const Grid2 g = residual2d_batched_grid(n);
     return g.bx * g.by;
 }
 
@@ -532,7 +545,7 @@ template <typename OutT>
 cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s,
                                       long opitch, long ooff)
 {
-    const Grid2 g = sweep2d_grid(n);
+    const Grid2 g = residual2d_batched_grid(n);
     const long items = (long)nprob * g.bx * g.by;
     const int grid = persistent_grid((const void *)residual2d_batched<OutT>, kSweepThreads / 2, items);
     residual2d_batched<OutT><<<grid, kSweepThreads / 2, 0, s>>>(tab, nprob, active, n, g.H, g.bx, g.by, h2_exponent(n),
