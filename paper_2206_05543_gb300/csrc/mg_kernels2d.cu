@@ -28,131 +28,139 @@ namespace mg {
 //   u' = fma(c2, C, fma(c1, E, fma(c0, rh_p, u_p)))
 // The pairs are shared between points: hp(q) = rh(q - x) + rh(q + x) gives
 // E = hp(p) + (rh_S + rh_N) and C = hp(p - y) + hp(p + y).
-// Block: two adjacent columns per thread (two independent FP64 chains):
-// 128 threads cover the 256 columns X0 .. X0 + 255 of a strip,
-// X0 = 254 bx - 1; columns 1 .. 254 of the strip are written, 0 and 255
-// supply halo residuals. Rows [y0, y0 + H). One barrier per row: at step j
-// the u row j + 1 goes to the other half of the double buffer next to the
-// residual row j, and every global load is issued one step before its use.
+// Block: K adjacent columns per thread (K independent FP64 chains; K = 2,
+// measured fastest against 1 and 4): 256 / K threads cover the 256 columns
+// X0 .. X0 + 255 of a strip, X0 = 254 bx - 1; columns 1 .. 254 of the strip
+// are written, 0 and 255 supply halo residuals. Rows [y0, y0 + H). One
+// barrier per row: at step j the u row j + 1 goes to the other half of the
+// double buffer next to the residual row j, and every global load is issued
+// one step before its use. Warps whose columns all lie at x >= n skip the
+// FP64 arithmetic and only store the zeros their neighbours read.
 // ZERO_U: the input is u = 0 (first sweep on a coarse level): rh = bh.
 // NORM: accumulate the squared residual of the input over owned points.
 // ---------------------------------------------------------------------------
-template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM, int K>
 __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out,
                                               int n, int H, T c0, T c1, T c2, int hk, int tbx, int tby,
                                               double *__restrict__ partial)
 {
-    constexpr int NT = kSweepThreads / 2;
-    __shared__ T su[2][kSweepThreads + 2];  // [c + 1]: column X0 + c, c in -1 .. 256
+    constexpr int NT = kSweepThreads / K;
+    __shared__ T su[2][kSweepThreads + 2];
     __shared__ T sr[2][kSweepThreads + 2];
     const int t = threadIdx.x;
     const int X0 = tbx * kSweepCols - 1;
-    const int xa = X0 + 2 * t, xb = xa + 1;
+    const int xc0 = X0 + K * t;
     const int y0 = tby * H, y1 = min(y0 + H, n);
-    const bool ina = xa >= 0 && xa < n, inb = xb >= 0 && xb < n;
-    const bool owna = t >= 1 && ina, ownb = t <= NT - 2 && inb;
     const bool lt = t == 0, rt = t == NT - 1;
-    // a warp whose 64 columns all lie at x >= n has only zero residuals: it
-    // skips the FP64 work (the pipe, not the bytes, bounds this kernel) and
-    // only stores the zeros its neighbours read
-    const bool wact = X0 + 2 * (t & ~31) < n;
+    const bool wact = X0 + K * (t & ~31) < n;  // the warp has a column inside the grid
     const size_t ld = (size_t)n;
     auto get = [&](const T *a, int yy, int xx) -> T {
         return (yy >= 0 && yy < n && xx >= 0 && xx < n) ? a[(size_t)yy * ld + xx] : T(0);
     };
-    T ap = T(0), ac = T(0), an = T(0), ann = T(0), bp = T(0), bc = T(0), bn = T(0), bnn = T(0);
-    T hn = T(0), hnn = T(0);  // halo column of the edge threads, rows j + 1, j + 2
+    bool in[K], own[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int x = xc0 + k, c = K * t + k;
+        in[k] = x >= 0 && x < n;
+        own[k] = in[k] && c >= 1 && c <= kSweepCols;
+    }
+    T up[K], uc[K], un[K], unn[K], bcur[K], r1[K], r2[K], p1[K], p2[K];
+    T hn = T(0), hnn = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        up[k] = uc[k] = un[k] = unn[k] = T(0);
+        r1[k] = r2[k] = p1[k] = p2[k] = T(0);
+    }
     if (!ZERO_U) {
-        ap = get(u, y0 - 2, xa);
-        bp = get(u, y0 - 2, xb);
-        ac = get(u, y0 - 1, xa);
-        bc = get(u, y0 - 1, xb);
-        an = get(u, y0, xa);
-        bn = get(u, y0, xb);
-        const int buf0 = (y0 - 1) & 1;
-        su[buf0][2 * t + 1] = ac;
-        su[buf0][2 * t + 2] = bc;
-        if (lt) su[buf0][0] = get(u, y0 - 1, xa - 1);
-        if (rt) su[buf0][kSweepThreads + 1] = get(u, y0 - 1, xb + 1);
-        if (lt) hn = get(u, y0, xa - 1);
-        if (rt) hn = get(u, y0, xb + 1);
+        const int b0 = (y0 - 1) & 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            up[k] = get(u, y0 - 2, xc0 + k);
+            uc[k] = get(u, y0 - 1, xc0 + k);
+            un[k] = get(u, y0, xc0 + k);
+            su[b0][K * t + k + 1] = uc[k];
+        }
+        if (lt) su[b0][0] = get(u, y0 - 1, xc0 - 1);
+        if (rt) su[b0][kSweepThreads + 1] = get(u, y0 - 1, xc0 + K);
+        if (lt) hn = get(u, y0, xc0 - 1);
+        if (rt) hn = get(u, y0, xc0 + K);
         __syncthreads();
     }
-    T ba_cur = get(b, y0 - 1, xa), bb_cur = get(b, y0 - 1, xb);
-    T ra1 = T(0), ra2 = T(0), rb1 = T(0), rb2 = T(0), pa1 = T(0), pa2 = T(0), pb1 = T(0), pb2 = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) bcur[k] = get(b, y0 - 1, xc0 + k);
     double acc = 0.0;
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
-        T fa = ba_cur, fb = bb_cur;
-        ba_cur = get(b, j + 1, xa);
-        bb_cur = get(b, j + 1, xb);
-        if (UNSCALED_B) {
-            fa = scale2(fa, hk);
-            fb = scale2(fb, hk);
+        T f[K], r[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            f[k] = bcur[k];
+            bcur[k] = get(b, j + 1, xc0 + k);
+            if (UNSCALED_B) f[k] = scale2(f[k], hk);
+            r[k] = T(0);
         }
-        T ra = T(0), rb = T(0);
         if (!ZERO_U) {
-            ann = get(u, j + 2, xa);
-            bnn = get(u, j + 2, xb);
-            if (lt) hnn = get(u, j + 2, xa - 1);
-            if (rt) hnn = get(u, j + 2, xb + 1);
+#pragma unroll
+            for (int k = 0; k < K; ++k) unn[k] = get(u, j + 2, xc0 + k);
+            if (lt) hnn = get(u, j + 2, xc0 - 1);
+            if (rt) hnn = get(u, j + 2, xc0 + K);
             if (wact) {
-                const T sa = radd(radd(su[buf][2 * t], bc), radd(ap, an));
-                const T sb = radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn));
-                ra = radd(rfma(T(-4), ac, fa), sa);
-                rb = radd(rfma(T(-4), bc, fb), sb);
+                const T wl = su[buf][K * t], wr = su[buf][K * t + K + 1];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const T W = k == 0 ? wl : uc[k - 1], E = k == K - 1 ? wr : uc[k + 1];
+                    r[k] = radd(rfma(T(-4), uc[k], f[k]), radd(radd(W, E), radd(up[k], un[k])));
+                }
             }
-            su[1 - buf][2 * t + 1] = an;
-            su[1 - buf][2 * t + 2] = bn;
+#pragma unroll
+            for (int k = 0; k < K; ++k) su[1 - buf][K * t + k + 1] = un[k];
             if (lt) su[1 - buf][0] = hn;
             if (rt) su[1 - buf][kSweepThreads + 1] = hn;
         } else {
-            ra = fa;
-            rb = fb;
+#pragma unroll
+            for (int k = 0; k < K; ++k) r[k] = f[k];
         }
         const bool jin = j >= 0 && j < n;
-        if (!(ina && jin)) ra = T(0);
-        if (!(inb && jin)) rb = T(0);
-        if (NORM && j >= y0 && j < y1) {
-            if (owna) acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
-            if (ownb) acc = fma(to_out<double>(rb), to_out<double>(rb), acc);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!(in[k] && jin)) r[k] = T(0);
+            if (NORM && own[k] && j >= y0 && j < y1) acc = fma(to_out<double>(r[k]), to_out<double>(r[k]), acc);
+            sr[buf][K * t + k + 1] = r[k];
         }
-        sr[buf][2 * t + 1] = ra;
-        sr[buf][2 * t + 2] = rb;
         __syncthreads();
-        const T pa = (lt || !wact) ? T(0) : radd(sr[buf][2 * t], rb);
-        const T pb = (rt || !wact) ? T(0) : radd(ra, sr[buf][2 * t + 3]);
-        if (j - 1 >= y0) {  // output row j - 1
-            if (owna) {
-                const T E = radd(pa1, radd(ra2, ra));
-                const T C = radd(pa2, pa);
-                const T base = ZERO_U ? rmul(c0, ra1) : rfma(c0, ra1, ap);
-                out[(size_t)(j - 1) * ld + xa] = rfma(c2, C, rfma(c1, E, base));
-            }
-            if (ownb) {
-                const T E = radd(pb1, radd(rb2, rb));
-                const T C = radd(pb2, pb);
-                const T base = ZERO_U ? rmul(c0, rb1) : rfma(c0, rb1, bp);
-                out[(size_t)(j - 1) * ld + xb] = rfma(c2, C, rfma(c1, E, base));
+        T p[K];
+        {
+            const T rl = sr[buf][K * t], rr = sr[buf][K * t + K + 1];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const T W = k == 0 ? rl : r[k - 1], E = k == K - 1 ? rr : r[k + 1];
+                const int c = K * t + k;
+                p[k] = (c >= 1 && c <= kSweepCols && wact) ? radd(W, E) : T(0);
             }
         }
-        ra2 = ra1;
-        ra1 = ra;
-        rb2 = rb1;
-        rb1 = rb;
-        pa2 = pa1;
-        pa1 = pa;
-        pb2 = pb1;
-        pb1 = pb;
-        if (!ZERO_U) {
-            ap = ac;
-            ac = an;
-            an = ann;
-            bp = bc;
-            bc = bn;
-            bn = bnn;
-            hn = hnn;
+        if (j - 1 >= y0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (!own[k]) continue;
+                const T E = radd(p1[k], radd(r2[k], r[k]));
+                const T C = radd(p2[k], p[k]);
+                const T base = ZERO_U ? rmul(c0, r1[k]) : rfma(c0, r1[k], up[k]);
+                out[(size_t)(j - 1) * ld + xc0 + k] = rfma(c2, C, rfma(c1, E, base));
+            }
         }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            r2[k] = r1[k];
+            r1[k] = r[k];
+            p2[k] = p1[k];
+            p1[k] = p[k];
+            if (!ZERO_U) {
+                up[k] = uc[k];
+                uc[k] = un[k];
+                un[k] = unn[k];
+            }
+        }
+        hn = hnn;
     }
     if (NORM) block_sum_store<NT>(acc, partial);
 }
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(kSweepThreads / 2, 10)
 sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int H,
                T c0, T c1, T c2, int hk, double *__restrict__ partials)
 {
-    sweep2d_tile<T, ZERO_U, UNSCALED_B, NORM>(u, b, out, n, H, c0, c1, c2, hk, blockIdx.x, blockIdx.y,
+    sweep2d_tile<T, ZERO_U, UNSCALED_B, NORM, 2>(u, b, out, n, H, c0, c1, c2, hk, blockIdx.x, blockIdx.y,
                                               NORM ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr);
 }
 
