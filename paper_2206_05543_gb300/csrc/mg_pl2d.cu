@@ -217,27 +217,33 @@ __device__ __forceinline__ void resrestrict2d_pl_tile(const float *__restrict__ 
         const int buf = f & 1;
         const float4 na = row4(U, f + 1, fx), nb = row4(U, f + 1, fx + 4);
         const float4 ba = row4(Bp, f, fx), bb = row4(Bp, f, fx + 4);
-        st4(&su[buf][4 + 8 * t], ca);
-        st4(&su[buf][8 + 8 * t], cb);
-        if (t == 0) st4(&su[buf][0], row4(U, f, fxb - 4));
-        if (t == kPLThreads - 1) st4(&su[buf][2 * kPLCols + 4], row4(U, f, fxb + 2 * kPLCols));
+        // horizontal neighbours: within a thread from registers, across
+        // threads of a warp by shuffles, across warps through shared memory
+        // (only the warp-edge values are stored)
+        const int lane = t & 31;
+        if (lane == 0) su[buf][4 + 8 * t] = ca.x;
+        if (lane == 31) su[buf][11 + 8 * t] = cb.w;
+        if (t == 0) su[buf][3] = row4(U, f, fxb - 4).w;
+        if (t == kPLThreads - 1) su[buf][2 * kPLCols + 4] = row4(U, f, fxb + 2 * kPLCols).x;
         __syncthreads();
         float r[8];
         {
-            const float *s = &su[buf][4 + 8 * t];
+            float uw = __shfl_up_sync(0xffffffffu, cb.w, 1), ue = __shfl_down_sync(0xffffffffu, ca.x, 1);
+            if (lane == 0) uw = su[buf][3 + 8 * t];
+            if (lane == 31) ue = su[buf][12 + 8 * t];
+            const float uc8[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
             for (int k = 0; k < 8; ++k) {
-                const float ucc = k < 4 ? cc4(ca, k) : cc4(cb, k - 4);
                 const float uu = k < 4 ? cc4(pa, k) : cc4(pb, k - 4);
                 const float ud = k < 4 ? cc4(na, k) : cc4(nb, k - 4);
                 const float bk = k < 4 ? cc4(ba, k) : cc4(bb, k - 4);
-                const float ss = radd(radd(s[k - 1], s[k + 1]), radd(uu, ud));
-                r[k] = radd(rfma(-4.f, ucc, bk), ss);
+                const float W = k == 0 ? uw : uc8[k - 1], E = k == 7 ? ue : uc8[k + 1];
+                const float ss = radd(radd(W, E), radd(uu, ud));
+                r[k] = radd(rfma(-4.f, uc8[k], bk), ss);
                 if (!(fx + k < n && f < n)) r[k] = 0.f;
             }
         }
         // the right neighbour fine column 2 ic + 8 comes from the next thread
-        st4(&sr[buf][4 + 8 * t], make_float4(r[0], r[1], r[2], r[3]));
-        st4(&sr[buf][8 + 8 * t], make_float4(r[4], r[5], r[6], r[7]));
+        if (lane == 0) sr[buf][4 + 8 * t] = r[0];
         if (t == kPLThreads - 1) {
             // fine column fxb + 2*kPLCols: residual recomputed from global memory
             const int xr = fxb + 2 * kPLCols;
@@ -252,8 +258,9 @@ __device__ __forceinline__ void resrestrict2d_pl_tile(const float *__restrict__ 
         __syncthreads();
         float4 tx;
         {
-            const float *s = &sr[buf][4 + 8 * t];
-            for (int k = 0; k < 4; ++k) c4(tx, k) = rfma(2.f, s[2 * k + 1], radd(s[2 * k], s[2 * k + 2]));
+            float r8 = __shfl_down_sync(0xffffffffu, r[0], 1);
+            if (lane == 31) r8 = sr[buf][12 + 8 * t];
+            for (int k = 0; k < 4; ++k) c4(tx, k) = rfma(2.f, r[2 * k + 1], radd(r[2 * k], k == 3 ? r8 : r[2 * k + 2]));
         }
         if (f >= f0 + 2 && (f & 1) == 0 && ic < nc) {
             const int jc = f / 2 - 1;
