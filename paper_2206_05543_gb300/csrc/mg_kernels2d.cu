@@ -262,7 +262,7 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
 
 // at most 6 blocks per SM (measured fastest for the FP64 form)
 template <typename T, bool UNSCALED_B>
-__global__ void __launch_bounds__(kRestrictThreads, 6)
+__global__ void __launch_bounds__(kRestrictThreads, 5)
 resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
                      int Hc, int hk)
 {

@@ -40,7 +40,7 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 // ---------------------------------------------------------------------------
 // at most 4 blocks per SM (64 registers; measured fastest for the FP64 form)
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__global__ void __launch_bounds__(kS3Threads, 4)
+__global__ void __launch_bounds__(kS3Threads, 2)
 sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int Z,
                T c0, T c1, int hk, double *__restrict__ partials)
 {
