@@ -260,7 +260,7 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
     }
 }
 
-// at most 6 blocks per SM (measured fastest for the FP64 form)
+// at most 5 blocks per SM (measured fastest for the FP64 form against 4, 6, 8)
 template <typename T, bool UNSCALED_B>
 __global__ void __launch_bounds__(kRestrictThreads, 5)
 resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,

@@ -38,7 +38,8 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 // reads the residual plane written one step earlier, and every global load
 // is issued one step before its use.
 // ---------------------------------------------------------------------------
-// at most 4 blocks per SM (64 registers; measured fastest for the FP64 form)
+// at most 2 blocks per SM (no register cap that forces spills; measured fastest
+// for the FP64 form against 1, 3 and 4)
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __global__ void __launch_bounds__(kS3Threads, 2)
 sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int Z,
@@ -170,7 +171,8 @@ constexpr int kR3F = 2 * kR3 + 1;    // fine residual patch edge (33)
 constexpr int kR3U = kR3F + 2;       // u patch edge incl. halo (35)
 constexpr int kR3Threads = kR3 * kR3;
 
-// at most 4 blocks per SM (64 registers; measured fastest for the FP64 form)
+// at most 2 blocks per SM (no register cap that forces spills; measured fastest
+// for the FP64 form against 1, 3 and 4)
 template <typename T, bool UNSCALED_B>
 __global__ void __launch_bounds__(kR3Threads, 4)
 resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n, int Zc,
