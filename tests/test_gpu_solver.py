@@ -89,6 +89,40 @@ def test_3d_sine_and_jacobi():
     _parity(3, 32, inputs.uniform(3, 32, 3), name="jacobi", max_cycles=80)
 
 
+def test_final_measurement_guess_that_misses():
+    """The solver replaces the speculative pre-sweep by a residual-norm-only
+    pass when the last convergence factor, carried one cycle forward, puts the
+    next residual under the tolerance. The factor of this problem grows from
+    cycle to cycle, so with the tolerance between the carried-forward guess
+    and the true residual of cycle j the guess misses: the solver must find
+    the cycle unconverged, smooth after all and go on. Cycles, history and u
+    stay those of the oracle, which never guesses."""
+    b = inputs.uniform(2, 64, 64)
+    w = coeffs.default(2)
+    full = oracle.solve(b, w, tol=0.0, max_cycles=10)
+    h = np.asarray(full.hist)
+    j = 8
+    guess = h[j - 1] ** 2 / h[j - 2]
+    assert guess < h[j] * (1 - 1e-3)  # the factor grew at cycle j
+    tol = float(np.sqrt(guess * h[j]) / h[0])
+    _, ref = _parity(2, 64, b, tol=tol)
+    assert ref.cycles == j + 1
+
+
+def test_final_measurement_guess_that_holds():
+    """Tolerance just above the residual of cycle j: the carried-forward guess
+    fires at cycle j and the residual-norm-only pass ends the solve there."""
+    b = inputs.uniform(3, 32, 5)
+    w = coeffs.default(3)
+    full = oracle.solve(b, w, tol=0.0, max_cycles=9, nu1=2, nu2=2)
+    h = np.asarray(full.hist)
+    j = 7
+    tol = float(h[j] * (1 + 1e-6) / h[0])
+    assert h[j - 1] ** 2 / h[j - 2] <= tol * h[0]
+    _, ref = _parity(3, 32, b, nu1=2, nu2=2, tol=tol)
+    assert ref.cycles == j
+
+
 def test_vcycle_single_cycle_bitwise():
     for d, N in ((2, 256), (3, 32)):
         b = inputs.uniform(d, N, 4)
