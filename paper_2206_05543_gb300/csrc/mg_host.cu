@@ -173,8 +173,7 @@ static int sweep_partials(int d, int n)
         const Grid2 g = sweep2d_grid(n);
         return g.bx * g.by;
     }
-    const Grid3 g = sweep3d_grid(n);
-    return g.bx * g.by * g.bz;
+    return sweep3d_plan(n).blocks;
 }
 static int residual_partials(int d, int n)
 {

@@ -49,7 +49,12 @@ cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *r
 struct Grid3 {
     int bx, by, bz, Z;
 };
-Grid3 sweep3d_grid(int n);
+// persistent 3D sweep: bx x bx tiles x n planes = total items, `per` per block
+struct S3Plan {
+    int bx, blocks;
+    long total, per;
+};
+S3Plan sweep3d_plan(int n);
 Grid3 residual3d_grid(int n);
 
 // 3D level operators (same conventions as the 2D ones; c = (c0, c1)).

@@ -38,18 +38,16 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 // reads the residual plane written one step earlier, and every global load
 // is issued one step before its use.
 // ---------------------------------------------------------------------------
-// at most 2 blocks per SM (no register cap that forces spills; measured fastest
-// for the FP64 form against 1, 3 and 4)
+// One segment: output planes [z0, z1) of tile (tx, ty). Starts and ends with
+// the shared buffers free (the last step of the march ends in a barrier).
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__global__ void __launch_bounds__(kS3Threads, 2)
-sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int Z,
-               T c0, T c1, int hk, double *__restrict__ partials)
+__device__ __forceinline__ void sweep3d_segment(T (&su)[2][kS3U * kS3U], T (&sr)[2][kS3 * kS3],
+                                                const T *__restrict__ u, const T *__restrict__ b,
+                                                T *__restrict__ out, int n, int tx, int ty, int z0, int z1,
+                                                T c0, T c1, int hk, double &acc)
 {
-    __shared__ T su[2][kS3U * kS3U];
-    __shared__ T sr[2][kS3 * kS3];
     const int t = threadIdx.x;
-    const int ex0 = blockIdx.x * kS3Out - 1, ey0 = blockIdx.y * kS3Out - 1;
-    const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
+    const int ex0 = tx * kS3Out - 1, ey0 = ty * kS3Out - 1;
     const size_t plane = (size_t)n * n;
 
     int px[kS3Pts], py[kS3Pts];
@@ -93,7 +91,6 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
         }
         __syncthreads();
     }
-    double acc = 0.0;
 
     for (int zz = z0 - 1; zz <= z1; ++zz) {  // residual plane zz, output plane zz - 1
         const int buf = zz & 1;
@@ -152,7 +149,32 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
         }
         ring_next = ring_nn;
     }
-    if (NORM) block_sum_store<kS3Threads>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
+}
+
+// Persistent and balanced: the (tile, plane) items, tile-major, are cut into
+// gridDim.x equal runs of `per` consecutive items, one per block; a run is
+// one or more z-segments of consecutive tiles. Every block does the same
+// work, so the launch has no partly filled last wave (with 2 blocks per SM a
+// tile-by-z-chunk grid left up to half of a wave idle). One squared partial
+// sum per block. At most 2 blocks per SM (no register cap that forces
+// spills; measured fastest for the FP64 form against 1, 3 and 4).
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+__global__ void __launch_bounds__(kS3Threads, 2)
+sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int bx, long total,
+               long per, T c0, T c1, int hk, double *__restrict__ partials)
+{
+    __shared__ T su[2][kS3U * kS3U];
+    __shared__ T sr[2][kS3 * kS3];
+    double acc = 0.0;
+    const long w0 = (long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
+    for (long w = w0; w < w1;) {
+        const int tile = (int)(w / n), z0 = (int)(w - (long)tile * n);
+        const int z1 = (int)(z0 + (w1 - w) < (long)n ? z0 + (w1 - w) : (long)n);
+        sweep3d_segment<T, ZERO_U, UNSCALED_B, NORM>(su, sr, u, b, out, n, tile % bx, tile / bx, z0, z1, c0, c1,
+                                                     hk, acc);
+        w += z1 - z0;
+    }
+    if (NORM) block_sum_store<kS3Threads>(acc, &partials[blockIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,12 +437,15 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-Grid3 sweep3d_grid(int n)
+// Runs of at least 8 planes; at most 2 resident blocks per SM.
+S3Plan sweep3d_plan(int n)
 {
-    Grid3 g;
-    g.bx = g.by = (n + kS3Out - 1) / kS3Out;
-    g.Z = chunk_rows(g.bx * g.by, n, 4 * num_sms(), 2, 64);
-    g.bz = (n + g.Z - 1) / g.Z;
+    S3Plan g;
+    g.bx = (n + kS3Out - 1) / kS3Out;
+    g.total = (long)g.bx * g.bx * n;
+    const long most = std::min<long>(2L * num_sms(), (g.total + 7) / 8);
+    g.per = (g.total + most - 1) / most;
+    g.blocks = (int)((g.total + g.per - 1) / g.per);
     return g;
 }
 
@@ -438,12 +463,12 @@ template <typename T>
 cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
                            double *partials, cudaStream_t s)
 {
-    const Grid3 g = sweep3d_grid(n);
-    const dim3 grid(g.bx, g.by, g.bz);
+    const S3Plan g = sweep3d_plan(n);
     const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]);
-#define MG_SWEEP(ZU, UB, NRM) \
-    sweep3d_kernel<T, ZU, UB, NRM><<<grid, kS3Threads, 0, s>>>(u, b, out, n, g.Z, c0, c1, hk, partials)
+#define MG_SWEEP(ZU, UB, NRM)                                                                                   \
+    sweep3d_kernel<T, ZU, UB, NRM><<<g.blocks, kS3Threads, 0, s>>>(u, b, out, n, g.bx, g.total, g.per, c0, c1, hk, \
+                                                                   partials)
     const bool z = u == nullptr, nrm = partials != nullptr;
     if (z) {
         if (unscaled) {

@@ -55,8 +55,7 @@ int partials_needed(int d, int n)
         const mg::Grid2 g = mg::sweep2d_grid(n);
         return g.bx * g.by;
     }
-    const mg::Grid3 g = mg::sweep3d_grid(n);
-    return g.bx * g.by * g.bz;
+    return mg::sweep3d_plan(n).blocks;
 }
 
 template <typename T>
