@@ -25,6 +25,15 @@ namespace mg {
 // issue at 1.6.
 static __device__ double k_unit_one = 1.0;
 __device__ __forceinline__ double radd(double a, double b) { return __fma_rn(a, __ldg(&k_unit_one), b); }
+// A constant or kernel-parameter FMA operand (stencil weight, SPAI
+// coefficient) copied into a register once per thread: v * 1 with the opaque
+// 1.0, exact. A DFMA that takes one operand from the constant bank issued at
+// 1.6 per clock per SM like DADD in a microbenchmark, with all operands in
+// registers at 1.9. Used where it measured faster (the 3D FP64 sweep and
+// restriction, 3D FP64 solve -2.6 %); the 2D kernels, whose register budget
+// is tight, got slower with it.
+__device__ __forceinline__ double in_reg(double v) { return __dmul_rn(v, __ldg(&k_unit_one)); }
+__device__ __forceinline__ float in_reg(float v) { return v; }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }

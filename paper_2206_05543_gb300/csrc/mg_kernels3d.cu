@@ -49,6 +49,9 @@ __device__ __forceinline__ void sweep3d_segment(T (&su)[2][kS3U * kS3U], T (&sr)
     const int t = threadIdx.x;
     const int ex0 = tx * kS3Out - 1, ey0 = ty * kS3Out - 1;
     const size_t plane = (size_t)n * n;
+    const T m6 = in_reg(T(-6));
+    c0 = in_reg(c0);
+    c1 = in_reg(c1);
 
     int px[kS3Pts], py[kS3Pts];
     bool inside[kS3Pts], own[kS3Pts];
@@ -112,7 +115,7 @@ __device__ __forceinline__ void sweep3d_segment(T (&su)[2][kS3U * kS3U], T (&sr)
                 const T *row = &su[buf][(j + 1) * kS3U + (i + 1)];
                 const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kS3U], row[kS3U])),
                                  radd(u_prev[k], u_next[k]));
-                r = radd(rfma(T(-6), u_cur[k], bb), s);
+                r = radd(rfma(m6, u_cur[k], bb), s);
                 su[1 - buf][(j + 1) * kS3U + (i + 1)] = u_next[k];
             } else {
                 r = bb;
@@ -203,6 +206,7 @@ resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
     __shared__ T su[3][kR3U * kR3U];
     __shared__ T sr[kR3F * kR3F];
     __shared__ T st1[kR3F * kR3];
+    const T m6 = in_reg(T(-6)), two = in_reg(T(2));
     const int nc = (n - 1) / 2;
     const int t = threadIdx.x;
     const int tic = t % kR3, tjc = t / kR3;
@@ -270,7 +274,7 @@ resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
                 if (UNSCALED_B) bb = scale2(bb, hk);
                 const T s = radd(radd(radd(uc[p - 1], uc[p + 1]), radd(uc[p - kR3U], uc[p + kR3U])),
                                  radd(um[p], up[p]));
-                r = radd(rfma(T(-6), uc[p], bb), s);
+                r = radd(rfma(m6, uc[p], bb), s);
             }
             sr[q] = r;
         }
@@ -278,13 +282,13 @@ resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__rest
         for (int q = t; q < kR3F * kR3; q += kR3Threads) {
             const int k = q % kR3, j = q / kR3;
             const T *row = &sr[j * kR3F + 2 * k];
-            st1[q] = rfma(T(2), row[1], radd(row[0], row[2]));
+            st1[q] = rfma(two, row[1], radd(row[0], row[2]));
         }
         __syncthreads();
-        const T t2 = rfma(T(2), st1[(2 * tjc + 1) * kR3 + tic], radd(st1[2 * tjc * kR3 + tic], st1[(2 * tjc + 2) * kR3 + tic]));
+        const T t2 = rfma(two, st1[(2 * tjc + 1) * kR3 + tic], radd(st1[2 * tjc * kR3 + tic], st1[(2 * tjc + 2) * kR3 + tic]));
         if (f >= f0 + 2 && (f & 1) == 0 && ic < nc && jc < nc) {
             const int kc = f / 2 - 1;
-            const T v = rfma(T(2), t2b, radd(t2a, t2));
+            const T v = rfma(two, t2b, radd(t2a, t2));
             bc[((size_t)kc * nc + jc) * nc + ic] = scale2<-4>(v);  // 0.0625 v
         }
         t2a = t2b;
