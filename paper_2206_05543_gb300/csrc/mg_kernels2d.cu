@@ -297,21 +297,47 @@ __device__ __forceinline__ void prolong2d_tile(const T *__restrict__ e, T *__res
     xpass(m0 - 1, pa, pb);
     const int fa = 2 * k, fb = 2 * k + 1;
     const bool inb = fb < n;
+    // software pipeline: step m + 1's coarse values and u values are loaded
+    // before step m is written (this thread owns columns fa, fb, the block its
+    // fine rows 2 m0 .. 2 m1 - 1)
+    auto ld_rows = [&](int m, T &ea, T &eb, T &oa, T &ob) {
+        const T *re = u + (size_t)(2 * m) * ld;
+        ea = re[fa];
+        eb = inb ? re[fb] : T(0);
+        oa = ob = T(0);
+        if (m < nc) {
+            const T *ro = re + ld;
+            oa = ro[fa];
+            ob = inb ? ro[fb] : T(0);
+        }
+    };
+    T ca, cb, ea, eb, oa, ob;
+    xpass(m0, ca, cb);
+    ld_rows(m0, ea, eb, oa, ob);
     for (int m = m0; m < m1; ++m) {
-        T ca, cb;
-        xpass(m, ca, cb);
+        T na = T(0), nb = T(0), nea = T(0), neb = T(0), noa = T(0), nob = T(0);
+        if (m + 1 < m1) {
+            xpass(m + 1, na, nb);
+            ld_rows(m + 1, nea, neb, noa, nob);
+        }
         {   // fine row 2m
             T *row = u + (size_t)(2 * m) * ld;
-            row[fa] = radd(row[fa], scale2<-1>(radd(pa, ca)));
-            if (inb) row[fb] = radd(row[fb], scale2<-1>(radd(pb, cb)));
+            row[fa] = radd(ea, scale2<-1>(radd(pa, ca)));
+            if (inb) row[fb] = radd(eb, scale2<-1>(radd(pb, cb)));
         }
         if (m < nc) {  // fine row 2m+1
             T *row = u + (size_t)(2 * m + 1) * ld;
-            row[fa] = radd(row[fa], ca);
-            if (inb) row[fb] = radd(row[fb], cb);
+            row[fa] = radd(oa, ca);
+            if (inb) row[fb] = radd(ob, cb);
         }
         pa = ca;
         pb = cb;
+        ca = na;
+        cb = nb;
+        ea = nea;
+        eb = neb;
+        oa = noa;
+        ob = nob;
     }
 }
 

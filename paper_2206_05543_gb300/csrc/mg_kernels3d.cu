@@ -332,18 +332,27 @@ prolong3d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Zc)
     if (fx >= n || fy >= n) return;
     const int m0 = blockIdx.z * Zc, m1 = min(m0 + Zc, nc + 1);
     const size_t plane = (size_t)n * n;
+    T *col = u + (size_t)fy * n + fx;
+    // software pipeline: the coarse values and the two u values of step m + 1
+    // are loaded before step m is written (this thread owns its column, the
+    // block its fine planes 2 m0 .. 2 m1 - 1)
     T prev = p3_interp_xy(e, nc, fx, fy, m0 - 1);
+    T cur = p3_interp_xy(e, nc, fx, fy, m0);
+    T ue = col[(size_t)(2 * m0) * plane];
+    T uo = m0 < nc ? col[(size_t)(2 * m0 + 1) * plane] : T(0);
     for (int m = m0; m < m1; ++m) {
-        const T cur = p3_interp_xy(e, nc, fx, fy, m);
-        {
-            T *p = u + (size_t)(2 * m) * plane + (size_t)fy * n + fx;
-            *p = radd(*p, scale2<-1>(radd(prev, cur)));
+        T nxt = T(0), ue_n = T(0), uo_n = T(0);
+        if (m + 1 < m1) {
+            nxt = p3_interp_xy(e, nc, fx, fy, m + 1);
+            ue_n = col[(size_t)(2 * m + 2) * plane];
+            if (m + 1 < nc) uo_n = col[(size_t)(2 * m + 3) * plane];
         }
-        if (m < nc) {
-            T *p = u + (size_t)(2 * m + 1) * plane + (size_t)fy * n + fx;
-            *p = radd(*p, cur);
-        }
+        col[(size_t)(2 * m) * plane] = radd(ue, scale2<-1>(radd(prev, cur)));
+        if (m < nc) col[(size_t)(2 * m + 1) * plane] = radd(uo, cur);
         prev = cur;
+        cur = nxt;
+        ue = ue_n;
+        uo = uo_n;
     }
 }
 
