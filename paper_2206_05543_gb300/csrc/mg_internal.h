@@ -49,12 +49,15 @@ cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *r
 struct Grid3 {
     int bx, by, bz, Z;
 };
-// persistent 3D sweep: bx x bx tiles x n planes = total items, `per` per block
+// persistent 3D sweep: bx x bx tiles x n planes = total items, `per` per block;
+// resident blocks per SM by element size (FP64 2: no register cap that forces
+// spills; FP32 4)
 struct S3Plan {
     int bx, blocks;
     long total, per;
 };
-S3Plan sweep3d_plan(int n);
+constexpr int sweep3d_blocks_per_sm(int elem_bytes) { return elem_bytes == 8 ? 2 : 4; }
+S3Plan sweep3d_plan(int n, int elem_bytes);
 Grid3 residual3d_grid(int n);
 
 // 3D level operators (same conventions as the 2D ones; c = (c0, c1)).

@@ -159,10 +159,10 @@ __device__ __forceinline__ void sweep3d_segment(T (&su)[2][kS3U * kS3U], T (&sr)
 // one or more z-segments of consecutive tiles. Every block does the same
 // work, so the launch has no partly filled last wave (with 2 blocks per SM a
 // tile-by-z-chunk grid left up to half of a wave idle). One squared partial
-// sum per block. At most 2 blocks per SM (no register cap that forces
-// spills; measured fastest for the FP64 form against 1, 3 and 4).
+// sum per block. Resident blocks per SM: FP64 2 (no register cap that forces
+// spills; measured fastest against 1, 3 and 4), FP32 4.
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__global__ void __launch_bounds__(kS3Threads, 2)
+__global__ void __launch_bounds__(kS3Threads, sweep3d_blocks_per_sm((int)sizeof(T)))
 sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int bx, long total,
                long per, T c0, T c1, int hk, double *__restrict__ partials)
 {
@@ -450,13 +450,13 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// Runs of at least 8 planes; at most 2 resident blocks per SM.
-S3Plan sweep3d_plan(int n)
+// Runs of at least 8 planes; one block per resident slot.
+S3Plan sweep3d_plan(int n, int elem_bytes)
 {
     S3Plan g;
     g.bx = (n + kS3Out - 1) / kS3Out;
     g.total = (long)g.bx * g.bx * n;
-    const long most = std::min<long>(2L * num_sms(), (g.total + 7) / 8);
+    const long most = std::min<long>((long)sweep3d_blocks_per_sm(elem_bytes) * num_sms(), (g.total + 7) / 8);
     g.per = (g.total + most - 1) / most;
     g.blocks = (int)((g.total + g.per - 1) / g.per);
     return g;
@@ -476,7 +476,7 @@ template <typename T>
 cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
                            double *partials, cudaStream_t s)
 {
-    const S3Plan g = sweep3d_plan(n);
+    const S3Plan g = sweep3d_plan(n, (int)sizeof(T));
     const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]);
 #define MG_SWEEP(ZU, UB, NRM)                                                                                   \

@@ -49,13 +49,13 @@ mg_status scratch_on_current_device(double **out)
     return MG_OK;
 }
 
-int partials_needed(int d, int n)
+int partials_needed(int d, int n, int elem_bytes)
 {
     if (d == 2) {
         const mg::Grid2 g = mg::sweep2d_grid(n);
         return g.bx * g.by;
     }
-    return mg::sweep3d_plan(n).blocks;
+    return mg::sweep3d_plan(n, elem_bytes).blocks;
 }
 
 template <typename T>
@@ -81,7 +81,7 @@ extern "C" mg_status mg_op_sweep_norm_noalloc(int d, int n, mg_prec prec, const 
         ncoeffs > (d == 2 ? 3 : 2) || !bh || !u_out || !rnorm2_dev_out || (prec != MG_FP64 && prec != MG_FP32_IR))
         return MG_EINVAL;
     if ((d == 2 && n > 16383) || (d == 3 && n > 1023)) return MG_EINVAL;
-    const int np = partials_needed(d, n);
+    const int np = partials_needed(d, n, prec == MG_FP64 ? 8 : 4);
     if (np > kMaxPartials) return MG_EINVAL;
     double c[3] = {0, 0, 0};
     for (int j = 0; j < ncoeffs; ++j) c[j] = spai_coeffs[j];
