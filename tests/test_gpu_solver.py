@@ -186,6 +186,27 @@ def test_mixed_precision_refinement(d, N, nu, tol_u):
     assert err_mixed <= max(tol_u, 10 * err_fp64)
 
 
+@pytest.mark.parametrize("d,N,nu", [(2, 128, 1), (3, 32, 2)])
+def test_refinement_vcycle_equals_the_solves_iterates(d, N, nu):
+    """mg_vcycle on a refinement context is one refinement iteration (FP64
+    residual, FP32 cycle, u += e in FP64) on the caller's u: one and two calls
+    equal solves stopped after one and two iterations, bit for bit, which
+    checks that the solve's graphs and the single iteration share their
+    arithmetic."""
+    b = inputs.uniform(d, N, 11)
+    with Solver(d, N, nu1=nu, nu2=nu, precision="fp32_ir") as s:
+        u = dev(np.zeros_like(b))
+        s.vcycle(u, dev(b))
+        one = host(u)
+        s.vcycle(u, dev(b))
+        two = host(u)
+        for k, want in ((1, one), (2, two)):
+            info = s.solve(dev(b), tol=0.0, max_cycles=k)
+            assert info.status == MG_ENOCONV and info.cycles == k
+            assert np.array_equal(host(info.u), want)
+    assert not np.array_equal(one, two)
+
+
 @pytest.mark.parametrize("d,N,nu", [(2, 256, 1), (3, 64, 2)])
 def test_refinement_with_several_cycles_per_iteration(d, N, nu):
     """Two and three FP32 cycles per refinement iteration: still the FP64
