@@ -450,13 +450,14 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// Runs of at least 8 planes; one block per resident slot.
+// One block per resident slot, runs of at least 2 planes (small levels need
+// the blocks more than they mind the two extra residual planes of a run).
 S3Plan sweep3d_plan(int n, int elem_bytes)
 {
     S3Plan g;
     g.bx = (n + kS3Out - 1) / kS3Out;
     g.total = (long)g.bx * g.bx * n;
-    const long most = std::min<long>((long)sweep3d_blocks_per_sm(elem_bytes) * num_sms(), (g.total + 7) / 8);
+    const long most = std::min<long>((long)sweep3d_blocks_per_sm(elem_bytes) * num_sms(), (g.total + 1) / 2);
     g.per = (g.total + most - 1) / most;
     g.blocks = (int)((g.total + g.per - 1) / g.per);
     return g;
