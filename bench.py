@@ -168,6 +168,25 @@ def run_reference(args):
     }), flush=True)
 
 
+def reduce_over_ranks(ms: float, cycles: float, device) -> tuple[float, float]:
+    """The job's timing across ranks: the slowest rank's time and the sum of
+    the cycles every rank ran (each rank solves its own replica). One rank
+    returns its own numbers. `device` is where the collective's tensor lives
+    (the rank's GPU under NCCL; the CPU under gloo)."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(ms), float(cycles)
+    if torch.distributed.get_world_size() == 1:
+        return float(ms), float(cycles)
+    t = torch.tensor([ms, cycles], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    tsum = t.clone()
+    torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def _cpu_baseline_sample(threads: int = 1):
     """The oracle timed on a bounded sample: one V(1,1) cycle of the full
     problem (a few seconds of single-threaded CPU work). threads > 1 spreads
@@ -378,15 +397,7 @@ def run_ours(args):
                               "note": "solve-only run"}), flush=True)
         solver.close()
         return
-    if world > 1:
-        t = torch.tensor([ms, cycles], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        ms, total_cycles = float(tmax[0]), float(tsum[1])
-    else:
-        total_cycles = cycles
+    ms, total_cycles = reduce_over_ranks(ms, cycles, "cuda")
     value = UNKNOWNS * total_cycles / (ms * 1e-3)
 
     # end to end through the public API, every step: its b from pinned host
