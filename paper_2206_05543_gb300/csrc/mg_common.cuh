@@ -154,7 +154,7 @@ __host__ __device__ inline int h2_exponent(int n)
 // Grid sizes of the marching kernels (host and device agree on them).
 constexpr int kSweepThreads = 256;            // threads per sweep block (one column each)
 constexpr int kSweepCols = kSweepThreads - 2; // output columns per sweep block
-constexpr int kRestrictThreads = 256;         // one coarse column per thread
+constexpr int kRestrictThreads = 128;         // one coarse column per thread
 constexpr int kRestrictCols = kRestrictThreads - 1;
 constexpr int kProlongThreads = 256;
 

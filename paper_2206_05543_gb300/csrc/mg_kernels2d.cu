@@ -182,8 +182,9 @@ sweep2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 //   along x, per fine row f:  t_f = (rh(2ic) + rh(2ic+2)) + 2 rh(2ic+1)
 //   along y:                  v   = (t_{2jc} + t_{2jc+2}) + 2 t_{2jc+1}
 //   bh_c = 0.25 v   (= 4 R rh with R = (1,2,1)/4 per axis, H^2/h^2 = 4)
-// with rh evaluated as in the sweep. Block: 256 threads, thread t owns fine
-// columns 2ic, 2ic+1 with ic = 255*bx + t; threads 0..254 write.
+// with rh evaluated as in the sweep. Block: kRestrictThreads (128) threads,
+// thread t owns fine columns 2ic, 2ic+1 with ic = kRestrictCols*bx + t;
+// threads 0 .. kRestrictCols-1 write.
 // ---------------------------------------------------------------------------
 template <typename T, bool UNSCALED_B>
 __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, const T *__restrict__ b,
@@ -260,9 +261,10 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
     }
 }
 
-// at most 5 blocks per SM (measured fastest for the FP64 form against 4, 6, 8)
+// 128-thread blocks, at most 10 per SM (measured fastest for the FP64 form
+// against 256-thread blocks at 4 to 8 per SM and 128-thread blocks at 8, 12)
 template <typename T, bool UNSCALED_B>
-__global__ void __launch_bounds__(kRestrictThreads, 5)
+__global__ void __launch_bounds__(kRestrictThreads, 10)
 resrestrict2d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n,
                      int Hc, int hk)
 {
