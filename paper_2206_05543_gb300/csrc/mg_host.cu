@@ -2,14 +2,16 @@
 // C ABI declared in include/mg.h (He, Liu, Wang, arXiv:2206.05543, Sec. 4).
 //
 // A context owns the level hierarchy N, N/2, ..., 4 of one problem. The
-// cycle is recorded once into two CUDA graphs on a private stream:
+// cycle is recorded once into CUDA graphs on a private stream:
 //   pre  - the first smoothing sweep on the finest level, which also yields
 //          ||b - A u_k|| of its input (or the FP64 residual in refinement
 //          mode), the fixed-order reduction and the copy of the norm to
 //          pinned host memory;
 //   rest - the remainder of the cycle: restriction, coarse levels (the last
 //          ones inside one block, see mg_tail.cu), interpolation and the
-//          post-smoothing sweeps.
+//          post-smoothing sweeps;
+//   meas - plain cycles only: the norm of ||b - A u_k|| alone, used for the
+//          test that is predicted to end the solve (see mg_solve).
 // mg_solve replays rest + pre once per cycle and reads one double back, so
 // the stopping test costs one synchronisation per cycle and a converged u is
 // never touched again (the pre sweep writes to the ping-pong buffer).
