@@ -45,16 +45,30 @@ __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf
 // fraction bits are the top of the 52, and the 29 dropped bits decide the
 // rounding (above half: up; exactly half: up when the kept part is odd); a
 // carry out of the fraction moves into the exponent, which is the correct
-// result, including the overflow to infinity. Zeros, results that would be
-// subnormal, NaNs and infinities take the hardware conversion. Equal to
+// result, including the overflow to infinity. Zeros and binary64 subnormals
+// give the zero of their sign; results that would be binary32 subnormal,
+// NaNs and infinities take the hardware conversion. Equal to
 // __double2float_rn bit for bit; on this part the hardware conversion issues
 // on the FP64 pipe, which the FP64 residual kernels saturate.
+//
+// The hardware conversions are kept out of line: inlined, the compiler
+// executed the conversion of the rare branch on every call (one F2F per
+// point in the executed-opcode counts of the FP64 residual), and an F2F
+// occupies the FP64 pipe that these kernels saturate.
+static __device__ __noinline__ float narrow_rn_hw(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double widen_hw(float x) { return (double)x; }
+
 __device__ __forceinline__ float narrow_rn(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
     const unsigned e = (hi >> 20) & 0x7ffu;  // biased binary64 exponent
-    if (e - 897u > 253u) return __double2float_rn(x);  // binary32 exponent outside 1..254
+    if (e - 897u > 253u) {  // binary32 exponent outside 1..254
+        // zeros and binary64 subnormals (below 2^-1022, far under half the
+        // smallest binary32 subnormal) round to zero of the same sign
+        if (e == 0) return __uint_as_float(hi & 0x80000000u);
+        return narrow_rn_hw(x);
+    }
     const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned rest = lo & 0x1fffffffu;
     unsigned r = (hi & 0x80000000u) | ((e - 896u) << 23) | frac;
@@ -63,13 +77,17 @@ __device__ __forceinline__ float narrow_rn(double x)
 }
 // IEEE 754 binary32 -> binary64 conversion (exact) on the integer pipe:
 // for normal inputs the exponent is rebiased (+896) and the 23 fraction bits
-// move to the top of the 52; zeros, subnormals, infinities and NaNs take the
-// hardware conversion, which on this part issues on the FP64 pipe.
+// move to the top of the 52, zeros keep their sign; subnormals, infinities
+// and NaNs take the hardware conversion (out of line, see above), which on
+// this part issues on the FP64 pipe.
 __device__ __forceinline__ double widen(float x)
 {
     const unsigned b = __float_as_uint(x);
     const unsigned e = (b >> 23) & 0xffu;
-    if (e - 1u > 253u) return (double)x;
+    if (e - 1u > 253u) {
+        if ((b & 0x7fffffffu) == 0) return __longlong_as_double((long long)((unsigned long long)b << 32));  // +-0
+        return widen_hw(x);
+    }
     return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
                                             ((unsigned long long)(e + 896u) << 52) |
                                             ((unsigned long long)(b & 0x7fffffu) << 29)));
