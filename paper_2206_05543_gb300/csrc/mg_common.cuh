@@ -110,6 +110,11 @@ __device__ __forceinline__ OutT to_out(InT x)
 // exact, so the result equals __dmul_rn(x, 2^k) bit for bit); zeros,
 // subnormals, infinities and NaNs take the FP64 multiply. On this part the
 // FP64 pipe is the bottleneck while the integer pipe is idle.
+// scale2_ool keeps the multiply out of line for the reason given at
+// narrow_rn: inlined, it was executed on every call in the 2D prolongation
+// (0.43 DMUL per DFMA in the executed-opcode counts) and restriction (2D
+// FP64 solve 56.8 -> 55.5 ms); the 3D FP64 kernels measured slower with it
+// (209.4 -> 217.2 ms) and keep the inline form.
 template <int K>
 __device__ __forceinline__ double scale2(double x)
 {
@@ -118,6 +123,16 @@ __device__ __forceinline__ double scale2(double x)
     if (e + K >= 1 && e + K <= 0x7fe && e != 0 && e != 0x7ff)
         return __longlong_as_double(bits + ((long long)K << 52));
     return __dmul_rn(x, K >= 0 ? (double)(1ll << (K >= 0 ? K : 0)) : 1.0 / (double)(1ll << (K < 0 ? -K : 0)));
+}
+static __device__ __noinline__ double scale2_hw(double x, double s) { return __dmul_rn(x, s); }
+template <int K>
+__device__ __forceinline__ double scale2_ool(double x)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e + K >= 1 && e + K <= 0x7fe && e != 0 && e != 0x7ff)
+        return __longlong_as_double(bits + ((long long)K << 52));
+    return scale2_hw(x, K >= 0 ? (double)(1ll << (K >= 0 ? K : 0)) : 1.0 / (double)(1ll << (K < 0 ? -K : 0)));
 }
 template <int K>
 __device__ __forceinline__ float scale2(float x)
@@ -135,6 +150,13 @@ __device__ __forceinline__ double scale2(double x, int k)
     if (e + k >= 1 && e + k <= 0x7fe && e != 0 && e != 0x7ff) return __longlong_as_double(bits + ((long long)k << 52));
     return __dmul_rn(x, __longlong_as_double((long long)(1023 + k) << 52));  // 2^k, |k| < 1022
 }
+__device__ __forceinline__ double scale2_ool(double x, int k)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e + k >= 1 && e + k <= 0x7fe && e != 0 && e != 0x7ff) return __longlong_as_double(bits + ((long long)k << 52));
+    return scale2_hw(x, __longlong_as_double((long long)(1023 + k) << 52));  // 2^k, |k| < 1022
+}
 __device__ __forceinline__ float scale2(float x, int k)
 {
     const int bits = __float_as_int(x);
@@ -142,6 +164,10 @@ __device__ __forceinline__ float scale2(float x, int k)
     if (e + k >= 1 && e + k <= 0xfe && e != 0 && e != 0xff) return __int_as_float(bits + (k << 23));
     return __fmul_rn(x, __int_as_float((127 + k) << 23));  // 2^k, |k| < 126
 }
+// FP32: the fallback multiply is on the FP32 pipe, inline is fine
+template <int K>
+__device__ __forceinline__ float scale2_ool(float x) { return scale2<K>(x); }
+__device__ __forceinline__ float scale2_ool(float x, int k) { return scale2(x, k); }
 
 // Sum of `v` over the block into *dst (fixed order: warp butterfly, then the
 // warp sums in warp order by warp 0). Called by every thread of the block.

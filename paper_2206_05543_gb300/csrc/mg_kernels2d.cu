@@ -227,8 +227,8 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
         const T ua_nn = get(u, f + 2, fx), ub_nn = get(u, f + 2, fx + 1);
         const T h_nn = lt ? get(u, f + 2, fx - 1) : rt ? get(u, f + 2, fx + 2) : T(0);
         if (UNSCALED_B) {
-            ba = scale2(ba, hk);
-            bb = scale2(bb, hk);
+            ba = scale2_ool(ba, hk);
+            bb = scale2_ool(bb, hk);
         }
         const T sa = radd(radd(su[buf][2 * t], su[buf][2 * t + 2]), radd(ua_prev, ua_next));
         const T sb = radd(radd(su[buf][2 * t + 1], su[buf][2 * t + 3]), radd(ub_prev, ub_next));
@@ -247,7 +247,7 @@ __device__ __forceinline__ void resrestrict2d_tile(const T *__restrict__ u, cons
         if (f >= f0 + 2 && (f & 1) == 0 && t < kRestrictCols && ic < nc) {
             const int jc = f / 2 - 1;
             const T v = rfma(T(2), t1, radd(t2, tx));
-            bc[(size_t)jc * nc + ic] = scale2<-2>(v);  // 0.25 v
+            bc[(size_t)jc * nc + ic] = scale2_ool<-2>(v);  // 0.25 v
         }
         t2 = t1;
         t1 = tx;
@@ -293,7 +293,7 @@ __device__ __forceinline__ void prolong2d_tile(const T *__restrict__ e, T *__res
     };
     auto xpass = [&](int mm, T &odd, T &on) {
         on = ge(mm, k);
-        odd = scale2<-1>(radd(ge(mm, k - 1), on));  // 0.5 (a + b)
+        odd = scale2_ool<-1>(radd(ge(mm, k - 1), on));  // 0.5 (a + b)
     };
     T pa, pb;  // x-pass of coarse row m-1: columns 2k, 2k+1
     xpass(m0 - 1, pa, pb);
@@ -324,8 +324,8 @@ __device__ __forceinline__ void prolong2d_tile(const T *__restrict__ e, T *__res
         }
         {   // fine row 2m
             T *row = u + (size_t)(2 * m) * ld;
-            row[fa] = radd(ea, scale2<-1>(radd(pa, ca)));
-            if (inb) row[fb] = radd(eb, scale2<-1>(radd(pb, cb)));
+            row[fa] = radd(ea, scale2_ool<-1>(radd(pa, ca)));
+            if (inb) row[fb] = radd(eb, scale2_ool<-1>(radd(pb, cb)));
         }
         if (m < nc) {  // fine row 2m+1
             T *row = u + (size_t)(2 * m + 1) * ld;
