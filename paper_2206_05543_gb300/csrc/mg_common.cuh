@@ -113,7 +113,7 @@ __device__ __forceinline__ OutT to_out(InT x)
 // scale2_ool keeps the multiply out of line for the reason given at
 // narrow_rn: inlined, it was executed on every call in the 2D prolongation
 // (0.43 DMUL per DFMA in the executed-opcode counts) and restriction (2D
-// FP64 solve 56.8 -> 55.5 ms); the 3D FP64 kernels measured slower with it
+// FP64 solve 56.8 -> 55.3 ms); the 3D FP64 kernels measured slower with it
 // (209.4 -> 217.2 ms) and keep the inline form.
 template <int K>
 __device__ __forceinline__ double scale2(double x)
