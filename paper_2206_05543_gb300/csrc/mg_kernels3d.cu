@@ -196,8 +196,7 @@ constexpr int kR3F = 2 * kR3 + 1;    // fine residual patch edge (33)
 constexpr int kR3U = kR3F + 2;       // u patch edge incl. halo (35)
 constexpr int kR3Threads = kR3 * kR3;
 
-// at most 2 blocks per SM (no register cap that forces spills; measured fastest
-// for the FP64 form against 1, 3 and 4)
+// at most 4 blocks per SM (measured fastest for the FP64 form against 2, 3 and 5)
 template <typename T, bool UNSCALED_B>
 __global__ void __launch_bounds__(kR3Threads, 4)
 resrestrict3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ bc, int n, int Zc,
