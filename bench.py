@@ -9,8 +9,8 @@ residual. One step = one complete solve (about ten cycles) with b resident
 in HBM; every field (537 MB) is larger than L2, so no flush is needed.
 
 value = unknowns x V-cycles / second (DOF/s), summed over ranks; each rank
-solves its own replica of the problem (the single-problem path does not
-shard). Printed as one JSON line by rank 0.
+solves its own replica of the problem (the single-problem path is not
+decomposed across GPUs). Printed as one JSON line by rank 0.
 
 --impl reference times the FP64 CPU oracle (the checker in oracle/) on this
 machine's host cores on the same workload; each step is a bounded sample,
