@@ -35,14 +35,22 @@ D, N, TOL, SEED = 2, 8192, 1e-10, 0
 NU1 = NU2 = 1
 UNKNOWNS = (N - 1) ** D
 WORKLOAD = "poisson2d-N8192-fp64-V(1,1)-M9-tol1e-10"
-# FP64 operations per point of one finest-level sweep, in the canonical
-# formula: s (3 add), rh (fma + add), hp (1 add), E (2 add), C (1 add),
-# update (3 fma) = 12. (h^2 b is an exact power-of-two scaling, applied to
-# the exponent field with integer instructions.)
-SWEEP_DP_OPS_PER_POINT = 12
+# Algorithmic floating-point operations per point of one 2D sweep
+# u' = u + c0 r + c1 E + c2 C with r = bh - 4u + (sum of the 4 neighbours),
+# each point's residual formed once: the residual 6 (3 adds for the
+# neighbour sum, 1 multiply and 2 adds), the edge and corner sums of r 3 + 3,
+# the update 3 multiplies + 3 adds = 18 flops.
+SWEEP_FLOPS_PER_POINT = 18
+# FP64 instructions the kernel issues per point (add, mul and fma count one
+# each): s (3), rh (fma + add), the vertical pair sum reused by neighbouring
+# points (1), E (2), C (1), update (3 fma) = 12. (h^2 b is an exact
+# power-of-two scaling on the exponent field, done with integer instructions.)
+SWEEP_DP_INSTR_PER_POINT = 12
 # algorithmic bytes per point of one sweep: read u, read b, write u' (FP64)
 SWEEP_BYTES_PER_POINT = 24
-# FP64 pipe: 2 operations (add, mul or fma) per SM per clock on this part
+# nominal FP64 pipe of this part: 2 operations (add, mul or fma) per SM per
+# clock, i.e. 2 x 2 flops per SM per clock for FMAs (1.26 TFLOP/s at 152 SMs
+# and 2070 MHz: the part's quoted 1.25 TFLOP/s FP64)
 FP64_OPS_PER_SM_CLK = 2
 # algorithmic words per finest unknown of one V(1,1) cycle, summed over the
 # levels (x 4/3 in 2D): the temporally fused lower bound (pre-sweeps,
@@ -459,8 +467,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     sweep_s = k0.elapsed_time(k1) * 1e-3 / reps
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak_ops = FP64_OPS_PER_SM_CLK * sms * peaks["sm_max_mhz"] * 1e6
-    achieved_ops = SWEEP_DP_OPS_PER_POINT * UNKNOWNS / sweep_s
+    clk_hz = peaks["sm_max_mhz"] * 1e6
+    # nominal FP64 FLOP peak (FMA = 2 flops) and the measured DFMA issue rate
+    peak_flops = 2 * FP64_OPS_PER_SM_CLK * sms * clk_hz
+    rates = {k: binding.measure_fp64_rate(k) for k in binding.FP64_RATE_KINDS}
+    measured_flops = 2 * rates["dfma_reg"][0] * sms * clk_hz
+    achieved_flops = SWEEP_FLOPS_PER_POINT * UNKNOWNS / sweep_s
+    issued_ops = SWEEP_DP_INSTR_PER_POINT * UNKNOWNS / sweep_s
     sweep_gbs = SWEEP_BYTES_PER_POINT * UNKNOWNS / sweep_s / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
@@ -513,12 +526,23 @@ def run_ours(args):
                                    "vcycles": rows["2d8192-mixed2"]["cycles"],
                                    "speedup_vs_fp64": (ms / args.steps) / rows["2d8192-mixed2"]["ms"]}}
                               if rows else None),
-            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": peak_ops / 1e9,
-                         "unit": "Gop/s FP64", "frac": achieved_ops / peak_ops, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved_flops / 1e9, "peak": peak_flops / 1e9,
+                         "unit": "GFLOP/s FP64", "frac": achieved_flops / peak_flops, "traffic": traffic,
                          "kernel": "sweep2d_kernel<double> (finest level, n=8191)",
-                         "peak_basis": f"{FP64_OPS_PER_SM_CLK} FP64 ops/SM/clk x {sms} SMs x "
-                                       f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['source']})",
+                         "achieved_basis": f"{SWEEP_FLOPS_PER_POINT} algorithmic flops/point x {UNKNOWNS} points"
+                                           " / CUDA-event time per launch",
+                         "peak_basis": f"nominal: {FP64_OPS_PER_SM_CLK} FP64 FMA/SM/clk x 2 flops x {sms} SMs x "
+                                       f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, {peaks['source']})",
+                         "flop_frac_nominal": achieved_flops / peak_flops,
+                         "flop_frac_measured_dfma": achieved_flops / measured_flops,
+                         "measured_dfma_gflops": measured_flops / 1e9,
+                         "fp64_issue_occupancy": issued_ops / (FP64_OPS_PER_SM_CLK * sms * clk_hz),
+                         "issue_basis": f"{SWEEP_DP_INSTR_PER_POINT} FP64 instructions/point issued by the kernel "
+                                        f"against the nominal {FP64_OPS_PER_SM_CLK}/SM/clk",
+                         "fp64_rates_ops_per_sm_clk": {k: round(v[0], 4) for k, v in rates.items()},
+                         "fp64_rates_sm_mhz": {k: round(v[1], 1) for k, v in rates.items()},
                          "hbm_gbs": sweep_gbs, "hbm_frac": sweep_gbs / peaks["hbm_gbs"],
+                         "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
                          "ms_per_launch": sweep_s * 1e3},
             # the whole solve against the algorithmic bytes of its cycles
             "effective_bandwidth": {

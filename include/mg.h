@@ -170,7 +170,13 @@ mg_status mg_vcycles_adjoint(mg_ctx *ctx, int K, const void *b, const void *grad
  * interior layout of that level, device pointers. prec selects the element
  * type: MG_FP64 -> double, MG_FP32_IR -> float. bh is the scaled right-hand
  * side h_l^2 b_l unless b_unscaled != 0, in which case b is unscaled and the
- * kernel forms h^2 b itself (h = 1/(n+1)). stream: cudaStream_t. */
+ * kernel forms h^2 b itself (h = 1/(n+1)). stream: cudaStream_t.
+ * These are checking paths, not the solver's hot path: they allocate
+ * temporaries with cudaMalloc and synchronise the stream whenever they return
+ * a number to the host (a norm), run an FP32 operator (the FP32 kernels work
+ * on zero-ringed padded copies made for the call) or solve the coarsest grid
+ * (a copy of the exact inverse); only the FP64 operators without a norm are
+ * asynchronous and allocation-free. */
 
 /* One SPAI sweep u_out = u + W (bh - h^2 A u) (Sec. 2, Eq. (2.1)); u == NULL
  * means u = 0. If rnorm2_out (HOST) is non-NULL it receives the sum of the
@@ -206,9 +212,10 @@ mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, v
 
 /* One SPAI sweep with the squared residual norm of its input, allocating
  * nothing. The paper has no counterpart: this is a service for callers that
- * cannot call cudaMalloc -- code running while its stream is captured into a
- * CUDA graph, code confined to a framework's own memory pool, or loops that
- * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * cannot call cudaMalloc -- code confined to a framework's own memory pool
+ * (whose caching allocator owns the device heap), services with a device
+ * memory budget fixed at start-up, or loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
  * Arguments as for mg_op_sweep, except that the norm goes to DEVICE memory:
  * rnorm2_dev_out (one double, caller-owned) receives sum(rh^2) of the input
  * u, written by a kernel on `stream`; nothing is copied to the host and the
@@ -234,6 +241,17 @@ const char *mg_last_cuda_error(void);
 /* Number of kernels the library launched (directly or as graph nodes)
  * since the process started; graph replays count every node. */
 unsigned long long mg_kernel_launch_count(void);
+
+/* Measured issue rate of the FP64 pipe on the current device, for the
+ * roofline of the FP64 kernels (which are bound by that pipe, not by HBM).
+ * The paper has no counterpart. One wave of blocks runs 8 independent chains
+ * per thread of one instruction kind: 0 = DFMA with all operands in
+ * registers, 1 = DADD, 2 = DMUL, 3 = DFMA with one operand from the constant
+ * bank. *ops_per_sm_clk (HOST) receives thread-level operations per SM per
+ * SM clock (the nominal rate of this part is 2); *sm_mhz (HOST, nullable) the
+ * SM clock seen during the run (cycles / elapsed time). Allocates a few
+ * bytes and synchronises; takes tens of milliseconds. */
+mg_status mg_measure_fp64_rate(int kind, double *ops_per_sm_clk, double *sm_mhz);
 
 /* Test hook for the bounded device-side waits (the TMA-staged 3D FP32
  * kernels wait on mbarriers for their copies). The next `launches` such

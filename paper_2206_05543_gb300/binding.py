@@ -50,6 +50,7 @@ SIGNATURES = {
     "mg_last_cuda_error": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (_U, []),
     "mg_test_arm_wait_expiry": (_I, [_I]),
+    "mg_measure_fp64_rate": (_I, [_I, _DP, _DP]),
 }
 
 
@@ -128,6 +129,18 @@ def arm_wait_expiry(launches: int) -> int:
     """Test hook: the next `launches` TMA-staged kernels let their first
     bounded wait expire (the call reports MG_ETIMEOUT). 0 disarms."""
     return int(lib().mg_test_arm_wait_expiry(int(launches)))
+
+
+FP64_RATE_KINDS = {"dfma_reg": 0, "dadd": 1, "dmul": 2, "dfma_const": 3}
+
+
+def measure_fp64_rate(kind: str = "dfma_reg"):
+    """(FP64 operations issued per SM per clock, SM clock in MHz) of one
+    instruction kind on the current device (see mg_measure_fp64_rate)."""
+    rate, mhz = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().mg_measure_fp64_rate(FP64_RATE_KINDS[kind], ctypes.byref(rate), ctypes.byref(mhz)),
+           "mg_measure_fp64_rate")
+    return rate.value, mhz.value
 
 
 class SolveInfo:

@@ -522,11 +522,14 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
     return MG_OK;
 }
 
+// Order the context's stream after the caller's and clear the error word, so
+// that an expired wait of an earlier call does not fail this one.
 static mg_status enter(mg_ctx *c)
 {
     MG_CUDA(cudaSetDevice(c->dev));
     MG_CUDA(cudaEventRecord(c->ev_in, c->user));
     MG_CUDA(cudaStreamWaitEvent(c->s, c->ev_in, 0));
+    MG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
     return MG_OK;
 }
 
@@ -550,11 +553,16 @@ static double norm_from_host(mg_ctx *c)
     return std::sqrt(*c->h_norm2) * (double)c->N * (double)c->N;
 }
 
-// a kernel of an earlier replay gave up on a bounded wait (sticky)
+// a kernel of this call gave up on a bounded wait (bit 0); bit 1: its drain
+// of the copies still in flight gave up too, so a copy may have landed after
+// the block ended and the context's buffers are no longer trustworthy
 static bool timed_out(const mg_ctx *c)
 {
     int e;
     std::memcpy(&e, c->h_norm2 + 1, sizeof e);
+    if (e & 2)
+        snprintf(g_last_error, sizeof g_last_error,
+                 "a bounded device wait and the drain of its copies both expired: destroy the context");
     return e != 0;
 }
 
@@ -770,22 +778,29 @@ mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b)
     if (!ctx || !u || !b || ctx->batch) return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
-    if ((st = record(ctx, u, b)) != MG_OK) return st;
-    if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
-    if ((st = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return st;
-    return leave(ctx);
+    if ((st = record(ctx, u, b)) == MG_OK && (st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) == MG_OK)
+        st = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes);
+    // every exit after enter() orders the caller's stream after the work queued here
+    const mg_status st2 = leave(ctx);
+    return st != MG_OK ? st : st2;
 }
 
-mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
-                   double *relres_out, double *hist_out)
+// wait for the context's stream; MG_ETIMEOUT when a kernel's bounded wait expired
+static mg_status sync_ctx(mg_ctx *ctx)
 {
-    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch) return MG_EINVAL;
-    mg_status st = enter(ctx);
-    if (st != MG_OK) return st;
+    const cudaError_t e = cudaStreamSynchronize(ctx->s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return timed_out(ctx) ? MG_ETIMEOUT : MG_OK;
+}
+
+// the cycle loop of mg_solve, between enter() and leave()
+static mg_status solve_loop(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
+                            double *relres_out, double *hist_out)
+{
+    mg_status st;
     if ((st = record(ctx, u, b)) != MG_OK) return st;
     if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
-    if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-    if (timed_out(ctx)) return MG_ETIMEOUT;
+    if ((st = sync_ctx(ctx)) != MG_OK) return st;
     const double r0 = norm_from_host(ctx);
     double rk = r0, rprev = 0.0;
     int k = 0;
@@ -806,29 +821,35 @@ mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycl
             break;
         }
         const bool guess = guessing && k >= 1 && rprev > 0.0 && rk * (rk / rprev) <= tol * r0;
-        if ((st = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return st;
-        if (guess) {
-            if ((st = launch_graph(ctx, ctx->g.meas, ctx->g.meas_nodes)) != MG_OK) return st;
-        } else if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) {
-            return st;
-        }
-        if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+        mg_status ls;
+        if ((ls = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return ls;
+        ls = guess ? launch_graph(ctx, ctx->g.meas, ctx->g.meas_nodes) : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes);
+        if (ls != MG_OK) return ls;
+        if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
         ++k;
-        if (timed_out(ctx)) return MG_ETIMEOUT;
         rprev = rk;
         rk = norm_from_host(ctx);
         if (hist_out) hist_out[k] = rk;
         if (!std::isfinite(rk)) st = MG_ENAN;
         if (st == MG_OK && guess && !(rk <= tol * r0) && k < max_cycles) {
             guessing = false;
-            if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
-            if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-            if (timed_out(ctx)) return MG_ETIMEOUT;
+            if ((ls = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return ls;
+            if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
         }
     }
     if (cycles_out) *cycles_out = k;
     if (relres_out) *relres_out = r0 > 0.0 ? rk / r0 : 0.0;
-    mg_status st2 = leave(ctx);
+    return st;
+}
+
+mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
+                   double *relres_out, double *hist_out)
+{
+    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch) return MG_EINVAL;
+    mg_status st = enter(ctx);
+    if (st != MG_OK) return st;
+    st = solve_loop(ctx, b, u, tol, max_cycles, cycles_out, relres_out, hist_out);
+    const mg_status st2 = leave(ctx);
     return st != MG_OK ? st : st2;
 }
 
@@ -869,11 +890,10 @@ mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *no
                                                       (double *)nullptr, n0, ctx->partials, ctx->s);
     if (!e) e = launch_sum_partials(ctx->partials, residual_partials(ctx->d, n0), ctx->d_norm2, ctx->s);
     if (!e) e = cudaMemcpyAsync(ctx->h_norm2, ctx->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, ctx->s);
-    if (!e) e = cudaStreamSynchronize(ctx->s);
-    if (e) return cuda_fail(e);
-    if (timed_out(ctx)) return MG_ETIMEOUT;
-    *norm_out = norm_from_host(ctx);
-    return leave(ctx);
+    st = e ? cuda_fail(e) : sync_ctx(ctx);
+    if (st == MG_OK) *norm_out = norm_from_host(ctx);
+    const mg_status st2 = leave(ctx);
+    return st != MG_OK ? st : st2;
 }
 
 mg_status mg_op_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs, const void *u,

@@ -3,12 +3,12 @@
 //
 // The allocating form (mg_op_sweep with a norm output) gets its per-block
 // partial sums from cudaMalloc on every call. Some callers cannot do that:
-// code that runs while a stream is being captured into a CUDA graph (an
-// allocation there is either illegal or not part of the graph), code that
-// lives under a framework's own memory pool and may not touch the device heap
-// behind its back, and latency-bound loops where cudaMalloc/cudaFree would
-// synchronise the whole device. This entry point takes its scratch from a
-// fixed array in device memory instead and allocates nothing.
+// code that lives under a framework's own memory pool (a caching allocator
+// that owns the device heap and must not be bypassed), services that run
+// with a fixed device-memory budget decided at start-up, and latency-bound
+// loops where cudaMalloc/cudaFree would synchronise the whole device. This
+// entry point takes its scratch from a fixed array in device memory instead
+// and allocates nothing.
 //
 // The scratch is a file-scope __device__ array of kMaxPartials doubles
 // (256 KiB). Every GPU that loads the library holds it until the process
@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "../../include/mg.h"
+#include "mg_ctx.h"
 #include "mg_internal.h"
 
 namespace {
@@ -38,11 +39,15 @@ double *g_addr[kMaxDevices] = {};
 mg_status scratch_on_current_device(double **out)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MG_ECUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mg::cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return mg::cuda_fail(cudaErrorInvalidDevice);
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_addr[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sweep_partials) != cudaSuccess || !p) return MG_ECUDA;
+        e = cudaGetSymbolAddress(&p, g_sweep_partials);
+        if (e != cudaSuccess) return mg::cuda_fail(e);
+        if (!p) return mg::cuda_fail(cudaErrorInvalidSymbol);
         g_addr[dev] = (double *)p;
     }
     *out = g_addr[dev];
@@ -67,7 +72,7 @@ mg_status run(int d, int n, const double *c, const void *u, const void *bh, int 
                            : mg::launch_sweep3d<T>((const T *)u, (const T *)bh, unscaled != 0, (T *)u_out, n, c,
                                                    partials, s);
     if (e == cudaSuccess) e = mg::launch_sum_partials(partials, np, norm2_dev, s);
-    return e == cudaSuccess ? MG_OK : MG_ECUDA;
+    return e == cudaSuccess ? MG_OK : mg::cuda_fail(e);
 }
 
 }  // namespace

@@ -17,7 +17,8 @@
 //   E. waits for the planes the next step reads, and synchronises.
 // Every wait is bounded by a clock limit; on expiry the block sets an error
 // word (the host reports MG_ETIMEOUT), waits, again bounded, for its copies
-// still in flight, and returns.
+// still in flight (best effort: a drain that also expires sets a second bit),
+// and returns.
 //
 // Formula and rounding order: those of the compact 3D sweep (Sec. 3.2,
 // u' = u + c0 r + c1 (sum of the six face neighbours of r)), so results are
@@ -294,9 +295,14 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
     }
     if (producer && s_fail) {
         atomicOr(err, 1);
-        // shared memory must not be released while a copy may still land in it
-        for (int p = u_done + 1; p <= u_issued; ++p) mbar_wait(ubar(p), upar(p));
-        for (int p = b_done + 1; p <= b_issued; ++p) mbar_wait(bbar(p), bpar(p));
+        // shared memory should not be released while a copy may still land in
+        // it: wait for the copies in flight, each wait again bounded. This is
+        // best effort: if a drain wait expires too, bit 1 of the error word
+        // tells the host that a copy may land after the block has ended.
+        bool drained = true;
+        for (int p = u_done + 1; drained && p <= u_issued; ++p) drained = mbar_wait(ubar(p), upar(p));
+        for (int p = b_done + 1; drained && p <= b_issued; ++p) drained = mbar_wait(bbar(p), bpar(p));
+        if (!drained) atomicOr(err, 2);
     }
 }
 
@@ -403,9 +409,15 @@ resrestrict3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_co
             s_fail = 1;
             atomicOr(err, 1);
         }
-        // before the block ends every issued copy must have landed (bounded)
-        for (int p = max(ufirst, u_last - kRUSlots + 1); p <= u_last; ++p) mbar_wait(full_u(p), upar(p));
-        for (int p = max(bfirst, b_last - kRBSlots + 1); p <= b_last; ++p) mbar_wait(full_b(p), bpar(p));
+        // before the block ends every issued copy should have landed; each
+        // wait is bounded, and bit 1 of the error word records a drain that
+        // gave up (a copy may then land after the block has ended)
+        bool drained = true;
+        for (int p = max(ufirst, u_last - kRUSlots + 1); drained && p <= u_last; ++p)
+            drained = mbar_wait(full_u(p), upar(p));
+        for (int p = max(bfirst, b_last - kRBSlots + 1); drained && p <= b_last; ++p)
+            drained = mbar_wait(full_b(p), bpar(p));
+        if (!drained) atomicOr(err, 3);
         return;
     }
 

@@ -82,3 +82,26 @@ def test_solve_reports_timeout_then_a_new_context_converges():
         u = info.u.cpu().numpy()
     assert info.converged
     assert oracle.residual_norm(u, b) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
+
+
+def test_solve_reports_timeout_then_the_same_context_converges():
+    """The error word is cleared at the start of every call: after a solve
+    that reported MG_ETIMEOUT, re-recording the cycle (mg_set_coeffs with the
+    same weights; the armed launch lives in the recorded graph) lets the same
+    context converge, and its result passes the oracle's FP64 residual check."""
+    b = inputs.uniform(3, 32, 6)
+    w = coeffs.default(3)
+    with Solver(3, 32, w, nu1=2, nu2=2, precision="fp32_ir") as s:
+        binding.arm_wait_expiry(1)  # consumed while the refinement cycle is recorded
+        with pytest.raises(MGError) as ei:
+            s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_cycles=30)
+        assert ei.value.status == MG_ETIMEOUT
+        assert binding.arm_wait_expiry(0) == 0
+        s.set_coeffs(w)
+        info = s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_cycles=30)
+        u = info.u.cpu().numpy()
+        # a second solve on the same context and graphs
+        info2 = s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_cycles=30)
+        assert info2.converged and np.array_equal(info2.u.cpu().numpy(), u)
+    assert info.converged
+    assert oracle.residual_norm(u, b) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)

@@ -1,8 +1,9 @@
 """The sweep entry point that allocates nothing (mg_op_sweep_norm_noalloc).
 
-It serves callers that may not call cudaMalloc (graph capture in progress,
-framework-owned memory pools, latency-bound loops): its block partial sums
-live in a fixed device array inside the library. These tests check, through
+It serves callers that may not call cudaMalloc (code under a framework's own
+memory pool, services with a fixed device-memory budget, latency-bound loops
+that cannot afford cudaMalloc's device-wide synchronisation): its block
+partial sums live in a fixed device array inside the library. These tests check, through
 the C ABI, that it gives the same sweep and the same residual norm as the
 allocating entry point mg_op_sweep, on two calls in a row (the array keeps
 the previous call's contents), and that grids beyond the array are refused
@@ -51,10 +52,14 @@ def test_noalloc_matches_allocating_entry_point(d, n, dtype, unscaled):
     for call in range(2):
         out = torch.full_like(u, float("nan"))
         nrm = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         st = L.mg_op_sweep_norm_noalloc(d, n, prec, c, nc, ctypes.c_void_p(u.data_ptr()),
                                         ctypes.c_void_p(bh.data_ptr()), int(unscaled), ctypes.c_void_p(out.data_ptr()),
                                         ctypes.c_void_p(nrm.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
         assert st == binding.MG_OK, call
         torch.cuda.synchronize()
+        if call == 1:  # the first call may load the kernels; the second must take no device memory
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
         assert torch.equal(out, ref_out), call
         assert nrm.item() == pytest.approx(ref_norm, rel=1e-13), call
