@@ -113,9 +113,9 @@ def _dim_n(a: np.ndarray):
 
 def _coeffs(d: int, c) -> np.ndarray:
     c = _f64(c).ravel()
-    if not 1 <= c.size <= (3 if d == 2 else 2):
-        raise ValueError("2D takes up to 3 weights (centre, edge, corner), 3D up to 2")
-    full = np.zeros(3)
+    if not 1 <= c.size <= (3 if d == 2 else 4):
+        raise ValueError("2D takes up to 3 weights (centre, edge, corner), 3D up to 4 (centre, face, edge, corner)")
+    full = np.zeros(4)
     full[: c.size] = c
     return full
 
@@ -197,7 +197,7 @@ def cycles(b, u0, c, ncycles: int, nu1: int = 1, nu2: int = 1, gamma: int = 1) -
     u = _f64(u0).copy()
     d, n = _dim_n(b)
     cc = _coeffs(d, c)
-    st = lib().orc_cycles(d, n + 1, _p(cc), 3 if d == 2 else 2, nu1, nu2, gamma, ncycles, _p(b), _p(u))
+    st = lib().orc_cycles(d, n + 1, _p(cc), 3 if d == 2 else 4, nu1, nu2, gamma, ncycles, _p(b), _p(u))
     if st != ORC_OK:
         raise ValueError(f"orc_cycles failed with status {st}")
     return u
@@ -230,7 +230,7 @@ def solve(b, c, u0=None, tol: float = 1e-10, max_cycles: int = 100, nu1: int = 1
     hist = np.zeros(max_cycles + 1)
     cyc = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
-    st = lib().orc_solve(d, n + 1, _p(cc), 3 if d == 2 else 2, nu1, nu2, gamma, _p(b), _p(u), tol,
+    st = lib().orc_solve(d, n + 1, _p(cc), 3 if d == 2 else 4, nu1, nu2, gamma, _p(b), _p(u), tol,
                          max_cycles, _p(hist), ctypes.byref(cyc), ctypes.byref(rel))
     if st not in (ORC_OK, ORC_ENOCONV):
         raise ValueError(f"orc_solve failed with status {st}")

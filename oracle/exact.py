@@ -6,8 +6,9 @@ TEST INFRASTRUCTURE (see the package docstring).
   second difference T = tridiag(-1, 2, -1) (independent of the stencil loops
   in mg_oracle.c), as a scipy sparse matrix.
 - ``spai_matrix``: the omega-folded SPAI stencil restricted to the interior,
-  c0 I + c1 (edge/face sum) + c2 (corner sum), from the 1D neighbour-sum
-  matrix Z = tridiag(1, 0, 1).
+  c0 I + c1 (edge/face sum) + c2 (corner sum) in 2D, c0 I + c1 (faces) +
+  c2 (edges) + c3 (corners) in 3D, from the 1D neighbour-sum matrix
+  Z = tridiag(1, 0, 1).
 - ``restriction`` / ``prolongation``: full weighting R = kron of the 1D
   (1, 2, 1)/4 matrix, P = 2^d R^T (Sec. 4).
 - ``dst_solve``: the exact discrete solution of A_h u = b by the sine
@@ -51,7 +52,8 @@ def laplacian(d: int, N: int):
 
 
 def spai_matrix(d: int, N: int, c):
-    """Interior-restricted stencil c0 I + c1 (edge/face sum) [+ c2 corner sum]."""
+    """Interior-restricted stencil: 2D c0 I + c1 (edges) + c2 (corners); 3D c0 I +
+    c1 (faces) + c2 (edges) + c3 (corners)."""
     n = N - 1
     Z, I = _neighbour_sum(n), sp.identity(n, format="csr")
     W = c[0] * _kron_all([I] * d)
@@ -63,6 +65,12 @@ def spai_matrix(d: int, N: int, c):
     W = W + c[1] * reduce(lambda a, b: a + b, faces)
     if d == 2 and len(c) > 2 and c[2] != 0.0:
         W = W + c[2] * sp.kron(Z, Z, format="csr")
+    if d == 3 and len(c) > 2:
+        # 12 edge offsets: Z on two of the three axes; 8 corners: Z on all three
+        edges = [_kron_all([Z if k != skip else I for k in range(3)]) for skip in range(3)]
+        W = W + c[2] * reduce(lambda a, b: a + b, edges)
+        if len(c) > 3:
+            W = W + c[3] * _kron_all([Z, Z, Z])
     return W
 
 

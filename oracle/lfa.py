@@ -122,3 +122,155 @@ def two_grid_factor(d: int, wfold, nu: int, n: int = 256) -> float:
     K = np.eye(2 ** d)[None] - r[:, :, None] * (r * a_h)[:, None, :] / a_H[:, None, None]
     T = s[:, :, None] * K
     return float(np.max(np.abs(np.linalg.eigvals(T))))
+
+
+# ---------------------------------------------------------------------------
+# numerical min-max over a symmetric stencil family (Sec. 3.1, Sec. 3.2)
+# ---------------------------------------------------------------------------
+# A symmetric stencil family is given by one weight per class of offsets: the
+# offsets with j non-zero components (centre, edges/faces, corners in 2D;
+# centre, faces, edges, corners in 3D). The symbol of class j, in the cosine
+# variables, is 2^j e_j(x) with e_j the j-th elementary symmetric polynomial
+# (Sec. 3.1 for Upsilon, Sec. 3.2 for T and its 19/27-point extensions).
+# The paper minimises over a family the smoothing factor
+#     mu(w) = min_omega max_{X^H} |1 - omega A~ M~_w| = (l1 - l0) / (l1 + l0)
+# (Eqs. (2.6), (2.7)); since omega absorbs a common factor of the weights,
+# the centre weight is fixed to 1 and the others are searched.
+
+#: family name -> (dimension, number of weight classes)
+FAMILIES = {
+    "jacobi2": (2, 1),      # M_J (Sec. 3.1)
+    "five": (2, 2),         # 5-point stencils (Sec. 3.1, M_5)
+    "nine": (2, 3),         # Upsilon(alpha, beta, gamma) (Sec. 3.1, Theorem 3.1)
+    "jacobi3": (3, 1),      # M_J (Sec. 3.2)
+    "seven": (3, 2),        # T(alpha, beta) (Sec. 3.2, Theorem 3.2)
+    "nineteen": (3, 3),     # + the 12 edge offsets (Sec. 3.2, closing remark)
+    "twentyseven": (3, 4),  # + the 8 corner offsets (Sec. 3.2, closing remark)
+}
+
+
+def _elementary(x: np.ndarray, j: int) -> np.ndarray:
+    """e_j of the last axis of x (j = 0..d)."""
+    d = x.shape[-1]
+    out = np.zeros(x.shape[:-1])
+    for sub in itertools.combinations(range(d), j):
+        out = out + (np.prod(x[..., list(sub)], axis=-1) if sub else 1.0)
+    return out
+
+
+def class_symbol(d: int, w, x) -> np.ndarray:
+    """M~ = sum_j w_j 2^j e_j(x) for class weights w (h = 1)."""
+    x = np.asarray(x, dtype=np.float64)
+    return sum(wj * 2.0 ** j * _elementary(x, j) for j, wj in enumerate(w))
+
+
+def class_product(d: int, w, x) -> np.ndarray:
+    """A~ M~ for class weights w."""
+    x = np.asarray(x, dtype=np.float64)
+    return 2.0 * (d - x.sum(axis=-1)) * class_symbol(d, w, x)
+
+
+def _class_product_grad(d: int, w, x: np.ndarray) -> np.ndarray:
+    """Gradient of A~ M~ in x (product rule; d e_j / d x_i = e_{j-1} of the others)."""
+    a = 2.0 * (d - x.sum())
+    m = class_symbol(d, w, x)
+    g = np.empty(d)
+    for i in range(d):
+        rest = np.delete(x, i)
+        dm = sum(wj * 2.0 ** j * (_elementary(rest, j - 1) if j >= 1 else 0.0) for j, wj in enumerate(w))
+        g[i] = -2.0 * m + a * dm
+    return g
+
+
+_GRIDS = {}
+
+
+def _sym_grid(d: int):
+    """Uniform grid of the box x_1 in [-1, 0], x_2.. in [-1, 1]: for a symbol
+    symmetric under permutations of the axes this box holds every value the
+    symbol takes on X^H (each point of X^H has some coordinate <= 0)."""
+    if d not in _GRIDS:
+        k1, k = (201, 401) if d == 2 else (25, 49)
+        axes = [np.linspace(-1.0, 0.0, k1)] + [np.linspace(-1.0, 1.0, k)] * (d - 1)
+        mesh = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1)
+        _GRIDS[d] = (mesh, [(-1.0, 0.0)] + [(-1.0, 1.0)] * (d - 1))
+    return _GRIDS[d]
+
+
+def _grid_local_extrema(vals: np.ndarray, sign: float) -> np.ndarray:
+    """Indices (flat) of grid points no smaller (sign=+1) / no larger than
+    every axis neighbour."""
+    v = sign * vals
+    keep = np.ones(v.shape, dtype=bool)
+    for ax in range(v.ndim):
+        for sh in (1, -1):
+            nb = np.roll(v, sh, axis=ax)
+            edge = [slice(None)] * v.ndim
+            edge[ax] = 0 if sh == 1 else -1
+            nb[tuple(edge)] = -np.inf
+            keep &= v >= nb
+    return np.flatnonzero(keep)
+
+
+def class_extremes(d: int, w):
+    """(l0, l1) = (min, max) of A~ M~ over X^H for symmetric class weights w:
+    grid local extrema of the box of _sym_grid, each polished by L-BFGS-B with
+    the analytic gradient inside the box."""
+    mesh, bounds = _sym_grid(d)
+    vals = class_product(d, w, mesh)
+    flat = mesh.reshape(-1, d)
+    out = []
+    for sign in (-1.0, 1.0):
+        idx = _grid_local_extrema(vals, sign)
+        idx = idx[np.argsort(-sign * vals.ravel()[idx])][:12]
+        best = sign * vals.ravel()[idx[0]]
+        for i in idx:
+            res = minimize(lambda x: -sign * float(class_product(d, w, x)), flat[i],
+                           jac=lambda x: -sign * _class_product_grad(d, w, x), bounds=bounds,
+                           method="L-BFGS-B", options={"ftol": 1e-16, "gtol": 1e-14, "maxiter": 200})
+            best = max(best, -res.fun)
+        out.append(sign * best)
+    return out[0], out[1]
+
+
+def class_mu(d: int, w) -> float:
+    """mu(w) = (l1 - l0)/(l1 + l0) (Eq. (2.6)); 1 + |l0| when A~ M~ is not
+    positive on X^H (no omega makes the sweep smooth)."""
+    l0, l1 = class_extremes(d, w)
+    if l0 <= 0.0:
+        return 1.0 + abs(l0)
+    return (l1 - l0) / (l1 + l0)
+
+
+def optimise_family(name: str, starts=None, seed: int = 0):
+    """Numerical min-max over a family: minimise mu over the class weights
+    (centre weight 1) by Nelder-Mead from several starts, then polish from the
+    best point. Returns (w, mu, omega) with w the unfolded class weights
+    (w_0 = 1) and omega = 2/(l0 + l1) (Eq. (2.7)), so that the folded weights
+    of the sweep are omega * w."""
+    from scipy.optimize import minimize as _min
+
+    d, nclass = FAMILIES[name]
+    if nclass == 1:
+        w = (1.0,)
+        l0, l1 = class_extremes(d, w)
+        return w, (l1 - l0) / (l1 + l0), 2.0 / (l0 + l1)
+    rng = np.random.default_rng(seed)
+    if starts is None:
+        starts = [np.zeros(nclass - 1)] + [rng.uniform(0.0, 0.3, nclass - 1) for _ in range(3)]
+    f = lambda p: class_mu(d, (1.0, *p))  # noqa: E731
+    best = None
+    for p0 in starts:
+        r = _min(f, np.asarray(p0, dtype=np.float64), method="Nelder-Mead",
+                 options={"xatol": 1e-7, "fatol": 1e-12, "maxiter": 4000, "maxfev": 8000})
+        if best is None or r.fun < best.fun:
+            best = r
+    for _ in range(3):  # restart from the best point with a fresh simplex
+        r = _min(f, best.x, method="Nelder-Mead",
+                 options={"xatol": 1e-11, "fatol": 1e-15, "maxiter": 4000, "maxfev": 8000,
+                          "initial_simplex": np.vstack([best.x] + [best.x + 1e-4 * e for e in np.eye(nclass - 1)])})
+        if r.fun <= best.fun:
+            best = r
+    w = (1.0, *best.x)
+    l0, l1 = class_extremes(d, w)
+    return w, (l1 - l0) / (l1 + l0), 2.0 / (l0 + l1)

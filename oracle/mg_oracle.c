@@ -144,12 +144,40 @@ int orc_set_threads(int threads)
 /* SPAI smoothing sweep                                               */
 /* ------------------------------------------------------------------ */
 
+/* In-plane sums of rh around (x, y) in plane z, for the 27-point stencil:
+ *   hp = rh_W + rh_E                    (the pair along x)
+ *   p1 = hp + (rh_S + rh_N)             (the 4 in-plane edge neighbours)
+ *   p2 = hp(y - 1) + hp(y + 1)          (the 4 in-plane corner neighbours)
+ * Outside the grid every rh is zero, so are these sums. */
+static double hp3(const double *rh, int n, int periodic, int x, int y, int z)
+{
+    return at3(rh, n, periodic, x - 1, y, z) + at3(rh, n, periodic, x + 1, y, z);
+}
+
+static double p1_3(const double *rh, int n, int periodic, int x, int y, int z)
+{
+    return hp3(rh, n, periodic, x, y, z) + (at3(rh, n, periodic, x, y - 1, z) + at3(rh, n, periodic, x, y + 1, z));
+}
+
+static double p2_3(const double *rh, int n, int periodic, int x, int y, int z)
+{
+    return hp3(rh, n, periodic, x, y - 1, z) + hp3(rh, n, periodic, x, y + 1, z);
+}
+
 /* Apply the omega-folded SPAI stencil to rh and add it to u [Eq. (2.1)]:
  *   2D: E = (rh_W + rh_E) + (rh_S + rh_N)
  *       C = (rh_SW + rh_SE) + (rh_NW + rh_NE)
  *       out = fma(c2, C, fma(c1, E, fma(c0, rh, u)))
- *   3D: E = ((rh_W + rh_E) + (rh_S + rh_N)) + (rh_D + rh_U)
+ *   3D, 7-point M (the family T of Sec. 3.2; c2 = c3 = 0):
+ *       E = ((rh_W + rh_E) + (rh_S + rh_N)) + (rh_D + rh_U)
  *       out = fma(c1, E, fma(c0, rh, u))
+ *   3D, 27-point M (Sec. 3.2, closing remark; weights c0 centre, c1 the 6
+ *   faces, c2 the 12 edges, c3 the 8 corners; used when c2 or c3 != 0):
+ *       F = p1(z) + (rh_D + rh_U)                 (faces)
+ *       E = p2(z) + (p1(z - 1) + p1(z + 1))       (edges)
+ *       C = p2(z - 1) + p2(z + 1)                 (corners)
+ *       out = fma(c3, C, fma(c2, E, fma(c1, F, fma(c0, rh, u))))
+ *   (p1, p2 as above; for c2 = c3 = 0 the face sum F is the 7-point E.)
  * rh is zero outside the interior, i.e. M_h is the stencil matrix restricted
  * to the interior points. */
 static void apply_spai(int d, int n, int periodic, const double *c,
@@ -166,7 +194,7 @@ static void apply_spai(int d, int n, int periodic, const double *c,
                            (at2(rh, n, periodic, x - 1, y + 1) + at2(rh, n, periodic, x + 1, y + 1));
                 out[p] = fma(c[2], C, fma(c[1], E, fma(c[0], rh[p], u[p])));
             }
-    } else {
+    } else if (c[2] == 0.0 && c[3] == 0.0) {
 #pragma omp parallel for schedule(static)
         for (int z = 0; z < n; ++z)
             for (int y = 0; y < n; ++y)
@@ -177,12 +205,26 @@ static void apply_spai(int d, int n, int periodic, const double *c,
                                (at3(rh, n, periodic, x, y, z - 1) + at3(rh, n, periodic, x, y, z + 1));
                     out[p] = fma(c[1], E, fma(c[0], rh[p], u[p]));
                 }
+    } else {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    long p = ((long)z * n + y) * n + x;
+                    double F = p1_3(rh, n, periodic, x, y, z) +
+                               (at3(rh, n, periodic, x, y, z - 1) + at3(rh, n, periodic, x, y, z + 1));
+                    double E = p2_3(rh, n, periodic, x, y, z) +
+                               (p1_3(rh, n, periodic, x, y, z - 1) + p1_3(rh, n, periodic, x, y, z + 1));
+                    double C = p2_3(rh, n, periodic, x, y, z - 1) + p2_3(rh, n, periodic, x, y, z + 1);
+                    out[p] = fma(c[3], C, fma(c[2], E, fma(c[1], F, fma(c[0], rh[p], u[p]))));
+                }
     }
 }
 
 /* One smoothing sweep u_out = u + omega M_h (b_h - A_h u), out of place.
  * c holds the omega-folded weights: 2D (centre, edge, corner), 3D (centre,
- * face). rh_work must hold n^d doubles. */
+ * face, edge, corner); 4 entries are read in 3D, 3 in 2D. rh_work must hold
+ * n^d doubles. */
 void orc_sweep(int d, int n, int periodic, const double *c, const double *u,
                const double *bh, double *u_out, double *rh_work)
 {
@@ -381,7 +423,7 @@ void orc_coarse_solve(int d, const double *bh, double *x)
 typedef struct {
     int d, N, L;      /* dimension, finest N, number of levels (N = 4 -> 1) */
     int nu1, nu2, gamma;
-    double c[3];
+    double c[4];
     double **u, **bh, **rh, **tmp; /* per level, index 0 = finest */
 } orc_mg;
 
@@ -427,7 +469,7 @@ static int mg_init(orc_mg *g, int d, int N, const double *c, int ncoef, int nu1,
 {
     memset(g, 0, sizeof *g);
     if ((d != 2 && d != 3) || !valid_N(N) || nu1 < 0 || nu2 < 0 || gamma < 1 ||
-        ncoef < 1 || ncoef > (d == 2 ? 3 : 2))
+        ncoef < 1 || ncoef > (d == 2 ? 3 : 4))
         return ORC_EINVAL;
     g->d = d;
     g->N = N;
@@ -435,7 +477,7 @@ static int mg_init(orc_mg *g, int d, int N, const double *c, int ncoef, int nu1,
     g->nu1 = nu1;
     g->nu2 = nu2;
     g->gamma = gamma;
-    for (int j = 0; j < 3; ++j) g->c[j] = j < ncoef ? c[j] : 0.0;
+    for (int j = 0; j < 4; ++j) g->c[j] = j < ncoef ? c[j] : 0.0;
     g->u = calloc(g->L, sizeof(double *));
     g->bh = calloc(g->L, sizeof(double *));
     g->rh = calloc(g->L, sizeof(double *));
@@ -520,7 +562,7 @@ static void load_rhs(orc_mg *g, const double *b)
 double orc_residual_norm(int d, int N, const double *u, const double *b)
 {
     orc_mg g;
-    double zero[3] = {0, 0, 0};
+    double zero[4] = {0, 0, 0, 0};
     if (mg_init(&g, d, N, zero, 1, 0, 0, 1) != ORC_OK) return -1.0;
     load_rhs(&g, b);
     memcpy(g.u[0], u, npoints(d, N - 1) * sizeof(double));

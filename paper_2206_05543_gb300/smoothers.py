@@ -4,9 +4,12 @@ A smoother u <- u + omega M_h (b_h - A_h u) (Eq. (2.1)) with M_h a symmetric
 stencil proportional to h^2 is passed to the library as h-free,
 omega-folded weights c_j = omega * (stencil weight of class j) / h^2:
 
-    2D: (centre, edge, corner)      3D: (centre, face)
+    2D: (centre, edge, corner)      3D: (centre, face[, edge, corner])
 
-Each literal below is the double nearest to the exact value given beside it.
+Each literal below is the double nearest to the exact value given beside it,
+except M19 and M27, which are the values a numerical min-max of the
+smoothing factor over their families gives (Sec. 3.2 names such stencils
+but prints no weights).
 """
 from __future__ import annotations
 
@@ -29,10 +32,20 @@ M7 = (16 / 73, 2 / 73)
 c = (16/73, 2/73); smoothing factor 25/73 ~ 0.343."""
 JACOBI_3D = (1 / 7,)
 """Weighted Jacobi h^2/6 with omega = 6/7: c0 = 1/7; mu = 5/7."""
+M19 = (0.20341192950260992, 0.038265610500452976, 0.007552423125074582)
+"""Symmetric 19-point stencil (centre, 6 faces, 12 edges) minimising the
+smoothing factor over its family (Sec. 3.2, closing remark): unfolded class
+weights (1, 0.188118811881, 0.0371287128712) with omega = 0.2034119295;
+mu = 0.22663 (M7: 0.343)."""
+M27 = (0.1965670905902807, 0.03973164596853401, 0.01150126593697686, 0.003659493706759684)
+"""Symmetric 27-point stencil (centre, 6 faces, 12 edges, 8 corners)
+minimising the smoothing factor over its family (Sec. 3.2, closing remark):
+unfolded class weights (1, 0.2021276596, 0.0585106383, 0.0186170213) with
+omega = 0.1965670906; mu = 0.19700 (M7: 0.343)."""
 
 BY_NAME = {
     (2, "m9"): M9, (2, "m5"): M5, (2, "vanka"): VANKA, (2, "tw5"): TANG_WAN, (2, "jacobi"): JACOBI_2D,
-    (3, "m7"): M7, (3, "jacobi"): JACOBI_3D,
+    (3, "m7"): M7, (3, "jacobi"): JACOBI_3D, (3, "m19"): M19, (3, "m27"): M27,
 }
 
 
