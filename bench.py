@@ -301,6 +301,19 @@ def make_workload(name, torch):
             return info.cycles
         label = "M5" if name.endswith("-m5") else "weighted Jacobi"
         return step, (n_ - 1) ** d_, f"{d_}D N={n_} fp64 V({nu},{nu}) {label} to 1e-10", s.close
+    if name in ("3d512-m27", "3d512-m27-v22"):
+        # the LFA-optimal symmetric 27-point smoother (min-max over its
+        # family, Sec. 3.2's wider stencils), FP64, V(1,1) and V(2,2)
+        nu = 2 if name.endswith("-v22") else 1
+        b = torch.from_numpy(inputs.uniform(3, 512, SEED)).cuda()
+        u = torch.zeros_like(b)
+        s = Solver(3, 512, smoothers.M27, nu1=nu, nu2=nu, precision="fp64")
+
+        def step():
+            u.zero_()
+            info = s.solve(b, u, tol=TOL, max_cycles=100)
+            return info.cycles
+        return step, 511 ** 3, f"3D N=512 fp64 V({nu},{nu}) 27-point LFA-optimal M to 1e-10", s.close
     if name == "adjoint128":
         b = torch.from_numpy(inputs.gaussian(3, 128, 0)).to("cuda", torch.float32)
         g = torch.from_numpy(np.random.default_rng(1).standard_normal(b.shape)).to("cuda", torch.float32)
@@ -314,7 +327,7 @@ def make_workload(name, torch):
 
 
 ROWS = ["2d64", "2d8192-mixed", "2d8192-mixed2", "3d512-fp64", "3d512-mixed", "3d512-mixed2", "batch256", "batch256-2",
-        "adjoint128", "2d8192-m5", "2d8192-jacobi", "3d512-jacobi"]
+        "adjoint128", "2d8192-m5", "2d8192-jacobi", "3d512-jacobi", "3d512-m27", "3d512-m27-v22"]
 
 
 def time_workload(name, torch, warmup=2, steps=3, keep=None):
@@ -505,7 +518,9 @@ def run_ours(args):
         rows["time_ratio_vs_optimal_smoother"] = {
             "2d_m5_vs_m9": rows["2d8192-m5"]["ms"] / (ms / args.steps),
             "2d_jacobi_vs_m9": rows["2d8192-jacobi"]["ms"] / (ms / args.steps),
-            "3d_jacobi_vs_m7": rows["3d512-jacobi"]["ms"] / rows["3d512-fp64"]["ms"]}
+            "3d_jacobi_vs_m7": rows["3d512-jacobi"]["ms"] / rows["3d512-fp64"]["ms"],
+            "3d_m27_v11_vs_m7_v22": rows["3d512-m27"]["ms"] / rows["3d512-fp64"]["ms"],
+            "3d_m27_v22_vs_m7_v22": rows["3d512-m27-v22"]["ms"] / rows["3d512-fp64"]["ms"]}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,

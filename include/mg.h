@@ -11,12 +11,17 @@
  * Smoother (Sec. 2, Eq. (2.1)): u <- u + omega M_h (b_h - A_h u) with M_h a
  * symmetric stencil proportional to h^2 (Sec. 3). The library takes the
  * omega-folded, h-free weights
- *     2D: c = (c0, c1, c2) = omega * (centre, edge, corner) / h^2
- *     3D: c = (c0, c1)     = omega * (centre, face) / h^2
+ *     2D: c = (c0, c1, c2)     = omega * (centre, edge, corner) / h^2
+ *     3D: c = (c0, c1, c2, c3) = omega * (centre, face, edge, corner) / h^2
  * e.g. M9 = Upsilon(44,10,3)/24 with omega = (309 - 12 sqrt 10)/1720
  * (Theorem 3.1) gives c = omega*(44, 10, 3)/24; M7 = T(8/5, 2/5) with
  * omega = 20/73 (Theorem 3.2) gives c = (16/73, 2/73). Fewer weights than
- * the maximum leave the rest zero (Jacobi: one weight, M5: two).
+ * the maximum leave the rest zero (Jacobi: one weight, M5 and M7: two). A 3D
+ * M with a non-zero edge or corner weight is the symmetric 27-point stencil
+ * (19-point without corners) that Sec. 3.2 mentions as a wider SPAI
+ * smoother; it runs on the FP64 and plain FP32 cycles (MG_FP64, MG_FP32) and
+ * the FP64 single operators; MG_FP32_IR contexts and the adjoint take the
+ * 7-point M only (MG_EINVAL otherwise).
  *
  * Cycle (Sec. 4): re-discretised coarse operators (H = 2h), full-weighting
  * restriction, bilinear/trilinear interpolation, nu1 pre- and nu2
@@ -67,7 +72,7 @@ typedef enum {
 
 /* Create a solver for dimension d (2 or 3) and grid N (power of two, >= 4).
  * spai_coeffs: HOST array of ncoeffs omega-folded weights (see above;
- * 1..3 in 2D, 1..2 in 3D). nu1, nu2 >= 0 sweeps, nu1 + nu2 >= 1.
+ * 1..3 in 2D, 1..4 in 3D). nu1, nu2 >= 0 sweeps, nu1 + nu2 >= 1.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Allocates the level hierarchy on the current device. MG_EINVAL, MG_ENOMEM
  * or MG_ECUDA on failure (*out is then NULL). */
@@ -156,7 +161,8 @@ mg_status mg_solve_batched(mg_ctx *ctx, const void *const *b, void *const *u, do
  * (double for MG_FP64, float for MG_FP32; MG_FP32_IR is rejected).
  * Outputs: grad_b_out = dL/db (device, same type) and grad_coeffs_out =
  * dL/dc (HOST, ncoeffs doubles, summed over every sweep of every level and
- * cycle, accumulated in FP64). Requires a V cycle (gamma = 1), nu1 >= 1 and N >= 8.
+ * cycle, accumulated in FP64). Requires a V cycle (gamma = 1), nu1 >= 1, N >= 8
+ * and, in 3D, a context made with at most 2 weights (the 7-point M).
  * The forward is replayed once keeping the input of every sweep of every
  * level visit and each visit's right-hand side (device workspace owned by
  * the context, allocated on the first call for a given K). Synchronises. */

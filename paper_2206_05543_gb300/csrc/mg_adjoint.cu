@@ -437,7 +437,8 @@ extern "C" mg_status mg_vcycles_adjoint(mg_ctx *ctx, int K, const void *b, const
                                         double *grad_coeffs_out)
 {
     if (!ctx || K < 1 || !b || !grad_uK || !grad_b_out || !grad_coeffs_out || ctx->batch ||
-        ctx->gamma != 1 || ctx->nu1 < 1 || ctx->prec == MG_FP32_IR || ctx->L < 2)
+        ctx->gamma != 1 || ctx->nu1 < 1 || ctx->prec == MG_FP32_IR || ctx->L < 2 ||
+        (ctx->d == 3 && ctx->ncoef > 2))  // the adjoint covers the 7-point M in 3D
         return MG_EINVAL;
     if (cudaSetDevice(ctx->dev) != cudaSuccess) return cuda_fail(cudaGetLastError());
     if (cudaEventRecord(ctx->ev_in, ctx->user) != cudaSuccess || cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0) != cudaSuccess)

@@ -33,7 +33,7 @@ struct mg_ctx {
     int d = 2, N = 0, L = 0, nu1 = 1, nu2 = 1, gamma = 1, lt = 0, dev = 0;
     int inner = 1;  // FP32 cycles per refinement iteration (MG_FP32_IR)
     mg_prec prec = MG_FP64;
-    double c[3] = {0, 0, 0};
+    double c[4] = {0, 0, 0, 0};  // omega-folded weights (3D: centre, face, edge, corner)
     int ncoef = 0;
     cudaStream_t user = nullptr, s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;

@@ -186,6 +186,15 @@ static int residual_partials(int d, int n)
 
 static size_t npoints(int d, int n) { return d == 2 ? (size_t)n * n : (size_t)n * n * n; }
 
+// 3D weights with a non-zero edge or corner weight: the 27-point M
+static bool wide_weights(int d, const double *w, int nw)
+{
+    if (d != 3) return false;
+    for (int j = 2; j < nw; ++j)
+        if (w[j] != 0.0) return true;
+    return false;
+}
+
 static bool valid_N(int N)
 {
     if (N < 4 || N > (1 << 20)) return false;
@@ -332,7 +341,7 @@ struct Recorder {
         memset(&a, 0, sizeof a);
         a.d = c->d;
         a.lu = c->lu;
-        for (int j = 0; j < 3; ++j) a.c[j] = c->c[j];
+        for (int j = 0; j < 4; ++j) a.c[j] = c->c[j];
         for (int k = c->lt; k < c->L; ++k) {
             // the tail always reads a scaled rhs buffer
             a.lv[k - c->lt] = tail_level(A(k), B(k), (void *)c->BH[k], c->RH[k], c->n[k]);
@@ -571,12 +580,15 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
 {
     if (!out) return MG_EINVAL;
     *out = nullptr;
-    if ((d != 2 && d != 3) || !valid_N(N) || !coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 2) ||
+    if ((d != 2 && d != 3) || !valid_N(N) || !coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 4) ||
         nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || gamma < 1 || gamma > 2 ||
         (prec != MG_FP64 && prec != MG_FP32_IR && prec != MG_FP32))
         return MG_EINVAL;
     for (int j = 0; j < ncoeffs; ++j)
         if (!std::isfinite(coeffs[j])) return MG_EINVAL;
+    // the 27-point M (edge or corner weights) runs on the compact-layout
+    // kernels: FP64 and plain FP32 cycles, not the padded FP32 refinement levels
+    if (wide_weights(d, coeffs, ncoeffs) && prec == MG_FP32_IR) return MG_EINVAL;
     if (d == 3 && (size_t)(N - 1) * (N - 1) * (N - 1) > (size_t)1 << 34) return MG_EINVAL;
     mg_ctx *c = new (std::nothrow) mg_ctx;
     if (!c) return MG_ENOMEM;
@@ -855,12 +867,13 @@ mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycl
 
 mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs)
 {
-    if (!ctx || !spai_coeffs || ncoeffs < 1 || ncoeffs > (ctx->d == 2 ? 3 : 2)) return MG_EINVAL;
+    if (!ctx || !spai_coeffs || ncoeffs < 1 || ncoeffs > (ctx->d == 2 ? 3 : 4)) return MG_EINVAL;
     for (int j = 0; j < ncoeffs; ++j)
         if (!std::isfinite(spai_coeffs[j])) return MG_EINVAL;
+    if (wide_weights(ctx->d, spai_coeffs, ncoeffs) && (ctx->prec == MG_FP32_IR || ctx->batch)) return MG_EINVAL;
     if (cudaSetDevice(ctx->dev) != cudaSuccess || cudaStreamSynchronize(ctx->s) != cudaSuccess)
         return cuda_fail(cudaGetLastError());
-    for (int j = 0; j < 3; ++j) ctx->c[j] = j < ncoeffs ? spai_coeffs[j] : 0.0;
+    for (int j = 0; j < 4; ++j) ctx->c[j] = j < ncoeffs ? spai_coeffs[j] : 0.0;
     ctx->ncoef = ncoeffs;
     free_graphs(ctx);
     return MG_OK;
@@ -899,9 +912,11 @@ mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *no
 mg_status mg_op_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs, const void *u,
                       const void *bh, int b_unscaled, void *u_out, double *rnorm2_out, void *stream)
 {
-    if (!valid_level(d, n) || !spai_coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 2) || !bh || !u_out)
+    if (!valid_level(d, n) || !spai_coeffs || ncoeffs < 1 || ncoeffs > (d == 2 ? 3 : 4) || !bh || !u_out)
         return MG_EINVAL;
-    double c[3] = {0, 0, 0};
+    // the FP32 operators run the padded-layout refinement kernels (7-point M in 3D)
+    if (wide_weights(d, spai_coeffs, ncoeffs) && prec != MG_FP64) return MG_EINVAL;
+    double c[4] = {0, 0, 0, 0};
     for (int j = 0; j < ncoeffs; ++j) c[j] = spai_coeffs[j];
     if (prec == MG_FP64)
         return op_sweep_t<double>(d, n, c, u, bh, b_unscaled, u_out, rnorm2_out, (cudaStream_t)stream);

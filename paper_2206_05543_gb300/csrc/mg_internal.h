@@ -60,7 +60,9 @@ constexpr int sweep3d_blocks_per_sm(int elem_bytes) { return elem_bytes == 8 ? 2
 S3Plan sweep3d_plan(int n, int elem_bytes);
 Grid3 residual3d_grid(int n);
 
-// 3D level operators (same conventions as the 2D ones; c = (c0, c1)).
+// 3D level operators (same conventions as the 2D ones; c = (c0, c1, c2, c3):
+// centre, face, edge, corner weights; the sweep takes the 27-point form when
+// c2 or c3 is non-zero).
 template <typename T>
 cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
                            double *partials, cudaStream_t s);
@@ -155,7 +157,7 @@ struct TailOp {
 struct TailArgs {
     TailLevel lv[kMaxTailLevels];
     TailOp ops[kMaxTailOps];
-    double c[3];
+    double c[4];  // 2D: centre, edge, corner; 3D: centre, face, edge, corner
     const double *lu;  // exact inverse of the coarsest operator (device, coarse_inverse)
     int d, nops;
 };

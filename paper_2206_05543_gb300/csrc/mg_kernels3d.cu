@@ -181,6 +181,186 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// 27-point SPAI sweep: a symmetric M with one weight per class of offsets,
+// c0 the centre, c1 the 6 faces, c2 the 12 edges, c3 the 8 corners (the
+// wider 3D stencils of Sec. 3.2's closing remark). Canonical evaluation at
+// interior point p (rh as in the 7-point sweep, zero outside the interior):
+//   per plane:  hp = rh_W + rh_E,  P1 = hp + (rh_S + rh_N),
+//               P2 = hp(y - 1) + hp(y + 1)
+//   F  = P1(z) + (rh(z - 1) + rh(z + 1))          (faces)
+//   E  = P2(z) + (P1(z - 1) + P1(z + 1))          (edges)
+//   C  = P2(z - 1) + P2(z + 1)                    (corners)
+//   u' = fma(c3, C, fma(c2, E, fma(c1, F, fma(c0, rh_p, u_p))))
+// With c2 = c3 = 0 the face sum F is the 7-point sweep's E; the library uses
+// this kernel only when c2 or c3 is non-zero.
+// Thread t owns column i = t % 32 of the 32x32 residual tile and the four
+// consecutive rows 4 (t / 32) .. + 3: its x-pair sums hp of rows j - 1 ..
+// j + 4 serve P1 and P2 of all four rows. Per output point (rh, P1, P2) of
+// planes z - 1 and z stay in registers, plane z + 1's are formed at the step;
+// the residual plane goes through shared memory once (double-buffered, one
+// barrier per plane), the u plane as in the 7-point sweep.
+// ---------------------------------------------------------------------------
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+__device__ __forceinline__ void sweep27_segment(T (&su)[2][kS3U * kS3U], T (&sr)[2][kS3 * kS3],
+                                                const T *__restrict__ u, const T *__restrict__ b,
+                                                T *__restrict__ out, int n, int tx, int ty, int z0, int z1,
+                                                T c0, T c1, T c2, T c3, int hk, double &acc)
+{
+    const int t = threadIdx.x;
+    const int i = t % kS3, j0 = kS3Pts * (t / kS3);
+    const int ex0 = tx * kS3Out - 1, ey0 = ty * kS3Out - 1;
+    const int px = ex0 + i;
+    const size_t plane = (size_t)n * n;
+    const T m6 = in_reg(T(-6));
+    c0 = in_reg(c0);
+    c1 = in_reg(c1);
+    c2 = in_reg(c2);
+    c3 = in_reg(c3);
+    const bool col_in = px >= 0 && px < n;
+    const bool col_own = col_in && i >= 1 && i <= kS3Out;
+    // neighbour columns in the residual tile (clamped: only owned columns use them)
+    const int il = i > 0 ? i - 1 : 0, ir = i < kS3 - 1 ? i + 1 : kS3 - 1;
+
+    bool inside[kS3Pts], own[kS3Pts];
+    T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], b_next[kS3Pts];
+    T r_m[kS3Pts], r_c[kS3Pts], p1_m[kS3Pts], p1_c[kS3Pts], p2_m[kS3Pts], p2_c[kS3Pts];
+#pragma unroll
+    for (int k = 0; k < kS3Pts; ++k) {
+        const int py = ey0 + j0 + k;
+        inside[k] = col_in && py >= 0 && py < n;
+        own[k] = inside[k] && col_own && j0 + k >= 1 && j0 + k <= kS3Out;
+        u_prev[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0 - 2);
+        u_cur[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0 - 1);
+        u_next[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0);
+        b_next[k] = get3(b, n, px, py, z0 - 1);
+        r_m[k] = r_c[k] = p1_m[k] = p1_c[k] = p2_m[k] = p2_c[k] = T(0);
+    }
+    // the one-point u ring around the 32x32 tile, one point per thread t < 132
+    const bool ring = !ZERO_U && t < 4 * (kS3 + 1);
+    int ri = 0, rj = 0;
+    if (ring) {
+        const int side = t / (kS3 + 1), q = t % (kS3 + 1);
+        if (side == 0) { ri = q - 1; rj = -1; }
+        else if (side == 1) { ri = kS3; rj = q - 1; }
+        else if (side == 2) { ri = q; rj = kS3; }
+        else { ri = -1; rj = q; }
+    }
+    T ring_next = T(0);
+    if (!ZERO_U) {
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) su[(z0 - 1) & 1][(j0 + k + 1) * kS3U + (i + 1)] = u_cur[k];
+        if (ring) {
+            su[(z0 - 1) & 1][(rj + 1) * kS3U + (ri + 1)] = get3(u, n, ex0 + ri, ey0 + rj, z0 - 1);
+            ring_next = get3(u, n, ex0 + ri, ey0 + rj, z0);
+        }
+        __syncthreads();
+    }
+
+    for (int zz = z0 - 1; zz <= z1; ++zz) {  // residual plane zz, output plane zz - 1
+        const int buf = zz & 1;
+        const bool zin = zz >= 0 && zz < n;
+        T r_n[kS3Pts], u_nn[kS3Pts];
+        T ring_nn = T(0);
+        if (!ZERO_U) {
+#pragma unroll
+            for (int k = 0; k < kS3Pts; ++k) u_nn[k] = get3(u, n, px, ey0 + j0 + k, zz + 2);
+            if (ring) ring_nn = get3(u, n, ex0 + ri, ey0 + rj, zz + 2);
+        }
+        // residual of plane zz at the thread's four tile points
+        T up = T(0), dn = T(0);
+        if (!ZERO_U) {
+            up = su[buf][(j0) * kS3U + (i + 1)];                // row j0 - 1
+            dn = su[buf][(j0 + kS3Pts + 1) * kS3U + (i + 1)];   // row j0 + 4
+        }
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) {
+            T bb = b_next[k];
+            b_next[k] = get3(b, n, px, ey0 + j0 + k, zz + 1);
+            if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
+            T r;
+            if (!ZERO_U) {
+                const T *row = &su[buf][(j0 + k + 1) * kS3U + (i + 1)];
+                const T us = k == 0 ? up : u_cur[k - 1];
+                const T un = k == kS3Pts - 1 ? dn : u_cur[k + 1];
+                const T s = radd(radd(radd(row[-1], row[1]), radd(us, un)), radd(u_prev[k], u_next[k]));
+                r = radd(rfma(m6, u_cur[k], bb), s);
+                su[1 - buf][(j0 + k + 1) * kS3U + (i + 1)] = u_next[k];
+            } else {
+                r = bb;
+            }
+            if (!(inside[k] && zin)) r = T(0);
+            if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
+            r_n[k] = r;
+            sr[buf][(j0 + k) * kS3 + i] = r;
+        }
+        if (ring) su[1 - buf][(rj + 1) * kS3U + (ri + 1)] = ring_next;
+        __syncthreads();
+        if (col_own) {
+            // x-pair sums of rows j0 - 1 .. j0 + 4 (rows clamped into the tile:
+            // a clamped row only feeds rows that are not output)
+            const T *rp = sr[buf];
+            T hp[kS3Pts + 2], rv[kS3Pts + 2];
+#pragma unroll
+            for (int q = 0; q < kS3Pts + 2; ++q) {
+                int jr = j0 - 1 + q;
+                jr = jr < 0 ? 0 : (jr > kS3 - 1 ? kS3 - 1 : jr);
+                hp[q] = radd(rp[jr * kS3 + il], rp[jr * kS3 + ir]);
+                rv[q] = q >= 1 && q <= kS3Pts ? r_n[q - 1] : rp[jr * kS3 + i];
+            }
+#pragma unroll
+            for (int k = 0; k < kS3Pts; ++k) {
+                const T p1 = radd(hp[k + 1], radd(rv[k], rv[k + 2]));
+                const T p2 = radd(hp[k], hp[k + 2]);
+                if (own[k] && zz - 1 >= z0) {
+                    const T F = radd(p1_c[k], radd(r_m[k], r_n[k]));
+                    const T E = radd(p2_c[k], radd(p1_m[k], p1));
+                    const T C = radd(p2_m[k], p2);
+                    const T base = ZERO_U ? rmul(c0, r_c[k]) : rfma(c0, r_c[k], u_prev[k]);
+                    out[(size_t)(zz - 1) * plane + (size_t)(ey0 + j0 + k) * n + px] =
+                        rfma(c3, C, rfma(c2, E, rfma(c1, F, base)));
+                }
+                p1_m[k] = p1_c[k];
+                p1_c[k] = p1;
+                p2_m[k] = p2_c[k];
+                p2_c[k] = p2;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) {
+            r_m[k] = r_c[k];
+            r_c[k] = r_n[k];
+            if (!ZERO_U) {
+                u_prev[k] = u_cur[k];
+                u_cur[k] = u_next[k];
+                u_next[k] = u_nn[k];
+            }
+        }
+        ring_next = ring_nn;
+    }
+    __syncthreads();  // the next segment refills both buffers
+}
+
+// persistent like sweep3d_kernel (same (tile, plane) runs, same partials)
+template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
+__global__ void __launch_bounds__(kS3Threads, 1)
+sweep27_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int bx, long total,
+               long per, T c0, T c1, T c2, T c3, int hk, double *__restrict__ partials)
+{
+    __shared__ T su[2][kS3U * kS3U];
+    __shared__ T sr[2][kS3 * kS3];
+    double acc = 0.0;
+    const long w0 = (long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
+    for (long w = w0; w < w1;) {
+        const int tile = (int)(w / n), z0 = (int)(w - (long)tile * n);
+        const int z1 = (int)(z0 + (w1 - w) < (long)n ? z0 + (w1 - w) : (long)n);
+        sweep27_segment<T, ZERO_U, UNSCALED_B, NORM>(su, sr, u, b, out, n, tile % bx, tile / bx, z0, z1, c0, c1, c2,
+                                                     c3, hk, acc);
+        w += z1 - z0;
+    }
+    if (NORM) block_sum_store<kS3Threads>(acc, &partials[blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
 // Residual + full weighting. Coarse point (ic, jc, kc) has fine centre
 // (2ic+1, 2jc+1, 2kc+1) (0-based):
 //   along x: t1 = (rh(2ic) + rh(2ic+2)) + 2 rh(2ic+1)
@@ -478,10 +658,17 @@ cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n,
 {
     const S3Plan g = sweep3d_plan(n, (int)sizeof(T));
     const int hk = h2_exponent(n);
-    const T c0 = T(c[0]), c1 = T(c[1]);
-#define MG_SWEEP(ZU, UB, NRM)                                                                                   \
-    sweep3d_kernel<T, ZU, UB, NRM><<<g.blocks, kS3Threads, 0, s>>>(u, b, out, n, g.bx, g.total, g.per, c0, c1, hk, \
-                                                                   partials)
+    const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]), c3 = T(c[3]);
+    const bool wide = c[2] != 0.0 || c[3] != 0.0;  // 27-point M (edge or corner weights)
+#define MG_SWEEP(ZU, UB, NRM)                                                                                     \
+    do {                                                                                                          \
+        if (wide)                                                                                                 \
+            sweep27_kernel<T, ZU, UB, NRM><<<g.blocks, kS3Threads, 0, s>>>(u, b, out, n, g.bx, g.total, g.per, c0, \
+                                                                           c1, c2, c3, hk, partials);              \
+        else                                                                                                      \
+            sweep3d_kernel<T, ZU, UB, NRM><<<g.blocks, kS3Threads, 0, s>>>(u, b, out, n, g.bx, g.total, g.per, c0, \
+                                                                           c1, hk, partials);                      \
+    } while (0)
     const bool z = u == nullptr, nrm = partials != nullptr;
     if (z) {
         if (unscaled) {

@@ -88,7 +88,7 @@ extern "C" mg_status mg_op_sweep_norm_noalloc(int d, int n, mg_prec prec, const 
     if ((d == 2 && n > 16383) || (d == 3 && n > 1023)) return MG_EINVAL;
     const int np = partials_needed(d, n, prec == MG_FP64 ? 8 : 4);
     if (np > kMaxPartials) return MG_EINVAL;
-    double c[3] = {0, 0, 0};
+    double c[4] = {0, 0, 0, 0};
     for (int j = 0; j < ncoeffs; ++j) c[j] = spai_coeffs[j];
     double *partials = nullptr;
     mg_status st = scratch_on_current_device(&partials);

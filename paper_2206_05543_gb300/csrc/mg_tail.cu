@@ -53,8 +53,26 @@ __device__ T residual_at(int d, const T *u, const T *bh, const Lay &L, int x, in
     return radd(rfma(T(-6), u[p], bh[p]), s);
 }
 
+// in-plane sums of the 27-point sweep (see mg_kernels3d.cu): x pair, the 4
+// edge neighbours and the 4 corner neighbours of (x, y) in plane z
 template <typename T>
-__device__ T sweep_at(int d, const T *rh, const T *u, const Lay &L, int x, int y, int z, T c0, T c1, T c2)
+__device__ __forceinline__ T hp_at(const T *rh, const Lay &L, int x, int y, int z)
+{
+    return radd(at(rh, L, x - 1, y, z), at(rh, L, x + 1, y, z));
+}
+template <typename T>
+__device__ __forceinline__ T p1_at(const T *rh, const Lay &L, int x, int y, int z)
+{
+    return radd(hp_at(rh, L, x, y, z), radd(at(rh, L, x, y - 1, z), at(rh, L, x, y + 1, z)));
+}
+template <typename T>
+__device__ __forceinline__ T p2_at(const T *rh, const Lay &L, int x, int y, int z)
+{
+    return radd(hp_at(rh, L, x, y - 1, z), hp_at(rh, L, x, y + 1, z));
+}
+
+template <typename T>
+__device__ T sweep_at(int d, const T *rh, const T *u, const Lay &L, int x, int y, int z, T c0, T c1, T c2, T c3)
 {
     const long p = lidx(L, x, y, z);
     if (d == 2) {
@@ -63,6 +81,12 @@ __device__ T sweep_at(int d, const T *rh, const T *u, const Lay &L, int x, int y
         const T C = radd(radd(at(rh, L, x - 1, y - 1, 0), at(rh, L, x + 1, y - 1, 0)),
                          radd(at(rh, L, x - 1, y + 1, 0), at(rh, L, x + 1, y + 1, 0)));
         return rfma(c2, C, rfma(c1, E, rfma(c0, rh[p], u[p])));
+    }
+    if (c2 != T(0) || c3 != T(0)) {  // 27-point M
+        const T F = radd(p1_at(rh, L, x, y, z), radd(at(rh, L, x, y, z - 1), at(rh, L, x, y, z + 1)));
+        const T E = radd(p2_at(rh, L, x, y, z), radd(p1_at(rh, L, x, y, z - 1), p1_at(rh, L, x, y, z + 1)));
+        const T C = radd(p2_at(rh, L, x, y, z - 1), p2_at(rh, L, x, y, z + 1));
+        return rfma(c3, C, rfma(c2, E, rfma(c1, F, rfma(c0, rh[p], u[p]))));
     }
     const T E = radd(radd(radd(at(rh, L, x - 1, y, z), at(rh, L, x + 1, y, z)),
                           radd(at(rh, L, x, y - 1, z), at(rh, L, x, y + 1, z))),
@@ -143,7 +167,7 @@ __device__ void coarse_apply(int d, const double *__restrict__ inv, const T *bh,
 }
 
 template <typename T>
-__device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d, T c0, T c1, T c2,
+__device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d, T c0, T c1, T c2, T c3,
                          const double *lu)
 {
     for (int o = 0; o < nops; ++o) {
@@ -175,7 +199,7 @@ __device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d
                 for (int i = threadIdx.x; i < np; i += blockDim.x) {
                     int x, y, z;
                     coords(i, n, x, y, z);
-                    tmp[lidx(L, x, y, z)] = sweep_at(d, rh, u, L, x, y, z, c0, c1, c2);
+                    tmp[lidx(L, x, y, z)] = sweep_at(d, rh, u, L, x, y, z, c0, c1, c2, c3);
                 }
                 __syncthreads();
                 for (int i = threadIdx.x; i < np; i += blockDim.x) {
@@ -214,7 +238,7 @@ __device__ void run_tail(const TailLevel *lv, const TailOp *ops, int nops, int d
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a)
 {
-    run_tail<T>(a.lv, a.ops, a.nops, a.d, T(a.c[0]), T(a.c[1]), T(a.c[2]), a.lu);
+    run_tail<T>(a.lv, a.ops, a.nops, a.d, T(a.c[0]), T(a.c[1]), T(a.c[2]), T(a.c[3]), a.lu);
 }
 
 // one block per problem: the tail of problem blockIdx.x (skipped when inactive)
@@ -226,7 +250,7 @@ tail_batched(const TailLevel *__restrict__ lv, const TailOp *__restrict__ ops, c
 {
     const int p = blockIdx.x;
     if (!active[p]) return;
-    run_tail<T>(lv + (size_t)p * kMaxTailLevels, ops + op_off[p], op_cnt[p], d, T(c0), T(c1), T(c2), lu);
+    run_tail<T>(lv + (size_t)p * kMaxTailLevels, ops + op_off[p], op_cnt[p], d, T(c0), T(c1), T(c2), T(0), lu);
 }
 
 template <typename T>

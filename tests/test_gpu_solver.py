@@ -160,7 +160,7 @@ def test_invalid_arguments_raise():
     with pytest.raises(MGError):
         Solver(2, 48)
     with pytest.raises(MGError):
-        Solver(3, 64, coeffs=(0.1, 0.2, 0.3))
+        Solver(3, 64, coeffs=(0.1, 0.2, 0.3, 0.01, 0.001))
     with Solver(2, 64) as s:
         with pytest.raises(ValueError):
             s.solve(dev(np.zeros((64, 64))))
