@@ -213,6 +213,25 @@ mg_status mg_op_residual_restrict(int d, int n, mg_prec prec, const void *u, con
  * e (((n-1)/2)^d points) (Sec. 4), in place on u. */
 mg_status mg_op_prolong_correct(int d, int n, mg_prec prec, const void *e_coarse, void *u, void *stream);
 
+/* The two temporally blocked passes of a V(1,1) visit of an FP32 2D level
+ * (the FP32 cycles of MG_FP32_IR contexts run them), for checking against
+ * the single steps; d must be 2, prec MG_FP32_IR (float arrays), n >= 7,
+ * 1..3 weights, bh scaled. Results equal the unfused steps bit for bit.
+ * mg_op_sweep_restrict: u_out = one SPAI sweep of u (Sec. 2, Eq. (2.1);
+ * u == NULL: from zero) and bh_coarse_out = 4 R (bh - h^2 A u_out), full
+ * weighting R (Sec. 4), ((n-1)/2)^2 points. */
+mg_status mg_op_sweep_restrict(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs, const void *u,
+                               const void *bh, void *u_out, void *bh_coarse_out, void *stream);
+
+/* mg_op_prolong_sweep: v = u + P e_coarse (bilinear interpolation and
+ * correction, Sec. 4), then one SPAI sweep of v (Sec. 2, Eq. (2.1)) into
+ * u_out (float); if u64_acc (DEVICE, n^2 doubles, compact) is non-NULL the
+ * sweep's result is instead added to it in FP64 (the update of the FP64
+ * solution that ends an FP32 refinement cycle) and u_out may be NULL. */
+mg_status mg_op_prolong_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs,
+                              const void *e_coarse, const void *u, const void *bh, void *u_out, double *u64_acc,
+                              void *stream);
+
 /* Exact solve of h0^2 A_h0 x = bh on the coarsest grid (n = 3, 3^d points). */
 mg_status mg_op_coarse_solve(int d, mg_prec prec, const void *bh, void *x_out, void *stream);
 

@@ -51,6 +51,8 @@ SIGNATURES = {
     "mg_kernel_launch_count": (_U, []),
     "mg_test_arm_wait_expiry": (_I, [_I]),
     "mg_measure_fp64_rate": (_I, [_I, _DP, _DP]),
+    "mg_op_sweep_restrict": (_I, [_I, _I, _I, _DP, _I, _P, _P, _P, _P, _P]),
+    "mg_op_prolong_sweep": (_I, [_I, _I, _I, _DP, _I, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -419,3 +421,36 @@ def op_coarse_solve(bh, stream=None):
     _check(lib().mg_op_coarse_solve(d, _prec_of(bh), _dev_ptr(bh, bh.dtype, bh.shape, "bh"),
                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "mg_op_coarse_solve")
     return out
+
+
+def op_sweep_restrict(u, bh, coeffs, stream=None):
+    """The temporally blocked pass (FP32, 2D): (one sweep of u (None: from
+    zero), 4 R of the residual of that sweep)."""
+    torch = _torch()
+    d, n = _level(bh)
+    nc = (n - 1) // 2
+    out = torch.empty_like(bh)
+    bc = torch.empty((nc,) * d, dtype=bh.dtype, device=bh.device)
+    arr, ncf = _coeff_array(coeffs)
+    pu = ctypes.c_void_p(0) if u is None else _dev_ptr(u, bh.dtype, bh.shape, "u")
+    _check(lib().mg_op_sweep_restrict(d, n, _prec_of(bh), arr, ncf, pu, _dev_ptr(bh, bh.dtype, bh.shape, "bh"),
+                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(bc.data_ptr()),
+                                      _stream_ptr(stream)), "mg_op_sweep_restrict")
+    return out, bc
+
+
+def op_prolong_sweep(e_coarse, u, bh, coeffs, u64_acc=None, stream=None):
+    """The temporally blocked pass (FP32, 2D): one sweep of u + P e_coarse,
+    returned as a new tensor, or (u64_acc given, float64) added to u64_acc in
+    place (returned)."""
+    torch = _torch()
+    d, n = _level(bh)
+    nc = (n - 1) // 2
+    arr, ncf = _coeff_array(coeffs)
+    out = None if u64_acc is not None else torch.empty_like(bh)
+    pacc = _dev_ptr(u64_acc, torch.float64, bh.shape, "u64_acc") if u64_acc is not None else None
+    _check(lib().mg_op_prolong_sweep(d, n, _prec_of(bh), arr, ncf, _dev_ptr(e_coarse, bh.dtype, (nc,) * d, "e"),
+                                     _dev_ptr(u, bh.dtype, bh.shape, "u"), _dev_ptr(bh, bh.dtype, bh.shape, "bh"),
+                                     ctypes.c_void_p(0 if out is None else out.data_ptr()), pacc,
+                                     _stream_ptr(stream)), "mg_op_prolong_sweep")
+    return u64_acc if out is None else out

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmg.so")
-SOURCES = ["mg_kernels2d.cu", "mg_pl2d.cu", "mg_pl3d.cu", "mg_tma3d.cu", "mg_kernels3d.cu", "mg_tail.cu", "mg_host.cu", "mg_adjoint.cu", "mg_batched.cu", "mg_noalloc.cu", "mg_probe.cu"]
+SOURCES = ["mg_kernels2d.cu", "mg_pl2d.cu", "mg_pl3d.cu", "mg_tma3d.cu", "mg_kernels3d.cu", "mg_tail.cu", "mg_host.cu", "mg_adjoint.cu", "mg_batched.cu", "mg_noalloc.cu", "mg_probe.cu", "mg_fused2d.cu"]
 HEADERS = ["mg_common.cuh", "mg_internal.h", "mg_ctx.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -387,6 +387,26 @@ struct Recorder {
         T *buf[2] = {A(l), B(l)};
         int cur = 0;
         bool zero = zero_start;
+        if (pl() && c->d == 2 && c->nu1 == 1 && c->nu2 == 1 && !skip_first) {
+            // V(1,1) on an FP32 2D level in two temporally blocked passes:
+            // pre-sweep + residual + restriction, then interpolation +
+            // correction + post-sweep (the last one of a refinement cycle
+            // adds into the FP64 solution)
+            e = launch_sweep_restrict2d_pl(zero ? nullptr : (const float *)buf[0], (const float *)BH(l),
+                                           (float *)buf[1], (float *)c->BH[l + 1], n, c->c, c->s);
+            if (e) return e;
+            for (int g = 0; g < c->gamma; ++g) {
+                e = visit(l + 1, g == 0, false);
+                if (e) return e;
+            }
+            if (l == 0 && acc64) {
+                fused_update = true;
+                return launch_prolong_sweep2d_pl((const float *)buf[1], (const float *)A(l + 1), (const float *)BH(l),
+                                                 nullptr, acc64, n, c->c, c->s);
+            }
+            return launch_prolong_sweep2d_pl((const float *)buf[1], (const float *)A(l + 1), (const float *)BH(l),
+                                             (float *)buf[0], nullptr, n, c->c, c->s);
+        }
         for (int s = 0; s < c->nu1; ++s) {
             if (s == 0 && skip_first) {
                 cur = 1;
@@ -1008,6 +1028,53 @@ mg_status mg_op_prolong_correct(int d, int n, mg_prec prec, const void *e_coarse
         e = op_prolong<float>(d, (const float *)e_coarse, (float *)u, n, (cudaStream_t)stream);
     else
         return MG_EINVAL;
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+// the temporally blocked V(1,1) passes of the FP32 2D levels, on padded copies
+static mg_status fused_args_ok(int d, int n, mg_prec prec, const double *w, int nw, double *c)
+{
+    if (d != 2 || prec != MG_FP32_IR || !valid_level(d, n) || n < 7 || !w || nw < 1 || nw > 3) return MG_EINVAL;
+    for (int j = 0; j < 4; ++j) c[j] = j < nw ? w[j] : 0.0;
+    return MG_OK;
+}
+
+mg_status mg_op_sweep_restrict(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs, const void *u,
+                               const void *bh, void *u_out, void *bh_coarse_out, void *stream)
+{
+    double c[4];
+    if (fused_args_ok(d, n, prec, spai_coeffs, ncoeffs, c) != MG_OK || !bh || !u_out || !bh_coarse_out)
+        return MG_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int nc = (n - 1) / 2;
+    cudaError_t e = cudaSuccess;
+    PaddedTmp tmp(d);
+    float *pu = u ? tmp.make(n, u, s, e) : nullptr;
+    float *pb = tmp.make(n, bh, s, e), *po = tmp.make(n, nullptr, s, e), *pc = tmp.make(nc, nullptr, s, e);
+    if (!e) e = launch_sweep_restrict2d_pl(pu, pb, po, pc, n, c, s);
+    if (!e) e = tmp.pack(po, (float *)u_out, n, false, s);
+    if (!e) e = tmp.pack(pc, (float *)bh_coarse_out, nc, false, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    return e ? cuda_fail(e) : MG_OK;
+}
+
+mg_status mg_op_prolong_sweep(int d, int n, mg_prec prec, const double *spai_coeffs, int ncoeffs,
+                              const void *e_coarse, const void *u, const void *bh, void *u_out, double *u64_acc,
+                              void *stream)
+{
+    double c[4];
+    if (fused_args_ok(d, n, prec, spai_coeffs, ncoeffs, c) != MG_OK || !e_coarse || !u || !bh ||
+        (!u_out && !u64_acc))
+        return MG_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int nc = (n - 1) / 2;
+    cudaError_t e = cudaSuccess;
+    PaddedTmp tmp(d);
+    float *pe = tmp.make(nc, e_coarse, s, e), *pu = tmp.make(n, u, s, e), *pb = tmp.make(n, bh, s, e);
+    float *po = u64_acc ? nullptr : tmp.make(n, nullptr, s, e);
+    if (!e) e = launch_prolong_sweep2d_pl(pu, pe, pb, po, u64_acc, n, c, s);
+    if (!e && !u64_acc) e = tmp.pack(po, (float *)u_out, n, false, s);
+    if (!e) e = cudaStreamSynchronize(s);
     return e ? cuda_fail(e) : MG_OK;
 }
 

@@ -119,6 +119,14 @@ cudaError_t launch_pack2d(const float *in, float *out, int n, bool to_padded, cu
 cudaError_t launch_add_pl2d(double *u, const float *e, int n, cudaStream_t s);
 cudaError_t launch_sweep2d_pl_acc64(const float *u, const float *b, double *u64, int n, const double *c, cudaStream_t s);
 int sweep2d_pl_blocks(int n, int H);
+// temporally blocked V(1,1) passes (mg_fused2d.cu), bit-identical to the
+// unfused kernels: (A) u1 = sweep of u0 (nullptr: from zero) and
+// bc = 4 R (bh - A u1); (B) out = sweep of u1 + P e, or, with u64 != nullptr,
+// u64 (compact FP64) += that sweep (out unused)
+cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *u1, float *bc, int n, const double *c,
+                                       cudaStream_t s);
+cudaError_t launch_prolong_sweep2d_pl(const float *u1, const float *e, const float *bh, float *out, double *u64, int n,
+                                      const double *c, cudaStream_t s);
 
 // 3D: element (x, y, z), each in [-1, n], at off + z*plane + y*pitch + x.
 struct Pitch3 {
