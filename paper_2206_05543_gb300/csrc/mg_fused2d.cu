@@ -15,14 +15,15 @@
 // same formula in the same operation order as in the unfused kernels
 // (mg_pl2d.cu, mg_kernels2d.cu), so the results are identical bit for bit.
 //
-// Layout of the work: a warp owns a tile of 32 lanes x 8 fine columns and
-// marches down a chunk of rows; lane l holds its 8 columns of every
+// Layout of the work: a warp owns a tile of 32 lanes x 4 fine columns and
+// marches down a chunk of rows; lane l holds its 4 columns of every
 // intermediate row in registers, and the horizontal neighbours come from
 // the adjacent lanes by shuffles. Lanes 0 and 31 are halo lanes: they
 // compute like the others (their outer columns are wrong, for lack of a
-// neighbour) but store nothing; lanes 1..30 own 240 fine columns (120
-// coarse columns), so adjacent tiles overlap by two lanes. No block barrier
-// and no shared memory are needed except for the FP64 epilogue.
+// neighbour) but store nothing; lanes 1..30 own 120 fine columns (60
+// coarse columns), so adjacent tiles overlap by two lanes. Global loads are
+// issued two row steps ahead of their use. No block barrier and no shared
+// memory are needed except for the FP64 epilogue.
 //
 // Pipeline per row step (A, from zero; newest row q):
 //   r0(q)  = bh(q)                              (zero outside the interior)
@@ -38,10 +39,11 @@ namespace mg {
 
 namespace {
 
-constexpr int kFC = 8;                 // fine columns per lane
+constexpr int kFC = 4;                 // fine columns per lane
 constexpr int kFOut = 30 * kFC;        // fine columns a warp stores (lanes 1..30)
 constexpr int kFWarps = 4;             // warps per block: adjacent tiles, same rows
 constexpr int kFThreads = 32 * kFWarps;
+constexpr int kFAhead = 2;             // rows of loads in flight ahead of their use
 
 struct Row8 {
     float v[kFC];
@@ -59,24 +61,49 @@ __device__ __forceinline__ Row8 zero8()
 // row's slot (columns -4 .. pitch - 5) when -4 <= x and x + 3 <= pitch - 5.
 __device__ __forceinline__ bool in_slot(const Pitch2 &g, int x) { return x >= -4 && x + 3 <= g.pitch - 5; }
 
-// 8 floats of row y at column x (x % 8 == 0) of a padded level; rows outside
-// [-1, n] and float4s outside the row's slot read as zero (inside the slot,
-// the ghost ring and the padding are zero in memory)
-__device__ __forceinline__ Row8 load8(const float *base, const Pitch2 &g, int x, int y)
+// Global rows reach the lanes through per-warp rings in shared memory filled
+// by asynchronous copies (cp.async), kFDepth row steps ahead of their use:
+// the bytes in flight no longer cost registers. Lane l copies and later
+// reads only its own entries, so completion needs no barrier, only
+// cp.async.wait_group in the lane itself. A ring has kFSlots > kFDepth slots,
+// so the slot refilled at a step was read two steps earlier.
+constexpr int kFDepth = 6;
+constexpr int kFSlots = 8;  // power of two
+static_assert(kFSlots > kFDepth + 1, "a refilled slot must have been read at least two steps earlier");
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// copy `bytes` (16 or 8) from src to shared dst; !valid: fill zeros, read nothing
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
 {
-    Row8 r = zero8();
-    if (y < -1 || y > g.n) return r;
-    const float *p = base + g.off + (long)y * g.pitch + x;
-    if (in_slot(g, x)) {
-        const float4 a = *reinterpret_cast<const float4 *>(p);
-        r.v[0] = a.x, r.v[1] = a.y, r.v[2] = a.z, r.v[3] = a.w;
-    }
-    if (in_slot(g, x + 4)) {
-        const float4 b = *reinterpret_cast<const float4 *>(p + 4);
-        r.v[4] = b.x, r.v[5] = b.y, r.v[6] = b.z, r.v[7] = b.w;
-    }
-    return r;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most kFDepth - 1 of this lane's copy groups are still pending
+__device__ __forceinline__ void cp_wait_depth() { asm volatile("cp.async.wait_group %0;" ::"n"(kFDepth - 1) : "memory"); }
+
+// one float4 per lane and row: ring[slot][lane]
+struct Ring4 {
+    float4 *s;
+    __device__ __forceinline__ void issue(const float *base, const Pitch2 &g, int x, int y, int lane) const
+    {
+        const bool ok = y >= -1 && y <= g.n && in_slot(g, x);
+        cp_async16(&s[(y & (kFSlots - 1)) * 32 + lane], ok ? base + g.off + (long)y * g.pitch + x : base, ok);
+    }
+    __device__ __forceinline__ Row8 read(int y, int lane) const
+    {
+        const float4 a = s[(y & (kFSlots - 1)) * 32 + lane];
+        Row8 r;
+        r.v[0] = a.x, r.v[1] = a.y, r.v[2] = a.z, r.v[3] = a.w;
+        return r;
+    }
+};
 
 // x pair sums v_W + v_E of the lane's 8 columns (neighbours across lanes by shuffles)
 __device__ __forceinline__ Row8 xpair(const Row8 &v)
@@ -135,9 +162,8 @@ __device__ __forceinline__ Row8 mask8(Row8 v, int x, int j, int n)
 __device__ __forceinline__ void store8(float *base, const Pitch2 &g, int x, int j, const Row8 &v)
 {
     float *p = base + g.off + (long)j * g.pitch + x;
-    if (x + 7 < g.n) {
+    if (x + kFC - 1 < g.n) {
         *reinterpret_cast<float4 *>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
-        *reinterpret_cast<float4 *>(p + 4) = make_float4(v.v[4], v.v[5], v.v[6], v.v[7]);
     } else {
 #pragma unroll
         for (int k = 0; k < kFC; ++k)
@@ -147,53 +173,72 @@ __device__ __forceinline__ void store8(float *base, const Pitch2 &g, int x, int 
 
 // ---------------------------------------------------------------------------
 // A. sweep + residual + full weighting. Block (bx, by): warp w of the block
-// owns tile t = bx * kFWarps + w (lane l: fine columns x = 240 t - 8 + 8 l)
+// owns tile t = bx * kFWarps + w (lane l: fine columns x = 120 t - 4 + 4 l)
 // and coarse rows [by Hc, by Hc + Hc). Writes u1 at fine rows [2 jc0, 2 jc1)
 // (the last chunk also row n - 1) and the coarse rows [jc0, jc1).
+// Rings: bh row R and, from a non-zero start, u0 row R + 1 at step R.
 // ---------------------------------------------------------------------------
 template <bool ZERO_U>
 __global__ void __launch_bounds__(kFThreads)
 sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ bh, float *__restrict__ u1out,
                         float *__restrict__ bc, Pitch2 g, Pitch2 gc, int Hc, float c0, float c1, float c2)
 {
+    extern __shared__ __align__(16) float4 fsm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x * kFWarps + w;
     const int n = g.n, nc = gc.n;
     const int x = kFOut * tile - kFC + kFC * lane;
     if (kFOut * tile >= n) return;  // the whole warp leaves together
+    const Ring4 rb{fsm + (ZERO_U ? 1 : 2) * w * kFSlots * 32};
+    const Ring4 ru{rb.s + kFSlots * 32};
     const bool owner = lane >= 1 && lane <= 30;
     const int jc0 = blockIdx.y * Hc, jc1 = min(jc0 + Hc, nc);
     // fine rows of u1 this chunk stores
     const int w0 = 2 * jc0, w1 = jc1 == nc ? n : 2 * jc1;
     // the newest residual row r0 is row R; u1 row R - 1; r1 row R - 2
     const int Rfirst = 2 * jc0 - 2, Rlast = 2 * jc1 + 2;
+    // prologue: the copies of steps Rfirst .. Rfirst + kFDepth - 1 (one group per step)
+    for (int k = 0; k < kFDepth; ++k) {
+        rb.issue(bh, g, x, Rfirst + k, lane);
+        if (!ZERO_U) {
+            if (k == 0) {
+                ru.issue(u0, g, x, Rfirst - 1, lane);
+                ru.issue(u0, g, x, Rfirst, lane);
+            }
+            ru.issue(u0, g, x, Rfirst + 1 + k, lane);
+        }
+        cp_commit();
+    }
     Row8 r0s = zero8(), r0c = zero8(), hs = zero8(), hc = zero8();
     Row8 u1s = zero8(), u1c = zero8();  // u1 rows R-3, R-2
     Row8 bq1 = zero8(), bq2 = zero8();  // bh rows R-1, R-2
     // non-zero start: u0 rows R-1, R (the residual r0(R) also needs R+1)
     Row8 ua = zero8(), ub = zero8(), ucur = zero8();  // ucur: u0 row R-1, the sweep's base
-    // loads are issued one row step ahead of their use
-    Row8 bnext = load8(bh, g, x, Rfirst), unext = zero8();
-    if (!ZERO_U) {
-        ua = load8(u0, g, x, Rfirst - 1);
-        ub = load8(u0, g, x, Rfirst);
-        unext = load8(u0, g, x, Rfirst + 1);
-    }
-    float t1[4] = {0.f, 0.f, 0.f, 0.f}, t2[4] = {0.f, 0.f, 0.f, 0.f};  // x passes of r1 rows f-1, f-2
+    constexpr int kCC = kFC / 2;  // coarse columns per lane
+    float t1[kCC], t2[kCC];       // x passes of r1 rows f-1, f-2
+#pragma unroll
+    for (int k = 0; k < kCC; ++k) t1[k] = t2[k] = 0.f;
     for (int R = Rfirst; R <= Rlast; ++R) {
-        const Row8 bR = bnext;
-        bnext = load8(bh, g, x, R + 1);
+        cp_wait_depth();  // the copies of step R have landed
+        const Row8 bR = rb.read(R, lane);
         Row8 r0;
         if (ZERO_U) {
             r0 = bR;  // the ghost ring of bh is zero
         } else {
-            const Row8 uc = unext;
-            unext = load8(u0, g, x, R + 2);
+            if (R == Rfirst) {
+                ua = ru.read(R - 1, lane);
+                ub = ru.read(R, lane);
+            }
+            const Row8 uc = ru.read(R + 1, lane);
             r0 = residual8(ua, ub, uc, bR, x, R, n);
             ucur = ua;  // u0 row R - 1
             ua = ub;
             ub = uc;
         }
+        // the copies of step R + kFDepth
+        rb.issue(bh, g, x, R + kFDepth, lane);
+        if (!ZERO_U) ru.issue(u0, g, x, R + 1 + kFDepth, lane);
+        cp_commit();
         const Row8 hn = xpair(r0);
         // u1 row R - 1 (masked to the interior: the residual below reads it as the boundary value)
         const Row8 u1n = mask8(spai8<ZERO_U>(r0s, r0c, r0, hs, hc, hn, ucur, c0, c1, c2), x, R - 1, n);
@@ -202,29 +247,30 @@ sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ 
         const Row8 r1 = residual8(u1s, u1c, u1n, bq2, x, R - 2, n);
         // full weighting: x pass of r1 row f = R - 2 at fine columns 2 ic, 2 ic + 1, 2 ic + 2
         const int f = R - 2;
-        const float r8 = __shfl_down_sync(0xffffffffu, r1.v[0], 1);
-        float tx[4];
+        const float rnext = __shfl_down_sync(0xffffffffu, r1.v[0], 1);
+        float tx[kCC];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) tx[k] = rfma(2.f, r1.v[2 * k + 1], radd(r1.v[2 * k], k == 3 ? r8 : r1.v[2 * k + 2]));
+        for (int k = 0; k < kCC; ++k)
+            tx[k] = rfma(2.f, r1.v[2 * k + 1], radd(r1.v[2 * k], k == kCC - 1 ? rnext : r1.v[2 * k + 2]));
         if (f >= 2 * jc0 + 2 && (f & 1) == 0) {
             const int jc = f / 2 - 1;
             const int ic = x / 2;
             if (owner && jc < jc1 && ic < nc) {
-                float v[4];
+                float v[kCC];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) v[k] = scale2<-2>(rfma(2.f, t1[k], radd(t2[k], tx[k])));
+                for (int k = 0; k < kCC; ++k) v[k] = scale2<-2>(rfma(2.f, t1[k], radd(t2[k], tx[k])));
                 float *p = bc + gc.off + (long)jc * gc.pitch + ic;
-                if (ic + 3 < nc) {
-                    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+                if (ic + kCC - 1 < nc) {
+                    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
+                    for (int k = 0; k < kCC; ++k)
                         if (ic + k < nc) p[k] = v[k];
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kCC; ++k) {
             t2[k] = t1[k];
             t1[k] = tx[k];
         }
@@ -237,26 +283,26 @@ sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ 
         bq2 = bq1;
         bq1 = bR;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the warp has left
 }
 
 // ---------------------------------------------------------------------------
 // B. interpolation + correction + sweep. Block (bx, by): warp tiles as in A,
 // fine output rows [by H, by H + H). u2 = u1 + P e; r = bh - A u2 (scaled);
 // out = u2 + W r, stored (ACC64: added to the compact FP64 array u64).
+// Rings at step Q: u1 row Q, bh row Q - 1, the coarse e rows as they are
+// first needed and (ACC64) the FP64 values of output row Q - 2.
 // ---------------------------------------------------------------------------
-// x pass of coarse row m for the lane's fine columns x .. x + 7 (coarse
-// k0 = x / 2 .. k0 + 3): fine 2k: 0.5 (e[k-1] + e[k]); fine 2k + 1: e[k]
-__device__ __forceinline__ Row8 interp_x8(const float *e, const Pitch2 &gc, int k0, int m)
+// x pass of the coarse row held in e2 (the lane's coarse columns k0 = x / 2,
+// k0 + 1) for its fine columns x .. x + 3: fine 2k: 0.5 (e[k-1] + e[k]);
+// fine 2k + 1: e[k]
+__device__ __forceinline__ Row8 interp_x8(float2 e2)
 {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    if (m >= -1 && m <= gc.n && in_slot(gc, k0)) {
-        const float4 a = *reinterpret_cast<const float4 *>(e + gc.off + (long)m * gc.pitch + k0);
-        c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w;
-    }
-    const float left = __shfl_up_sync(0xffffffffu, c[3], 1);
+    const float c[2] = {e2.x, e2.y};
+    const float left = __shfl_up_sync(0xffffffffu, c[1], 1);
     Row8 v;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 2; ++k) {
         v.v[2 * k] = scale2<-1>(radd(k == 0 ? left : c[k - 1], c[k]));
         v.v[2 * k + 1] = c[k];
     }
@@ -269,52 +315,78 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
                        float *__restrict__ out, double *__restrict__ u64, Pitch2 g, Pitch2 gc, int H, float c0,
                        float c1, float c2)
 {
-    __shared__ __align__(16) float sacc[kFWarps][32 * kFC];
+    extern __shared__ __align__(16) float4 fsm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x * kFWarps + w;
     const int n = g.n;
     const int x = kFOut * tile - kFC + kFC * lane;
     if (kFOut * tile >= n) return;
+    // per warp: u1 and bh rings (float4), the e ring (float2) and, ACC64, the
+    // FP64 ring (kFC doubles per lane) and the staging row
+    constexpr int kRing4 = kFSlots * 32;                      // float4s
+    constexpr int kWarpF4 = 2 * kRing4 + kRing4 / 2 + (ACC64 ? kFC * kRing4 / 2 + 32 : 0);
+    float4 *base = fsm + w * kWarpF4;
+    const Ring4 ru{base}, rb{base + kRing4};
+    float2 *re = reinterpret_cast<float2 *>(base + 2 * kRing4);          // [slot][lane]
+    double *r64 = reinterpret_cast<double *>(base + 2 * kRing4 + kRing4 / 2);  // [slot][q][lane]
+    float *sacc = reinterpret_cast<float *>(base + 2 * kRing4 + kRing4 / 2 + kFC * kRing4 / 2);
     const bool owner = lane >= 1 && lane <= 30;
     const int k0 = x / 2;
     const int xw = kFOut * tile - kFC;  // column of lane 0's first value
     const int y0 = blockIdx.y * H, y1 = min(y0 + H, n);
     // the newest corrected row u2 is row Q; residual row Q - 1; output row Q - 2
     const int Qfirst = y0 - 2, Qlast = y1 + 1;
-    // x passes v_m of the coarse rows: fine row 2m + 1 takes v_m, fine row 2m
-    // takes 0.5 (v_{m-1} + v_m); vprev = v_{mQ}, vcur = v_{mQ + 1} with
-    // mQ = floor((Q - 1) / 2)
-    int mcur = (Qfirst - 1) >> 1;
-    Row8 vprev = interp_x8(e, gc, k0, mcur - 1), vcur = interp_x8(e, gc, k0, mcur);
-    Row8 u2s = zero8(), u2c = zero8();                            // u2 rows Q-2, Q-1
-    Row8 rs = zero8(), rc = zero8(), hs = zero8(), hc = zero8();  // residual rows Q-3, Q-2 and x pairs
-    Row8 unext = load8(u1, g, x, Qfirst), bnext = load8(bh, g, x, Qfirst - 1);
-    double a64[kFC];  // ACC64: the FP64 values of output row Q - 2, loaded one step ahead
-#pragma unroll
-    for (int q = 0; q < kFC; ++q) a64[q] = 0.0;
-    auto load64 = [&](int j, double *dst) {
+    // coarse row m (0-based) sits at fine row 2m + 1; fine row Q needs the
+    // coarse rows mQ = floor((Q - 1) / 2) and mQ + 1
+    auto issue_e = [&](int m) {
+        const bool ok = m >= -1 && m <= gc.n && k0 >= -4 && k0 + 1 <= gc.pitch - 5;
+        cp_async8(&re[(m & (kFSlots - 1)) * 32 + lane], ok ? e + gc.off + (long)m * gc.pitch + k0 : e, ok);
+    };
+    auto issue_64 = [&](int j) {
 #pragma unroll
         for (int q = 0; q < kFC; ++q) {
             const int col = xw + lane + 32 * q;
             const int src = (lane + 32 * q) / kFC;
-            dst[q] = (j >= y0 && j < y1 && src >= 1 && src <= 30 && col >= 0 && col < n) ? u64[(long)j * n + col] : 0.0;
+            const bool ok = j >= y0 && j < y1 && src >= 1 && src <= 30 && col >= 0 && col < n;
+            cp_async8(&r64[((j & (kFSlots - 1)) * kFC + q) * 32 + lane], ok ? u64 + (long)j * n + col : u64, ok);
         }
     };
-    if (ACC64) load64(Qfirst - 2, a64);
+    int m_issued = ((Qfirst - 1) >> 1) - 1;
+    auto issue_step = [&](int F) {  // the copies for fine row F
+        ru.issue(u1, g, x, F, lane);
+        rb.issue(bh, g, x, F - 1, lane);
+        const int mneed = ((F - 1) >> 1) + 1;
+        while (m_issued < mneed) issue_e(++m_issued);
+        if (ACC64) issue_64(F - 2);
+        cp_commit();
+    };
+    for (int k = 0; k < kFDepth; ++k) issue_step(Qfirst + k);
+    int mcur = 0;
+    Row8 vprev = zero8(), vcur = zero8();
+    Row8 u2s = zero8(), u2c = zero8();                            // u2 rows Q-2, Q-1
+    Row8 rs = zero8(), rc = zero8(), hs = zero8(), hc = zero8();  // residual rows Q-3, Q-2 and x pairs
     for (int Q = Qfirst; Q <= Qlast; ++Q) {
-        // fine row Q (0-based) = 2m + 1 sits on coarse m; Q = 2m lies between m - 1 and m
-        Row8 u2 = unext;
-        unext = load8(u1, g, x, Q + 1);
-        const Row8 bq = bnext;
-        bnext = load8(bh, g, x, Q);
-        double a64n[kFC];
-        if (ACC64) load64(Q - 1, a64n);
+        cp_wait_depth();  // the copies of step Q have landed
+        Row8 u2 = ru.read(Q, lane);
+        const Row8 bQ = rb.read(Q - 1, lane);
         const int mQ = (Q - 1) >> 1;
+        if (Q == Qfirst) {
+            mcur = mQ + 1;
+            vprev = interp_x8(re[(mQ & (kFSlots - 1)) * 32 + lane]);
+            vcur = interp_x8(re[(mcur & (kFSlots - 1)) * 32 + lane]);
+        }
         while (mcur < mQ + 1) {
             vprev = vcur;
             ++mcur;
-            vcur = interp_x8(e, gc, k0, mcur);
+            vcur = interp_x8(re[(mcur & (kFSlots - 1)) * 32 + lane]);
         }
+        double a64[kFC];
+        if (ACC64) {
+#pragma unroll
+            for (int q = 0; q < kFC; ++q) a64[q] = r64[(((Q - 2) & (kFSlots - 1)) * kFC + q) * 32 + lane];
+        }
+        issue_step(Q + kFDepth);
+        // here vcur = x pass of coarse row mQ + 1, vprev = of mQ
         if (Q & 1) {  // Q = 2 mQ + 1
 #pragma unroll
             for (int k = 0; k < kFC; ++k) u2.v[k] = radd(u2.v[k], vprev.v[k]);
@@ -324,33 +396,29 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
         }
         u2 = mask8(u2, x, Q, n);
         // residual of row Q - 1 and its x pairs
-        const Row8 r = residual8(u2s, u2c, u2, bq, x, Q - 1, n);
+        const Row8 r = residual8(u2s, u2c, u2, bQ, x, Q - 1, n);
         const Row8 hn = xpair(r);
         // sweep of row Q - 2
         const int j = Q - 2;
         if (j >= y0) {
             const Row8 o = spai8<false>(rs, rc, r, hs, hc, hn, u2s, c0, c1, c2);
             if (ACC64) {
-                // stage the warp's 256 FP32 results; lane l then updates the
-                // FP64 columns xw + l + 32 q (q < 8), 256 contiguous bytes per access
+                // stage the warp's 32 kFC FP32 results; lane l then updates the
+                // FP64 columns xw + l + 32 q (q < kFC), 256 contiguous bytes per access
 #pragma unroll
-                for (int k = 0; k < kFC; ++k) sacc[w][kFC * lane + k] = o.v[k];
+                for (int k = 0; k < kFC; ++k) sacc[kFC * lane + k] = o.v[k];
                 __syncwarp();
 #pragma unroll
                 for (int q = 0; q < kFC; ++q) {
                     const int col = xw + lane + 32 * q;
                     const int src = (lane + 32 * q) / kFC;
                     if (src >= 1 && src <= 30 && col >= 0 && col < n)
-                        u64[(long)j * n + col] = __dadd_rn(a64[q], widen(sacc[w][lane + 32 * q]));
+                        u64[(long)j * n + col] = radd(a64[q], widen(sacc[lane + 32 * q]));
                 }
                 __syncwarp();
             } else if (owner && x < n) {
                 store8(out, g, x, j, o);
             }
-        }
-        if (ACC64) {
-#pragma unroll
-            for (int q = 0; q < kFC; ++q) a64[q] = a64n[q];
         }
         rs = rc;
         rc = r;
@@ -359,12 +427,20 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
         u2s = u2c;
         u2c = u2;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the warp has left
 }
 
 }  // namespace
 
-// tiles of 240 fine columns, kFWarps per block
+// tiles of kFOut fine columns, kFWarps per block
 static int fused_tiles(int n) { return (n + kFOut - 1) / kFOut; }
+
+static size_t smem_a(bool zero_u) { return (size_t)kFWarps * (zero_u ? 1 : 2) * kFSlots * 32 * sizeof(float4); }
+static size_t smem_b(bool acc64)
+{
+    const size_t ring4 = (size_t)kFSlots * 32;
+    return (size_t)kFWarps * (2 * ring4 + ring4 / 2 + (acc64 ? kFC * ring4 / 2 + 32 : 0)) * sizeof(float4);
+}
 
 cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *u1, float *bc, int n, const double *c,
                                        cudaStream_t s)
@@ -376,9 +452,9 @@ cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *
     const dim3 grid(bx, (nc + Hc - 1) / Hc);
     const float c0 = (float)c[0], c1 = (float)c[1], c2 = (float)c[2];
     if (u0)
-        sweep_restrict2d_kernel<false><<<grid, kFThreads, 0, s>>>(u0, bh, u1, bc, g, gc, Hc, c0, c1, c2);
+        sweep_restrict2d_kernel<false><<<grid, kFThreads, smem_a(false), s>>>(u0, bh, u1, bc, g, gc, Hc, c0, c1, c2);
     else
-        sweep_restrict2d_kernel<true><<<grid, kFThreads, 0, s>>>(u0, bh, u1, bc, g, gc, Hc, c0, c1, c2);
+        sweep_restrict2d_kernel<true><<<grid, kFThreads, smem_a(true), s>>>(u0, bh, u1, bc, g, gc, Hc, c0, c1, c2);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -386,15 +462,25 @@ cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *
 cudaError_t launch_prolong_sweep2d_pl(const float *u1, const float *e, const float *bh, float *out, double *u64, int n,
                                       const double *c, cudaStream_t s)
 {
+    static cudaError_t attr = cudaErrorNotReady;
+    if (attr == cudaErrorNotReady) {
+        attr = cudaFuncSetAttribute(prolong_sweep2d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_b(true));
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(prolong_sweep2d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_b(false));
+    }
+    if (attr != cudaSuccess) return attr;
     const Pitch2 g = pitch2(n), gc = pitch2((n - 1) / 2);
     const int bx = (fused_tiles(n) + kFWarps - 1) / kFWarps;
     const int H = chunk_rows(bx, n, 8 * num_sms(), 16, 128);
     const dim3 grid(bx, (n + H - 1) / H);
     const float c0 = (float)c[0], c1 = (float)c[1], c2 = (float)c[2];
     if (u64)
-        prolong_sweep2d_kernel<true><<<grid, kFThreads, 0, s>>>(u1, e, bh, out, u64, g, gc, H, c0, c1, c2);
+        prolong_sweep2d_kernel<true><<<grid, kFThreads, smem_b(true), s>>>(u1, e, bh, out, u64, g, gc, H, c0, c1, c2);
     else
-        prolong_sweep2d_kernel<false><<<grid, kFThreads, 0, s>>>(u1, e, bh, out, u64, g, gc, H, c0, c1, c2);
+        prolong_sweep2d_kernel<false><<<grid, kFThreads, smem_b(false), s>>>(u1, e, bh, out, u64, g, gc, H, c0, c1,
+                                                                             c2);
     count_launch(1);
     return cudaGetLastError();
 }
