@@ -134,12 +134,13 @@ __device__ __forceinline__ double scale2_ool(double x)
         return __longlong_as_double(bits + ((long long)K << 52));
     return scale2_hw(x, K >= 0 ? (double)(1ll << (K >= 0 ? K : 0)) : 1.0 / (double)(1ll << (K < 0 ? -K : 0)));
 }
+// FP32: a plain multiply by the power of two (one FP32 instruction; the FP32
+// pipes are not the limit of any FP32 kernel here). It rounds exactly like
+// the exponent-field form wherever that form applies (the product is exact)
+// and is that form's own fallback elsewhere, so the result is the same.
 template <int K>
 __device__ __forceinline__ float scale2(float x)
 {
-    const int bits = __float_as_int(x);
-    const int e = (bits >> 23) & 0xff;
-    if (e + K >= 1 && e + K <= 0xfe && e != 0 && e != 0xff) return __int_as_float(bits + (K << 23));
     return __fmul_rn(x, K >= 0 ? (float)(1 << (K >= 0 ? K : 0)) : 1.0f / (float)(1 << (K < 0 ? -K : 0)));
 }
 // runtime exponent form (k = -2 log2 N for h^2 = 1/N^2)
@@ -159,9 +160,6 @@ __device__ __forceinline__ double scale2_ool(double x, int k)
 }
 __device__ __forceinline__ float scale2(float x, int k)
 {
-    const int bits = __float_as_int(x);
-    const int e = (bits >> 23) & 0xff;
-    if (e + k >= 1 && e + k <= 0xfe && e != 0 && e != 0xff) return __int_as_float(bits + (k << 23));
     return __fmul_rn(x, __int_as_float((127 + k) << 23));  // 2^k, |k| < 126
 }
 // FP32: the fallback multiply is on the FP32 pipe, inline is fine

@@ -88,17 +88,37 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 // wait until at most kFDepth - 1 of this lane's copy groups are still pending
 __device__ __forceinline__ void cp_wait_depth() { asm volatile("cp.async.wait_group %0;" ::"n"(kFDepth - 1) : "memory"); }
 
-// one float4 per lane and row: ring[slot][lane]
+// One float4 per lane and row of a padded level, issued row after row:
+// ring[slot][lane]. The element offset of the next row advances by the
+// pitch; only rows in [-1, n] with the lane's float4 inside the row's slot
+// are read, other rows arrive as zeros.
 struct Ring4 {
     float4 *s;
-    __device__ __forceinline__ void issue(const float *base, const Pitch2 &g, int x, int y, int lane) const
+    const float *base;
+    long off;       // element offset of row y, column x
+    long pitch;
+    int y, n;       // next row to issue; rows [-1, n] hold data
+    bool col_ok;    // the lane's float4 lies inside the row's slot
+    __device__ __forceinline__ void init(float4 *ring, const float *b, const Pitch2 &g, int x, int y_first)
     {
-        const bool ok = y >= -1 && y <= g.n && in_slot(g, x);
-        cp_async16(&s[(y & (kFSlots - 1)) * 32 + lane], ok ? base + g.off + (long)y * g.pitch + x : base, ok);
+        s = ring;
+        base = b;
+        pitch = g.pitch;
+        n = g.n;
+        y = y_first;
+        off = g.off + (long)y_first * g.pitch + x;
+        col_ok = in_slot(g, x);
     }
-    __device__ __forceinline__ Row8 read(int y, int lane) const
+    __device__ __forceinline__ void issue(int lane)
     {
-        const float4 a = s[(y & (kFSlots - 1)) * 32 + lane];
+        const bool ok = col_ok && y >= -1 && y <= n;
+        cp_async16(&s[(y & (kFSlots - 1)) * 32 + lane], ok ? base + off : base, ok);
+        off += pitch;
+        ++y;
+    }
+    __device__ __forceinline__ Row8 read(int row, int lane) const
+    {
+        const float4 a = s[(row & (kFSlots - 1)) * 32 + lane];
         Row8 r;
         r.v[0] = a.x, r.v[1] = a.y, r.v[2] = a.z, r.v[3] = a.w;
         return r;
@@ -117,17 +137,16 @@ __device__ __forceinline__ Row8 xpair(const Row8 &v)
 }
 
 // scaled 5-point residual of row j: fma(-4, u, bh) + ((u_W + u_E) + (u_S + u_N)),
-// zero outside the interior
-__device__ __forceinline__ Row8 residual8(const Row8 &us, const Row8 &uc, const Row8 &un, const Row8 &bh, int x, int j,
-                                          int n)
+// zero outside the interior (cols: bit k set when column x + k is interior)
+__device__ __forceinline__ Row8 residual8(const Row8 &us, const Row8 &uc, const Row8 &un, const Row8 &bh, unsigned cols,
+                                          bool jin)
 {
     const Row8 h = xpair(uc);
     Row8 r;
-    const bool jin = j >= 0 && j < n;
 #pragma unroll
     for (int k = 0; k < kFC; ++k) {
         const float v = radd(rfma(-4.f, uc.v[k], bh.v[k]), radd(h.v[k], radd(us.v[k], un.v[k])));
-        r.v[k] = jin && x + k >= 0 && x + k < n ? v : 0.f;
+        r.v[k] = jin && ((cols >> k) & 1u) ? v : 0.f;
     }
     return r;
 }
@@ -150,13 +169,22 @@ __device__ __forceinline__ Row8 spai8(const Row8 &rs, const Row8 &rc, const Row8
     return o;
 }
 
-__device__ __forceinline__ Row8 mask8(Row8 v, int x, int j, int n)
+__device__ __forceinline__ Row8 mask8(Row8 v, unsigned cols, bool jin)
 {
-    const bool jin = j >= 0 && j < n;
 #pragma unroll
     for (int k = 0; k < kFC; ++k)
-        if (!(jin && x + k >= 0 && x + k < n)) v.v[k] = 0.f;
+        if (!(jin && ((cols >> k) & 1u))) v.v[k] = 0.f;
     return v;
+}
+
+// bit k: column x + k is an interior column (0 <= x + k < n)
+__device__ __forceinline__ unsigned col_bits(int x, int n)
+{
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < kFC; ++k)
+        if (x + k >= 0 && x + k < n) m |= 1u << k;
+    return m;
 }
 
 __device__ __forceinline__ void store8(float *base, const Pitch2 &g, int x, int j, const Row8 &v)
@@ -189,23 +217,26 @@ sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ 
     const int n = g.n, nc = gc.n;
     const int x = kFOut * tile - kFC + kFC * lane;
     if (kFOut * tile >= n) return;  // the whole warp leaves together
-    const Ring4 rb{fsm + (ZERO_U ? 1 : 2) * w * kFSlots * 32};
-    const Ring4 ru{rb.s + kFSlots * 32};
     const bool owner = lane >= 1 && lane <= 30;
+    const unsigned cols = col_bits(x, n);
     const int jc0 = blockIdx.y * Hc, jc1 = min(jc0 + Hc, nc);
     // fine rows of u1 this chunk stores
     const int w0 = 2 * jc0, w1 = jc1 == nc ? n : 2 * jc1;
     // the newest residual row r0 is row R; u1 row R - 1; r1 row R - 2
     const int Rfirst = 2 * jc0 - 2, Rlast = 2 * jc1 + 2;
-    // prologue: the copies of steps Rfirst .. Rfirst + kFDepth - 1 (one group per step)
+    // rings: bh row R and (non-zero start) u0 row R + 1 at step R; the
+    // prologue issues steps Rfirst .. Rfirst + kFDepth - 1 (one group per step)
+    Ring4 rb, ru;
+    rb.init(fsm + (ZERO_U ? 1 : 2) * w * kFSlots * 32, bh, g, x, Rfirst);
+    if (!ZERO_U) ru.init(rb.s + kFSlots * 32, u0, g, x, Rfirst - 1);
     for (int k = 0; k < kFDepth; ++k) {
-        rb.issue(bh, g, x, Rfirst + k, lane);
+        rb.issue(lane);
         if (!ZERO_U) {
-            if (k == 0) {
-                ru.issue(u0, g, x, Rfirst - 1, lane);
-                ru.issue(u0, g, x, Rfirst, lane);
+            if (k == 0) {  // u0 rows Rfirst - 1, Rfirst
+                ru.issue(lane);
+                ru.issue(lane);
             }
-            ru.issue(u0, g, x, Rfirst + 1 + k, lane);
+            ru.issue(lane);
         }
         cp_commit();
     }
@@ -230,21 +261,21 @@ sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ 
                 ub = ru.read(R, lane);
             }
             const Row8 uc = ru.read(R + 1, lane);
-            r0 = residual8(ua, ub, uc, bR, x, R, n);
+            r0 = residual8(ua, ub, uc, bR, cols, R >= 0 && R < n);
             ucur = ua;  // u0 row R - 1
             ua = ub;
             ub = uc;
         }
         // the copies of step R + kFDepth
-        rb.issue(bh, g, x, R + kFDepth, lane);
-        if (!ZERO_U) ru.issue(u0, g, x, R + 1 + kFDepth, lane);
+        rb.issue(lane);
+        if (!ZERO_U) ru.issue(lane);
         cp_commit();
         const Row8 hn = xpair(r0);
         // u1 row R - 1 (masked to the interior: the residual below reads it as the boundary value)
-        const Row8 u1n = mask8(spai8<ZERO_U>(r0s, r0c, r0, hs, hc, hn, ucur, c0, c1, c2), x, R - 1, n);
+        const Row8 u1n = mask8(spai8<ZERO_U>(r0s, r0c, r0, hs, hc, hn, ucur, c0, c1, c2), cols, R - 1 >= 0 && R - 1 < n);
         if (owner && R - 1 >= w0 && R - 1 < w1 && x < n) store8(u1out, g, x, R - 1, u1n);
         // r1 row R - 2 from u1 rows R-3 .. R-1 and bh(R-2)
-        const Row8 r1 = residual8(u1s, u1c, u1n, bq2, x, R - 2, n);
+        const Row8 r1 = residual8(u1s, u1c, u1n, bq2, cols, R - 2 >= 0 && R - 2 < n);
         // full weighting: x pass of r1 row f = R - 2 at fine columns 2 ic, 2 ic + 1, 2 ic + 2
         const int f = R - 2;
         const float rnext = __shfl_down_sync(0xffffffffu, r1.v[0], 1);
@@ -326,7 +357,6 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
     constexpr int kRing4 = kFSlots * 32;                      // float4s
     constexpr int kWarpF4 = 2 * kRing4 + kRing4 / 2 + (ACC64 ? kFC * kRing4 / 2 + 32 : 0);
     float4 *base = fsm + w * kWarpF4;
-    const Ring4 ru{base}, rb{base + kRing4};
     float2 *re = reinterpret_cast<float2 *>(base + 2 * kRing4);          // [slot][lane]
     double *r64 = reinterpret_cast<double *>(base + 2 * kRing4 + kRing4 / 2);  // [slot][q][lane]
     float *sacc = reinterpret_cast<float *>(base + 2 * kRing4 + kRing4 / 2 + kFC * kRing4 / 2);
@@ -338,26 +368,44 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
     const int Qfirst = y0 - 2, Qlast = y1 + 1;
     // coarse row m (0-based) sits at fine row 2m + 1; fine row Q needs the
     // coarse rows mQ = floor((Q - 1) / 2) and mQ + 1
-    auto issue_e = [&](int m) {
-        const bool ok = m >= -1 && m <= gc.n && k0 >= -4 && k0 + 1 <= gc.pitch - 5;
-        cp_async8(&re[(m & (kFSlots - 1)) * 32 + lane], ok ? e + gc.off + (long)m * gc.pitch + k0 : e, ok);
-    };
-    auto issue_64 = [&](int j) {
+    const unsigned cols = col_bits(x, n);
+    // FP64 columns of this lane in the epilogue: xw + lane + 32 q, q < kFC,
+    // valid when inside the grid and produced by an owner lane
+    unsigned cols64 = 0;
 #pragma unroll
-        for (int q = 0; q < kFC; ++q) {
-            const int col = xw + lane + 32 * q;
-            const int src = (lane + 32 * q) / kFC;
-            const bool ok = j >= y0 && j < y1 && src >= 1 && src <= 30 && col >= 0 && col < n;
-            cp_async8(&r64[((j & (kFSlots - 1)) * kFC + q) * 32 + lane], ok ? u64 + (long)j * n + col : u64, ok);
-        }
-    };
+    for (int q = 0; q < kFC; ++q) {
+        const int col = xw + lane + 32 * q, src = (lane + 32 * q) / kFC;
+        if (src >= 1 && src <= 30 && col >= 0 && col < n) cols64 |= 1u << q;
+    }
+    // rings: u1 row F and bh row F - 1 for fine row F, e rows as first
+    // needed, FP64 row F - 2 (ACC64)
+    Ring4 ru, rb;
+    ru.init(base, u1, g, x, Qfirst);
+    rb.init(base + kRing4, bh, g, x, Qfirst - 1);
+    const bool e_col_ok = k0 >= -4 && k0 + 1 <= gc.pitch - 5;  // a float2 inside the coarse row's slot
+    long e_off = gc.off + (long)(((Qfirst - 1) >> 1) - 1) * gc.pitch + k0;
     int m_issued = ((Qfirst - 1) >> 1) - 1;
+    long off64 = (long)(Qfirst - 2) * n + xw + lane;
     auto issue_step = [&](int F) {  // the copies for fine row F
-        ru.issue(u1, g, x, F, lane);
-        rb.issue(bh, g, x, F - 1, lane);
+        ru.issue(lane);
+        rb.issue(lane);
         const int mneed = ((F - 1) >> 1) + 1;
-        while (m_issued < mneed) issue_e(++m_issued);
-        if (ACC64) issue_64(F - 2);
+        while (m_issued < mneed) {
+            ++m_issued;
+            e_off += gc.pitch;
+            const bool ok = e_col_ok && m_issued >= -1 && m_issued <= gc.n;
+            cp_async8(&re[(m_issued & (kFSlots - 1)) * 32 + lane], ok ? e + e_off : e, ok);
+        }
+        if (ACC64) {
+            const int j = F - 2;
+            const bool jok = j >= y0 && j < y1;
+#pragma unroll
+            for (int q = 0; q < kFC; ++q) {
+                const bool ok = jok && ((cols64 >> q) & 1u);
+                cp_async8(&r64[((j & (kFSlots - 1)) * kFC + q) * 32 + lane], ok ? u64 + off64 + 32 * q : u64, ok);
+            }
+            off64 += n;
+        }
         cp_commit();
     };
     for (int k = 0; k < kFDepth; ++k) issue_step(Qfirst + k);
@@ -394,9 +442,9 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
 #pragma unroll
             for (int k = 0; k < kFC; ++k) u2.v[k] = radd(u2.v[k], scale2<-1>(radd(vprev.v[k], vcur.v[k])));
         }
-        u2 = mask8(u2, x, Q, n);
+        u2 = mask8(u2, cols, Q >= 0 && Q < n);
         // residual of row Q - 1 and its x pairs
-        const Row8 r = residual8(u2s, u2c, u2, bQ, x, Q - 1, n);
+        const Row8 r = residual8(u2s, u2c, u2, bQ, cols, Q - 1 >= 0 && Q - 1 < n);
         const Row8 hn = xpair(r);
         // sweep of row Q - 2
         const int j = Q - 2;
@@ -408,13 +456,10 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
 #pragma unroll
                 for (int k = 0; k < kFC; ++k) sacc[kFC * lane + k] = o.v[k];
                 __syncwarp();
+                double *dst = u64 + (long)j * n + xw + lane;
 #pragma unroll
-                for (int q = 0; q < kFC; ++q) {
-                    const int col = xw + lane + 32 * q;
-                    const int src = (lane + 32 * q) / kFC;
-                    if (src >= 1 && src <= 30 && col >= 0 && col < n)
-                        u64[(long)j * n + col] = radd(a64[q], widen(sacc[lane + 32 * q]));
-                }
+                for (int q = 0; q < kFC; ++q)
+                    if ((cols64 >> q) & 1u) dst[32 * q] = radd(a64[q], widen(sacc[lane + 32 * q]));
                 __syncwarp();
             } else if (owner && x < n) {
                 store8(out, g, x, j, o);
