@@ -321,8 +321,9 @@ sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ 
 // B. interpolation + correction + sweep. Block (bx, by): warp tiles as in A,
 // fine output rows [by H, by H + H). u2 = u1 + P e; r = bh - A u2 (scaled);
 // out = u2 + W r, stored (ACC64: added to the compact FP64 array u64).
-// Rings at step Q: u1 row Q, bh row Q - 1, the coarse e rows as they are
-// first needed and (ACC64) the FP64 values of output row Q - 2.
+// Rings at step Q: u1 row Q, bh row Q - 1 and the coarse e rows as they are
+// first needed; (ACC64) the FP64 values of output row Q - 2 come by plain
+// loads issued one step earlier.
 // ---------------------------------------------------------------------------
 // x pass of the coarse row held in e2 (the lane's coarse columns k0 = x / 2,
 // k0 + 1) for its fine columns x .. x + 3: fine 2k: 0.5 (e[k-1] + e[k]);
@@ -353,13 +354,12 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
     const int x = kFOut * tile - kFC + kFC * lane;
     if (kFOut * tile >= n) return;
     // per warp: u1 and bh rings (float4), the e ring (float2) and, ACC64, the
-    // FP64 ring (kFC doubles per lane) and the staging row
-    constexpr int kRing4 = kFSlots * 32;                      // float4s
-    constexpr int kWarpF4 = 2 * kRing4 + kRing4 / 2 + (ACC64 ? kFC * kRing4 / 2 + 32 : 0);
+    // staging row of the FP64 epilogue
+    constexpr int kRing4 = kFSlots * 32;  // float4s
+    constexpr int kWarpF4 = 2 * kRing4 + kRing4 / 2 + (ACC64 ? 32 : 0);
     float4 *base = fsm + w * kWarpF4;
-    float2 *re = reinterpret_cast<float2 *>(base + 2 * kRing4);          // [slot][lane]
-    double *r64 = reinterpret_cast<double *>(base + 2 * kRing4 + kRing4 / 2);  // [slot][q][lane]
-    float *sacc = reinterpret_cast<float *>(base + 2 * kRing4 + kRing4 / 2 + kFC * kRing4 / 2);
+    float2 *re = reinterpret_cast<float2 *>(base + 2 * kRing4);  // [slot][lane]
+    float *sacc = reinterpret_cast<float *>(base + 2 * kRing4 + kRing4 / 2);
     const bool owner = lane >= 1 && lane <= 30;
     const int k0 = x / 2;
     const int xw = kFOut * tile - kFC;  // column of lane 0's first value
@@ -377,15 +377,21 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
         const int col = xw + lane + 32 * q, src = (lane + 32 * q) / kFC;
         if (src >= 1 && src <= 30 && col >= 0 && col < n) cols64 |= 1u << q;
     }
-    // rings: u1 row F and bh row F - 1 for fine row F, e rows as first
-    // needed, FP64 row F - 2 (ACC64)
+    // rings: u1 row F and bh row F - 1 for fine row F, e rows as first needed
     Ring4 ru, rb;
     ru.init(base, u1, g, x, Qfirst);
     rb.init(base + kRing4, bh, g, x, Qfirst - 1);
     const bool e_col_ok = k0 >= -4 && k0 + 1 <= gc.pitch - 5;  // a float2 inside the coarse row's slot
     long e_off = gc.off + (long)(((Qfirst - 1) >> 1) - 1) * gc.pitch + k0;
     int m_issued = ((Qfirst - 1) >> 1) - 1;
-    long off64 = (long)(Qfirst - 2) * n + xw + lane;
+    // ACC64: the FP64 values of output row j are loaded (plain loads into
+    // registers) one step before the step that updates them
+    auto load64 = [&](int j, double *dst) {
+        const bool jok = j >= y0 && j < y1;
+        const double *src = u64 + (long)j * n + xw + lane;
+#pragma unroll
+        for (int q = 0; q < kFC; ++q) dst[q] = jok && ((cols64 >> q) & 1u) ? src[32 * q] : 0.0;
+    };
     auto issue_step = [&](int F) {  // the copies for fine row F
         ru.issue(lane);
         rb.issue(lane);
@@ -396,19 +402,11 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
             const bool ok = e_col_ok && m_issued >= -1 && m_issued <= gc.n;
             cp_async8(&re[(m_issued & (kFSlots - 1)) * 32 + lane], ok ? e + e_off : e, ok);
         }
-        if (ACC64) {
-            const int j = F - 2;
-            const bool jok = j >= y0 && j < y1;
-#pragma unroll
-            for (int q = 0; q < kFC; ++q) {
-                const bool ok = jok && ((cols64 >> q) & 1u);
-                cp_async8(&r64[((j & (kFSlots - 1)) * kFC + q) * 32 + lane], ok ? u64 + off64 + 32 * q : u64, ok);
-            }
-            off64 += n;
-        }
         cp_commit();
     };
     for (int k = 0; k < kFDepth; ++k) issue_step(Qfirst + k);
+    double a64n[kFC];
+    if (ACC64) load64(Qfirst - 2, a64n);
     int mcur = 0;
     Row8 vprev = zero8(), vcur = zero8();
     Row8 u2s = zero8(), u2c = zero8();                            // u2 rows Q-2, Q-1
@@ -428,10 +426,11 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
             ++mcur;
             vcur = interp_x8(re[(mcur & (kFSlots - 1)) * 32 + lane]);
         }
-        double a64[kFC];
+        double a64[kFC];  // row Q - 2, loaded at the previous step
         if (ACC64) {
 #pragma unroll
-            for (int q = 0; q < kFC; ++q) a64[q] = r64[(((Q - 2) & (kFSlots - 1)) * kFC + q) * 32 + lane];
+            for (int q = 0; q < kFC; ++q) a64[q] = a64n[q];
+            load64(Q - 1, a64n);
         }
         issue_step(Q + kFDepth);
         // here vcur = x pass of coarse row mQ + 1, vprev = of mQ
@@ -484,7 +483,7 @@ static size_t smem_a(bool zero_u) { return (size_t)kFWarps * (zero_u ? 1 : 2) * 
 static size_t smem_b(bool acc64)
 {
     const size_t ring4 = (size_t)kFSlots * 32;
-    return (size_t)kFWarps * (2 * ring4 + ring4 / 2 + (acc64 ? kFC * ring4 / 2 + 32 : 0)) * sizeof(float4);
+    return (size_t)kFWarps * (2 * ring4 + ring4 / 2 + (acc64 ? 32 : 0)) * sizeof(float4);
 }
 
 cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *u1, float *bc, int n, const double *c,
