@@ -163,11 +163,22 @@ mg_status mg_solve_batched(mg_ctx *ctx, const void *const *b, void *const *u, do
  * dL/dc (HOST, ncoeffs doubles, summed over every sweep of every level and
  * cycle, accumulated in FP64). Requires a V cycle (gamma = 1), nu1 >= 1, N >= 8
  * and, in 3D, a context made with at most 2 weights (the 7-point M).
- * The forward is replayed once keeping the input of every sweep of every
- * level visit and each visit's right-hand side (device workspace owned by
- * the context, allocated on the first call for a given K). Synchronises. */
+ * Checkpointing: a first forward pass keeps only the cycle inputs
+ * u_1 .. u_{K-1}; each cycle is replayed from its input just before it is
+ * reversed, keeping per level the inputs of that visit's sweeps and its
+ * right-hand side. Device workspace (owned by the context, allocated on the
+ * first call for a given K, size from mg_adjoint_workspace_bytes):
+ * (K - 1) finest fields + per level (nu1 + nu2 + 5) fields (the finest
+ * nu1 + nu2 + 4, the coarsest 6) + 24 bytes per block of the reverse sweeps;
+ * e.g. 3D N = 512 FP64, K = 4, V(1,1): about 11 GB. The evaluation is
+ * recorded into a CUDA graph and replayed while b, grad_uK and grad_b_out
+ * stay the same arrays. Synchronises. */
 mg_status mg_vcycles_adjoint(mg_ctx *ctx, int K, const void *b, const void *grad_uK, void *grad_b_out,
                              double *grad_coeffs_out);
+
+/* Device bytes of the workspace mg_vcycles_adjoint uses for K cycles on this
+ * context (HOST *bytes_out). No GPU work. */
+mg_status mg_adjoint_workspace_bytes(mg_ctx *ctx, int K, unsigned long long *bytes_out);
 
 /* ---------------------------------------------------------------------- */
 /* single operators on one level (each step of the cycle, for checking)    */

@@ -52,6 +52,7 @@ SIGNATURES = {
     "mg_test_arm_wait_expiry": (_I, [_I]),
     "mg_measure_fp64_rate": (_I, [_I, _DP, _DP]),
     "mg_op_sweep_restrict": (_I, [_I, _I, _I, _DP, _I, _P, _P, _P, _P, _P]),
+    "mg_adjoint_workspace_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_ulonglong)]),
     "mg_op_prolong_sweep": (_I, [_I, _I, _I, _DP, _I, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -236,6 +237,12 @@ class Solver:
                                         _dev_ptr(grad_uK, self.dtype, self.shape, "grad_uK"),
                                         ctypes.c_void_p(gb.data_ptr()), gc), "mg_vcycles_adjoint")
         return gb, np.array(list(gc))
+
+    def adjoint_workspace_bytes(self, K: int) -> int:
+        """Device bytes mg_vcycles_adjoint uses for K cycles on this context."""
+        out = ctypes.c_ulonglong(0)
+        _check(lib().mg_adjoint_workspace_bytes(self._ctx, int(K), ctypes.byref(out)), "mg_adjoint_workspace_bytes")
+        return int(out.value)
 
     def vcycle(self, u, b):
         """One cycle in place on u (asynchronous on the solver's stream)."""

@@ -2,10 +2,8 @@
 //
 // Forward map (Sec. 4 cycle in the scaled form): u_K = K V(nu1, nu2) cycles
 // from u_0 = 0 for right-hand side b and omega-folded weights c. Given
-// g = dL/du_K this computes dL/db and dL/dc_j by replaying the forward once
-// with every sweep input kept (one field per sweep of every level visit plus
-// the visit's restricted right-hand side) and applying, in reverse order,
-// the transpose of each operator:
+// g = dL/du_K this computes dL/db and dL/dc_j by applying, in reverse
+// order, the transpose of each operator of the cycles:
 //   sweep    u' = u + W rh, rh = bh - Ah u  ->  t = W g',  g = g' - Ah t,
 //            gbh += t,  gc_j += <N_j g', rh>          (W, Ah, N_j symmetric)
 //   restrict bh_c = 4 R (bh - Ah u)         ->  t = (4/2^d) P g_c,
@@ -13,9 +11,20 @@
 //   correct  u' = u + P e                   ->  g_e = P^T g' = 2^d R g'
 //   solve    e = A0^{-1} bh                 ->  g_bh = A0^{-1} g_e
 //   load     bh_0 = h^2 b                   ->  g_b = h^2 g_bh_0
-// Note g - Ah t = fma(-2d, t, g) + (neighbour sum of t): the residual kernel
-// with u := t, bh := g. Coefficient gradients are accumulated in FP64 with a
-// fixed-order reduction after every adjoint sweep.
+//
+// Checkpoints: only the cycle inputs u_1 .. u_{K-1} (finest level) are kept
+// from a first forward pass; before cycle k is reversed, it is replayed from
+// its input, keeping for every level the inputs of its sweeps and its
+// right-hand side (one cycle's worth), so the workspace grows with the
+// number of levels, not with K (the sweeps are computed twice).
+//
+// The transposed sweep is one marching kernel (t = W g on the tile and a
+// one-point halo, then g' = g - Ah t, gbh += t and the per-block partials of
+// <g, rh>, <N_1 g, rh>, <N_2 g, rh>, in the same pass; g' goes to a second
+// buffer, since neighbouring tiles read g). The coefficient partials of all
+// reverse sweeps are reduced once, in a fixed order, at the end. The whole
+// evaluation (forward, replays, reverse, reduction) is recorded into one
+// CUDA graph, replayed while the caller's arrays stay the same.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -36,59 +45,200 @@ __device__ __forceinline__ T ld(const T *a, int n, int x, int y, int z)
     return a[((size_t)z * n + y) * n + x];
 }
 
-// t = W g at every point; per block: sum g rh, sum (N_1 g) rh, sum (N_2 g) rh
-// with rh = bh - Ah u_in (u_in == nullptr: zero).
-template <typename T, int D>
-__global__ void __launch_bounds__(256)
-adj_sweep_stage1(const T *__restrict__ g, const T *__restrict__ u, const T *__restrict__ b, bool unscaled,
-                 T *__restrict__ t, int n, T c0, T c1, T c2, int hk, double *__restrict__ partials)
+// ---------------------------------------------------------------------------
+// fused transposed sweep, 3D (7-point M and A). Block: 32 x 8 output columns
+// marching over the planes [z0, z1); per step q: (A) g plane q on the tile
+// plus a 2-point halo and u plane q on the tile plus a 1-point halo into
+// shared rings; (B) t = W g of plane q - 1 on the tile plus a 1-point halo,
+// and the partials of plane q - 1 at the tile; (C) g' and gbh of plane q - 2
+// at the tile. Formulas (zero outside the interior):
+//   E  = ((g_W + g_E) + (g_S + g_N)) + (g_D + g_U)
+//   t  = fma(c1, E, c0 g)
+//   rh = fma(-6, u, bh) + (((u_W + u_E) + (u_S + u_N)) + (u_D + u_U))   (u = 0: bh)
+//   g' = fma(-6, t, g) + (((t_W + t_E) + (t_S + t_N)) + (t_D + t_U)),  gbh += t
+//   partials: sum g rh, sum E rh (FP64)
+// ---------------------------------------------------------------------------
+constexpr int kAX = 32, kAY = 8, kAThreads = kAX * kAY;
+constexpr int kAGX = kAX + 4, kAGY = kAY + 4;  // g region (2-point halo)
+constexpr int kATX = kAX + 2, kATY = kAY + 2;  // t and u region (1-point halo)
+
+template <typename T, bool ZERO_U, bool UNSCALED>
+__global__ void __launch_bounds__(kAThreads)
+adj_sweep3d_kernel(const T *__restrict__ g, T *__restrict__ gout, const T *__restrict__ u, const T *__restrict__ b,
+                   T *__restrict__ gbh, int n, int Z, T c0, T c1, int hk, double *__restrict__ partials)
 {
-    const size_t np = D == 2 ? (size_t)n * n : (size_t)n * n * n;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < np; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % n), y = (int)((i / n) % n), z = D == 2 ? 0 : (int)(i / ((size_t)n * n));
-        const T gp = g[i];
-        T E, C = T(0), s = T(0);
-        if (D == 2) {
-            E = radd(radd(ld(g, n, x - 1, y, 0), ld(g, n, x + 1, y, 0)), radd(ld(g, n, x, y - 1, 0), ld(g, n, x, y + 1, 0)));
-            C = radd(radd(ld(g, n, x - 1, y - 1, 0), ld(g, n, x + 1, y - 1, 0)),
-                     radd(ld(g, n, x - 1, y + 1, 0), ld(g, n, x + 1, y + 1, 0)));
-            if (u)
-                s = radd(radd(ld(u, n, x - 1, y, 0), ld(u, n, x + 1, y, 0)), radd(ld(u, n, x, y - 1, 0), ld(u, n, x, y + 1, 0)));
-            t[i] = rfma(c2, C, rfma(c1, E, rmul(c0, gp)));
-        } else {
-            E = radd(radd(radd(ld(g, n, x - 1, y, z), ld(g, n, x + 1, y, z)), radd(ld(g, n, x, y - 1, z), ld(g, n, x, y + 1, z))),
-                     radd(ld(g, n, x, y, z - 1), ld(g, n, x, y, z + 1)));
-            if (u)
-                s = radd(radd(radd(ld(u, n, x - 1, y, z), ld(u, n, x + 1, y, z)), radd(ld(u, n, x, y - 1, z), ld(u, n, x, y + 1, z))),
-                         radd(ld(u, n, x, y, z - 1), ld(u, n, x, y, z + 1)));
-            t[i] = rfma(c1, E, rmul(c0, gp));
+    __shared__ T sg[4][kAGX * kAGY];
+    __shared__ T st[3][kATX * kATY];
+    __shared__ T su[ZERO_U ? 1 : 3][kATX * kATY];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kAX, y0 = blockIdx.y * kAY;
+    const int z0 = blockIdx.z * Z, z1 = min(z0 + Z, n);
+    const int ox = tid % kAX, oy = tid / kAX;  // the thread's output column
+    const int X = x0 + ox, Y = y0 + oy;
+    const bool own = X < n && Y < n;
+    const int it = (oy + 1) * kATX + (ox + 1);  // its index in the t / u region
+    const int ig = (oy + 2) * kAGX + (ox + 2);  // in the g region
+    const size_t plane = (size_t)n * n;
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = z0 - 2; q <= z1 + 1; ++q) {
+        // A. g plane q (2-point halo), u plane q (1-point halo)
+        const bool qin = q >= 0 && q < n;
+        for (int i = tid; i < kAGX * kAGY; i += kAThreads) {
+            const int gx = x0 - 2 + i % kAGX, gy = y0 - 2 + i / kAGX;
+            sg[q & 3][i] = qin && gx >= 0 && gx < n && gy >= 0 && gy < n ? g[q * plane + (size_t)gy * n + gx] : T(0);
         }
-        T bb = b[i];
-        if (unscaled) bb = scale2(bb, hk);
-        const T rh = u ? radd(rfma(T(-2 * D), u[i], bb), s) : bb;
-        a0 = fma((double)gp, (double)rh, a0);
-        a1 = fma((double)E, (double)rh, a1);
-        a2 = fma((double)C, (double)rh, a2);
+        if (!ZERO_U)
+            for (int i = tid; i < kATX * kATY; i += kAThreads) {
+                const int ux = x0 - 1 + i % kATX, uy = y0 - 1 + i / kATX;
+                su[(q + 3) % 3][i] = qin && ux >= 0 && ux < n && uy >= 0 && uy < n ? u[q * plane + (size_t)uy * n + ux]
+                                                                                  : T(0);
+            }
+        __syncthreads();
+        // B. t of plane p = q - 1 on the 1-point halo region
+        const int p = q - 1;
+        if (p >= z0 - 1) {
+            const bool pin = p >= 0 && p < n;
+            const T *gm = sg[(p + 3) & 3], *gc = sg[p & 3], *gp = sg[(p + 1) & 3];
+            for (int k = 0; k < 2; ++k) {
+                // the thread's own column first, then the 84 halo points
+                int tx, ty;
+                if (k == 0) {
+                    tx = ox + 1;
+                    ty = oy + 1;
+                } else {
+                    if (tid >= 2 * kATX + 2 * kAY) break;
+                    const int h = tid;
+                    if (h < kATX) { tx = h; ty = 0; }
+                    else if (h < 2 * kATX) { tx = h - kATX; ty = kATY - 1; }
+                    else if (h < 2 * kATX + kAY) { tx = 0; ty = h - 2 * kATX + 1; }
+                    else { tx = kATX - 1; ty = h - 2 * kATX - kAY + 1; }
+                }
+                const int j = (ty + 1) * kAGX + (tx + 1);
+                const T E = radd(radd(radd(gc[j - 1], gc[j + 1]), radd(gc[j - kAGX], gc[j + kAGX])), radd(gm[j], gp[j]));
+                const T tv = rfma(c1, E, rmul(c0, gc[j]));
+                const int Xt = x0 - 1 + tx, Yt = y0 - 1 + ty;
+                st[(p + 3) % 3][ty * kATX + tx] = pin && Xt >= 0 && Xt < n && Yt >= 0 && Yt < n ? tv : T(0);
+                if (k == 0 && own && p >= z0 && p < z1) {
+                    T bb = b[p * plane + (size_t)Y * n + X];
+                    if (UNSCALED) bb = scale2(bb, hk);
+                    T rh = bb;
+                    if (!ZERO_U) {
+                        const T *uc = su[(p + 3) % 3];
+                        const T s = radd(radd(radd(uc[it - 1], uc[it + 1]), radd(uc[it - kATX], uc[it + kATX])),
+                                         radd(su[(p + 2) % 3][it], su[(p + 4) % 3][it]));
+                        rh = radd(rfma(T(-6), uc[it], bb), s);
+                    }
+                    a0 = fma((double)gc[j], (double)rh, a0);
+                    a1 = fma((double)E, (double)rh, a1);
+                }
+            }
+        }
+        __syncthreads();
+        // C. g' and gbh of plane r = q - 2 at the tile
+        const int r = q - 2;
+        if (own && r >= z0 && r < z1) {
+            const T *tc = st[(r + 3) % 3];
+            const T tv = tc[it];
+            const T s = radd(radd(radd(tc[it - 1], tc[it + 1]), radd(tc[it - kATX], tc[it + kATX])),
+                             radd(st[(r + 2) % 3][it], st[(r + 4) % 3][it]));
+            const size_t o = r * plane + (size_t)Y * n + X;
+            gout[o] = radd(rfma(T(-6), tv, sg[r & 3][ig]), s);
+            gbh[o] = radd(gbh[o], tv);
+        }
     }
-    __shared__ double red[3][256 / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        red[0][w] = a0;
-        red[1][w] = a1;
-        red[2][w] = a2;
-    }
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    block_sum_store<kAThreads>(a0, &partials[3 * bid]);
     __syncthreads();
-    if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int k = 0; k < 256 / 32; ++k) s += red[threadIdx.x][k];
-        partials[3 * blockIdx.x + threadIdx.x] = s;
+    block_sum_store<kAThreads>(a1, &partials[3 * bid + 1]);
+    if (tid == 0) partials[3 * bid + 2] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// fused transposed sweep, 2D (9-point M, 5-point A): 256 output columns
+// marching over rows [y0, y1); the same three phases per row step:
+//   E  = (g_W + g_E) + (g_S + g_N),  C = (g_SW + g_SE) + (g_NW + g_NE)
+//   t  = fma(c2, C, fma(c1, E, c0 g))
+//   rh = fma(-4, u, bh) + ((u_W + u_E) + (u_S + u_N))          (u = 0: bh)
+//   g' = fma(-4, t, g) + ((t_W + t_E) + (t_S + t_N)),  gbh += t
+//   partials: sum g rh, sum E rh, sum C rh (FP64)
+// ---------------------------------------------------------------------------
+constexpr int kA2X = 256;
+constexpr int kA2G = kA2X + 4, kA2T = kA2X + 2;
+
+template <typename T, bool ZERO_U, bool UNSCALED>
+__global__ void __launch_bounds__(kA2X)
+adj_sweep2d_kernel(const T *__restrict__ g, T *__restrict__ gout, const T *__restrict__ u, const T *__restrict__ b,
+                   T *__restrict__ gbh, int n, int H, T c0, T c1, T c2, int hk, double *__restrict__ partials)
+{
+    __shared__ T sg[4][kA2G];
+    __shared__ T st[3][kA2T];
+    __shared__ T su[ZERO_U ? 1 : 3][kA2T];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kA2X;
+    const int y0 = blockIdx.y * H, y1 = min(y0 + H, n);
+    const int X = x0 + tid;
+    const bool own = X < n;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int q = y0 - 2; q <= y1 + 1; ++q) {
+        const bool qin = q >= 0 && q < n;
+        for (int i = tid; i < kA2G; i += kA2X) {
+            const int gx = x0 - 2 + i;
+            sg[q & 3][i] = qin && gx >= 0 && gx < n ? g[(size_t)q * n + gx] : T(0);
+        }
+        if (!ZERO_U)
+            for (int i = tid; i < kA2T; i += kA2X) {
+                const int ux = x0 - 1 + i;
+                su[(q + 3) % 3][i] = qin && ux >= 0 && ux < n ? u[(size_t)q * n + ux] : T(0);
+            }
+        __syncthreads();
+        const int p = q - 1;
+        if (p >= y0 - 1) {
+            const bool pin = p >= 0 && p < n;
+            const T *gm = sg[(p + 3) & 3], *gc = sg[p & 3], *gp = sg[(p + 1) & 3];
+            for (int k = 0; k < 2; ++k) {
+                int tx;
+                if (k == 0) tx = tid + 1;
+                else if (tid < 2) tx = tid == 0 ? 0 : kA2T - 1;
+                else break;
+                const int j = tx + 1;
+                const T E = radd(radd(gc[j - 1], gc[j + 1]), radd(gm[j], gp[j]));
+                const T C = radd(radd(gm[j - 1], gm[j + 1]), radd(gp[j - 1], gp[j + 1]));
+                const T tv = rfma(c2, C, rfma(c1, E, rmul(c0, gc[j])));
+                const int Xt = x0 - 1 + tx;
+                st[(p + 3) % 3][tx] = pin && Xt >= 0 && Xt < n ? tv : T(0);
+                if (k == 0 && own && p >= y0 && p < y1) {
+                    T bb = b[(size_t)p * n + X];
+                    if (UNSCALED) bb = scale2(bb, hk);
+                    T rh = bb;
+                    if (!ZERO_U) {
+                        const T *uc = su[(p + 3) % 3];
+                        const T s = radd(radd(uc[tx - 1], uc[tx + 1]), radd(su[(p + 2) % 3][tx], su[(p + 4) % 3][tx]));
+                        rh = radd(rfma(T(-4), uc[tx], bb), s);
+                    }
+                    a0 = fma((double)gc[j], (double)rh, a0);
+                    a1 = fma((double)E, (double)rh, a1);
+                    a2 = fma((double)C, (double)rh, a2);
+                }
+            }
+        }
+        __syncthreads();
+        const int r = q - 2;
+        if (own && r >= y0 && r < y1) {
+            const T *tc = st[(r + 3) % 3];
+            const int it = tid + 1;
+            const T tv = tc[it];
+            const T s = radd(radd(tc[it - 1], tc[it + 1]), radd(st[(r + 2) % 3][it], st[(r + 4) % 3][it]));
+            const size_t o = (size_t)r * n + X;
+            gout[o] = radd(rfma(T(-4), tv, sg[r & 3][it + 1]), s);
+            gbh[o] = radd(gbh[o], tv);
+        }
     }
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum_store<kA2X>(a0, &partials[3 * bid]);
+    __syncthreads();
+    block_sum_store<kA2X>(a1, &partials[3 * bid + 1]);
+    __syncthreads();
+    block_sum_store<kA2X>(a2, &partials[3 * bid + 2]);
 }
 
 // g = g - Ah t (= fma(-2d, t, g) + neighbour sum of t);  gbh += t
@@ -176,19 +326,18 @@ adj_interp(const T *__restrict__ e, T *__restrict__ out, int n, T scale)
     }
 }
 
-// acc[j] += sum over blocks of partials[3 b + j]: thread t sums the blocks
-// t, t + 256, ... in that order, then a fixed shuffle/warp tree (the same
-// order every run, independent of timing)
-__global__ void __launch_bounds__(256) adj_accumulate(const double *__restrict__ partials, int nblocks,
-                                                      double *__restrict__ acc)
+// acc[j] = sum over all nblocks block partials partials[3 b + j], in a fixed
+// order: thread t sums the blocks t, t + 256, ..., then a fixed warp tree
+__global__ void __launch_bounds__(256) adj_reduce(const double *__restrict__ partials, long nblocks,
+                                                  double *__restrict__ acc)
 {
     __shared__ double tot;
     for (int j = 0; j < 3; ++j) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[3 * b + j];
+        for (long b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[3 * b + j];
         block_sum_store<256>(s, &tot);
         __syncthreads();
-        if (threadIdx.x == 0) acc[j] += tot;
+        if (threadIdx.x == 0) acc[j] = tot;
         __syncthreads();
     }
 }
@@ -207,10 +356,37 @@ static int grid_for(size_t np)
 
 static size_t npts(int d, int n) { return d == 2 ? (size_t)n * n : (size_t)n * n * n; }
 
+// launch shape of the fused transposed sweep on a level with n points per axis
+struct AdjGrid {
+    dim3 grid;
+    int Z;  // planes (3D) or rows (2D) per block
+};
+static AdjGrid adj_grid(int d, int n)
+{
+    AdjGrid a;
+    if (d == 3) {
+        const int bx = (n + kAX - 1) / kAX, by = (n + kAY - 1) / kAY;
+        a.Z = chunk_rows(bx * by, n, 4 * num_sms(), 4, 64);
+        a.grid = dim3(bx, by, (n + a.Z - 1) / a.Z);
+    } else {
+        const int bx = (n + kA2X - 1) / kA2X;
+        a.Z = chunk_rows(bx, n, 4 * num_sms(), 8, 128);
+        a.grid = dim3(bx, (n + a.Z - 1) / a.Z, 1);
+    }
+    return a;
+}
+static long adj_blocks(int d, int n)
+{
+    const AdjGrid a = adj_grid(d, n);
+    return (long)a.grid.x * a.grid.y * a.grid.z;
+}
+
 void free_adjoint(mg_ctx *c)
 {
     if (!c->adj) return;
+    if (c->adj->graph) cudaGraphExecDestroy(c->adj->graph);
     for (void *p : c->adj->owned) cudaFree(p);
+    if (c->adj->h_acc) cudaFreeHost(c->adj->h_acc);
     delete c->adj;
     c->adj = nullptr;
 }
@@ -222,6 +398,8 @@ struct Adjoint {
     mg_ctx *c;
     AdjointWork *w;
     const T *b;  // caller's unscaled finest right-hand side
+    long pofs = 0;  // next free block slot of the coefficient partials
+    int cur[32] = {0};  // which of the two gradient buffers G[2l], G[2l+1] is current
     cudaError_t err = cudaSuccess;
 
     bool ok(cudaError_t e)
@@ -230,10 +408,11 @@ struct Adjoint {
         return err == cudaSuccess;
     }
     int n(int l) const { return c->n[l]; }
-    const T *bh(int k, int l) const { return l == 0 ? b : (const T *)w->bh[k][l]; }
-    T *slot(int k, int l, int s) const { return (T *)w->work[k][l][s]; }
+    const T *bh(int l) const { return l == 0 ? b : (const T *)w->bh[l]; }
+    T *slot(int l, int s) const { return (T *)w->sw[l][s]; }
+    T *G(int l) const { return (T *)w->G[2 * l + cur[l]]; }
+    T *G2(int l) const { return (T *)w->G[2 * l + 1 - cur[l]]; }
 
-    // ---- forward replay with checkpoints ---------------------------------
     void solve_coarsest(const T *rhs, T *x)
     {
         TailArgs a;
@@ -246,93 +425,108 @@ struct Adjoint {
         ok(launch_tail<T>(a, c->s));
     }
 
-    // visit of level l in cycle k with input `in` (nullptr = zero); the output
-    // is left in the visit's last slot
-    T *fwd_visit(int k, int l, const T *in)
-    {
-        const int nn = n(l);
-        if (nn == 3) {
-            T *x = slot(k, l, 0);
-            solve_coarsest(bh(k, l), x);
-            return x;
-        }
-        const bool unsc = l == 0;
-        const T *cur = in;
-        for (int s = 0; s < c->nu1; ++s) {
-            T *out = slot(k, l, s);
-            if (!ok(op_sweep_any(cur, bh(k, l), unsc, out, nn))) return nullptr;
-            cur = out;
-        }
-        T *ua = slot(k, l, c->nu1 - 1);
-        if (!ok(c->d == 2 ? launch_resrestrict2d<T>(ua, bh(k, l), unsc, (T *)w->bh[k][l + 1], nn, c->s)
-                          : launch_resrestrict3d<T>(ua, bh(k, l), unsc, (T *)w->bh[k][l + 1], nn, c->s)))
-            return nullptr;
-        const T *e = fwd_visit(k, l + 1, nullptr);
-        if (!e) return nullptr;
-        if (!ok(c->d == 2 ? launch_prolong2d<T>(e, ua, nn, c->s) : launch_prolong3d<T>(e, ua, nn, c->s)))
-            return nullptr;
-        cur = ua;
-        for (int s = 0; s < c->nu2; ++s) {
-            T *out = slot(k, l, c->nu1 + s);
-            if (!ok(op_sweep_any(cur, bh(k, l), unsc, out, nn))) return nullptr;
-            cur = out;
-        }
-        return (T *)cur;
-    }
-
     cudaError_t op_sweep_any(const T *u, const T *rhs, bool unsc, T *out, int nn)
     {
         return c->d == 2 ? launch_sweep2d<T>(u, rhs, unsc, out, nn, c->c, nullptr, c->s)
                          : launch_sweep3d<T>(u, rhs, unsc, out, nn, c->c, nullptr, c->s);
     }
 
-    // ---- reverse ---------------------------------------------------------
-    void adj_sweep(int k, int l, const T *u_in)
+    // ---- forward: visit of level l with input `in` (nullptr = zero); the
+    // sweep outputs go to the level's slots, the output is the last slot ----
+    T *fwd_visit(int l, const T *in)
     {
         const int nn = n(l);
-        const size_t np = npts(c->d, nn);
-        const int grid = grid_for(np);
-        const int hk = h2_exponent(nn);
-        T *G = (T *)w->G[l], *Tt = (T *)w->T[l], *GB = (T *)w->GB[l];
-        if (c->d == 2)
-            adj_sweep_stage1<T, 2><<<grid, 256, 0, c->s>>>(G, u_in, bh(k, l), l == 0, Tt, nn, T(c->c[0]),
-                                                           T(c->c[1]), T(c->c[2]), hk, w->partials);
-        else
-            adj_sweep_stage1<T, 3><<<grid, 256, 0, c->s>>>(G, u_in, bh(k, l), l == 0, Tt, nn, T(c->c[0]),
-                                                           T(c->c[1]), T(0), hk, w->partials);
-        adj_accumulate<<<1, 256, 0, c->s>>>(w->partials, grid, w->acc);
-        if (c->d == 2)
-            adj_stage2<T, 2><<<grid, 256, 0, c->s>>>(G, Tt, GB, nn);
-        else
-            adj_stage2<T, 3><<<grid, 256, 0, c->s>>>(G, Tt, GB, nn);
-        count_launch(3);
-        ok(cudaGetLastError());
+        if (nn == 3) {
+            T *x = slot(l, 0);
+            solve_coarsest(bh(l), x);
+            return x;
+        }
+        const bool unsc = l == 0;
+        const T *cur_u = in;
+        for (int s = 0; s < c->nu1; ++s) {
+            T *out = slot(l, s);
+            if (!ok(op_sweep_any(cur_u, bh(l), unsc, out, nn))) return nullptr;
+            cur_u = out;
+        }
+        T *ua = slot(l, c->nu1 - 1);
+        if (!ok(c->d == 2 ? launch_resrestrict2d<T>(ua, bh(l), unsc, (T *)w->bh[l + 1], nn, c->s)
+                          : launch_resrestrict3d<T>(ua, bh(l), unsc, (T *)w->bh[l + 1], nn, c->s)))
+            return nullptr;
+        const T *e = fwd_visit(l + 1, nullptr);
+        if (!e) return nullptr;
+        // the correction is applied in place: the transposes need the inputs
+        // of the sweeps, and the last pre-sweep's output is not one of them
+        if (!ok(c->d == 2 ? launch_prolong2d<T>(e, ua, nn, c->s) : launch_prolong3d<T>(e, ua, nn, c->s)))
+            return nullptr;
+        cur_u = ua;
+        for (int s = 0; s < c->nu2; ++s) {
+            T *out = slot(l, c->nu1 + s);
+            if (!ok(op_sweep_any(cur_u, bh(l), unsc, out, nn))) return nullptr;
+            cur_u = out;
+        }
+        return (T *)cur_u;
     }
 
-    // on entry w->G[l] = gradient w.r.t. the visit's output; on exit
-    // w->G[l] = gradient w.r.t. its input and w->GB[l] has received the
-    // gradient w.r.t. its right-hand side
-    void rev_visit(int k, int l, const T *in)
+    // input of sweep s (pre-sweeps 0 .. nu1-1, then post-sweeps) of the
+    // visit of level l (nullptr: zero); the first post-sweep's input is the
+    // corrected field, which replaced the last pre-sweep's output
+    const T *sweep_in(int l, int s, const T *in) const { return s == 0 ? in : slot(l, s - 1); }
+
+    // ---- reverse -----------------------------------------------------------
+    void adj_sweep(int l, const T *u_in)
+    {
+        const int nn = n(l);
+        const AdjGrid a = adj_grid(c->d, nn);
+        const int hk = h2_exponent(nn);
+        const bool unsc = l == 0;
+        double *part = w->partials + 3 * pofs;
+        pofs += (long)a.grid.x * a.grid.y * a.grid.z;
+        const T *gin = G(l);
+        T *gout = G2(l), *gbh = (T *)w->GB[l];
+        const T *bb = bh(l);
+        const T c0 = T(c->c[0]), c1 = T(c->c[1]), c2 = T(c->c[2]);
+#define MG_ADJ3(ZU, UN)                                                                                               \
+    adj_sweep3d_kernel<T, ZU, UN><<<a.grid, kAThreads, 0, c->s>>>(gin, gout, u_in, bb, gbh, nn, a.Z, c0, c1, hk, part)
+#define MG_ADJ2(ZU, UN)                                                                                               \
+    adj_sweep2d_kernel<T, ZU, UN><<<a.grid, kA2X, 0, c->s>>>(gin, gout, u_in, bb, gbh, nn, a.Z, c0, c1, c2, hk, part)
+        if (c->d == 3) {
+            if (u_in) { if (unsc) MG_ADJ3(false, true); else MG_ADJ3(false, false); }
+            else { if (unsc) MG_ADJ3(true, true); else MG_ADJ3(true, false); }
+        } else {
+            if (u_in) { if (unsc) MG_ADJ2(false, true); else MG_ADJ2(false, false); }
+            else { if (unsc) MG_ADJ2(true, true); else MG_ADJ2(true, false); }
+        }
+#undef MG_ADJ3
+#undef MG_ADJ2
+        count_launch(1);
+        ok(cudaGetLastError());
+        cur[l] = 1 - cur[l];
+    }
+
+    // on entry G(l) = gradient w.r.t. the visit's output; on exit G(l) =
+    // gradient w.r.t. its input and GB[l] has received the gradient w.r.t.
+    // its right-hand side
+    void rev_visit(int l, const T *in)
     {
         const int nn = n(l);
         const size_t np = npts(c->d, nn);
         if (nn == 3) {
-            solve_coarsest((const T *)w->G[l], (T *)w->GB[l]);
-            ok(cudaMemsetAsync(w->G[l], 0, np * sizeof(T), c->s));
+            solve_coarsest(G(l), (T *)w->GB[l]);
+            ok(cudaMemsetAsync(G(l), 0, np * sizeof(T), c->s));
             return;
         }
-        for (int s = c->nu2 - 1; s >= 0; --s) adj_sweep(k, l, slot(k, l, c->nu1 - 1 + s));
+        for (int s = c->nu2 - 1; s >= 0; --s) adj_sweep(l, sweep_in(l, c->nu1 + s, in));
         // interpolation + correction: the child's output gradient is P^T g
         const int ncoarse = (nn - 1) / 2;
         const size_t npc = npts(c->d, ncoarse);
         const int gridc = grid_for(npc);
         if (c->d == 2)
-            adj_fw<T, 2><<<gridc, 256, 0, c->s>>>((const T *)w->G[l], (T *)w->G[l + 1], nn, T(0.25));
+            adj_fw<T, 2><<<gridc, 256, 0, c->s>>>(G(l), G(l + 1), nn, T(0.25));
         else
-            adj_fw<T, 3><<<gridc, 256, 0, c->s>>>((const T *)w->G[l], (T *)w->G[l + 1], nn, T(0.125));
+            adj_fw<T, 3><<<gridc, 256, 0, c->s>>>(G(l), G(l + 1), nn, T(0.125));
         count_launch(1);
         ok(cudaMemsetAsync(w->GB[l + 1], 0, npc * sizeof(T), c->s));
-        rev_visit(k, l + 1, nullptr);
+        rev_visit(l + 1, nullptr);
         // restriction: t = (4/2^d) P g_bh_child; g -= Ah t; gbh += t
         const int grid = grid_for(np);
         if (c->d == 2)
@@ -340,12 +534,45 @@ struct Adjoint {
         else
             adj_interp<T, 3><<<grid, 256, 0, c->s>>>((const T *)w->GB[l + 1], (T *)w->T[l], nn, T(0.5));
         if (c->d == 2)
-            adj_stage2<T, 2><<<grid, 256, 0, c->s>>>((T *)w->G[l], (const T *)w->T[l], (T *)w->GB[l], nn);
+            adj_stage2<T, 2><<<grid, 256, 0, c->s>>>(G(l), (const T *)w->T[l], (T *)w->GB[l], nn);
         else
-            adj_stage2<T, 3><<<grid, 256, 0, c->s>>>((T *)w->G[l], (const T *)w->T[l], (T *)w->GB[l], nn);
+            adj_stage2<T, 3><<<grid, 256, 0, c->s>>>(G(l), (const T *)w->T[l], (T *)w->GB[l], nn);
         count_launch(2);
         ok(cudaGetLastError());
-        for (int s = c->nu1 - 1; s >= 0; --s) adj_sweep(k, l, s == 0 ? in : slot(k, l, s - 1));
+        for (int s = c->nu1 - 1; s >= 0; --s) adj_sweep(l, sweep_in(l, s, in));
+    }
+
+    // the whole evaluation for dL/du_K = g_uK: forward to the checkpoints,
+    // then per cycle (last first) a replay and the reverse
+    cudaError_t record_all(int K, const T *g_uK, T *g_b)
+    {
+        const size_t np0 = npts(c->d, c->n[0]);
+        const size_t bytes0 = np0 * sizeof(T);
+        // forward: u_1 .. u_{K-1}
+        const T *u = nullptr;
+        for (int k = 0; k + 1 < K; ++k) {
+            const T *out = fwd_visit(0, u);
+            if (!out) return err;
+            if (!ok(cudaMemcpyAsync(w->ck[k + 1], out, bytes0, cudaMemcpyDeviceToDevice, c->s))) return err;
+            u = (const T *)w->ck[k + 1];
+        }
+        for (int l = 0; l < c->L; ++l) cur[l] = 0;
+        if (!ok(cudaMemcpyAsync(G(0), g_uK, bytes0, cudaMemcpyDeviceToDevice, c->s)) ||
+            !ok(cudaMemsetAsync(w->GB[0], 0, bytes0, c->s)))
+            return err;
+        for (int k = K - 1; k >= 0; --k) {
+            const T *in = k == 0 ? nullptr : (const T *)w->ck[k];
+            if (!fwd_visit(0, in)) return err;  // replay: the sweep inputs of cycle k
+            rev_visit(0, in);
+            if (err) return err;
+        }
+        adj_reduce<<<1, 256, 0, c->s>>>(w->partials, pofs, w->acc);
+        const T h2 = T(1.0 / ((double)c->N * c->N));
+        adj_scale<T><<<grid_for(np0), 256, 0, c->s>>>((const T *)w->GB[0], g_b, np0, h2);
+        count_launch(2);
+        if (!ok(cudaGetLastError())) return err;
+        ok(cudaMemcpyAsync(w->h_acc, w->acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+        return err;
     }
 };
 
@@ -353,6 +580,30 @@ struct Adjoint {
 }  // namespace mg
 
 using namespace mg;
+
+// blocks of coefficient partials written by the reverse of K cycles
+static long adj_partial_blocks(const mg_ctx *c, int K)
+{
+    long per_cycle = 0;
+    for (int l = 0; l < c->L; ++l)
+        if (c->n[l] > 3) per_cycle += (long)(c->nu1 + c->nu2) * adj_blocks(c->d, c->n[l]);
+    return per_cycle * K;
+}
+
+// device bytes of the adjoint workspace for K cycles (see AdjointWork)
+static unsigned long long adj_bytes(const mg_ctx *c, int K)
+{
+    const size_t es = c->esize;
+    unsigned long long total = (unsigned long long)(K - 1) * npts(c->d, c->n[0]) * es;
+    const int slots = c->nu1 + c->nu2;
+    for (int l = 0; l < c->L; ++l) {
+        const unsigned long long f = (unsigned long long)npts(c->d, c->n[l]) * es;
+        total += f * ((c->n[l] == 3 ? 1 : slots) + (l >= 1 ? 1 : 0) + 4);
+    }
+    const long nb = adj_partial_blocks(c, K);
+    total += (unsigned long long)3 * (nb > 0 ? nb : 1) * sizeof(double) + 3 * sizeof(double);
+    return total;
+}
 
 static mg_status adj_alloc(mg_ctx *c, int K)
 {
@@ -369,33 +620,46 @@ static mg_status adj_alloc(mg_ctx *c, int K)
             return nullptr;
         }
         w->owned.push_back(p);
+        w->bytes += bytes;
         return p;
     };
     const size_t es = c->esize;
+    const size_t bytes0 = npts(c->d, c->n[0]) * es;
+    w->ck.assign(K, nullptr);
+    for (int k = 1; k < K; ++k)
+        if (!(w->ck[k] = alloc(bytes0))) return MG_ENOMEM;
+    // per level: the sweep outputs of one visit (nu1 + nu2 fields; the
+    // coarsest: its solution), the right-hand side (level >= 1), two
+    // gradient buffers, the gradient of the right-hand side and a scratch
+    // field
     const int slots = c->nu1 + c->nu2;
-    w->work.assign(K, std::vector<std::vector<void *>>(c->L));
-    w->bh.assign(K, std::vector<void *>(c->L, nullptr));
-    for (int k = 0; k < K; ++k)
-        for (int l = 0; l < c->L; ++l) {
-            const size_t bytes = npts(c->d, c->n[l]) * es;
-            const int ns = c->n[l] == 3 ? 1 : slots;
-            for (int s = 0; s < ns; ++s) {
-                void *p = alloc(bytes);
-                if (!p) return MG_ENOMEM;
-                w->work[k][l].push_back(p);
-            }
-            if (l >= 1 && !(w->bh[k][l] = alloc(bytes))) return MG_ENOMEM;
-        }
-    w->G.assign(c->L, nullptr);
+    w->sw.assign(c->L, {});
+    w->bh.assign(c->L, nullptr);
+    w->G.assign(2 * c->L, nullptr);
     w->GB.assign(c->L, nullptr);
     w->T.assign(c->L, nullptr);
     for (int l = 0; l < c->L; ++l) {
         const size_t bytes = npts(c->d, c->n[l]) * es;
-        if (!(w->G[l] = alloc(bytes)) || !(w->GB[l] = alloc(bytes)) || !(w->T[l] = alloc(bytes))) return MG_ENOMEM;
+        const int ns = c->n[l] == 3 ? 1 : slots;
+        for (int s = 0; s < ns; ++s) {
+            void *p = alloc(bytes);
+            if (!p) return MG_ENOMEM;
+            w->sw[l].push_back(p);
+        }
+        if (l >= 1 && !(w->bh[l] = alloc(bytes))) return MG_ENOMEM;
+        if (!(w->G[2 * l] = alloc(bytes)) || !(w->G[2 * l + 1] = alloc(bytes)) || !(w->GB[l] = alloc(bytes)) ||
+            !(w->T[l] = alloc(bytes)))
+            return MG_ENOMEM;
     }
-    w->npartials = grid_for(npts(c->d, c->n[0]));
-    if (!(w->partials = (double *)alloc((size_t)3 * w->npartials * sizeof(double)))) return MG_ENOMEM;
+    const long nb = adj_partial_blocks(c, K);
+    w->npartials = (size_t)3 * (nb > 0 ? nb : 1);
+    if (!(w->partials = (double *)alloc(w->npartials * sizeof(double)))) return MG_ENOMEM;
     if (!(w->acc = (double *)alloc(3 * sizeof(double)))) return MG_ENOMEM;
+    if (cudaMallocHost((void **)&w->h_acc, 3 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        w->h_acc = nullptr;
+        return MG_ENOMEM;
+    }
     return MG_OK;
 }
 
@@ -403,33 +667,22 @@ template <typename T>
 static mg_status run_adjoint(mg_ctx *c, int K, const T *b, const T *g_uK, T *g_b, double *g_c)
 {
     AdjointWork *w = c->adj;
-    Adjoint<T> A{c, w, b};
-    // forward replay
-    const T *u = nullptr;
-    for (int k = 0; k < K; ++k) {
-        u = A.fwd_visit(k, 0, u);
-        if (!u) return cuda_fail(A.err);
+    if (!w->graph || w->cap_b != b || w->cap_g != g_uK || w->cap_gb != g_b) {
+        if (w->graph) cudaGraphExecDestroy(w->graph);
+        w->graph = nullptr;
+        Adjoint<T> A{c, w, b};
+        mg_status st =
+            capture_graph(c, &w->graph, &w->nodes, [&]() -> cudaError_t { return A.record_all(K, g_uK, g_b); });
+        if (st != MG_OK) return st;
+        w->cap_b = b;
+        w->cap_g = g_uK;
+        w->cap_gb = g_b;
     }
-    // reverse
-    const size_t np0 = npts(c->d, c->n[0]);
-    if (cudaMemcpyAsync(w->G[0], g_uK, np0 * sizeof(T), cudaMemcpyDeviceToDevice, c->s) != cudaSuccess ||
-        cudaMemsetAsync(w->GB[0], 0, np0 * sizeof(T), c->s) != cudaSuccess ||
-        cudaMemsetAsync(w->acc, 0, 3 * sizeof(double), c->s) != cudaSuccess)
-        return cuda_fail(cudaGetLastError());
-    for (int k = K - 1; k >= 0; --k) {
-        const T *in = k == 0 ? nullptr : A.slot(k - 1, 0, c->nu1 + c->nu2 - 1);
-        A.rev_visit(k, 0, in);
-        if (A.err != cudaSuccess) return cuda_fail(A.err);
-    }
-    const T h2 = T(1.0 / ((double)c->N * c->N));
-    adj_scale<T><<<grid_for(np0), 256, 0, c->s>>>((const T *)w->GB[0], g_b, np0, h2);
-    count_launch(1);
-    double acc[3];
-    cudaError_t e = cudaGetLastError();
-    if (!e) e = cudaMemcpyAsync(acc, w->acc, sizeof acc, cudaMemcpyDeviceToHost, c->s);
+    cudaError_t e = cudaGraphLaunch(w->graph, c->s);
+    if (!e) count_launch(w->nodes);
     if (!e) e = cudaStreamSynchronize(c->s);
     if (e) return cuda_fail(e);
-    for (int j = 0; j < c->ncoef; ++j) g_c[j] = acc[j];
+    for (int j = 0; j < c->ncoef; ++j) g_c[j] = w->h_acc[j];
     return MG_OK;
 }
 
@@ -437,19 +690,28 @@ extern "C" mg_status mg_vcycles_adjoint(mg_ctx *ctx, int K, const void *b, const
                                         double *grad_coeffs_out)
 {
     if (!ctx || K < 1 || !b || !grad_uK || !grad_b_out || !grad_coeffs_out || ctx->batch ||
-        ctx->gamma != 1 || ctx->nu1 < 1 || ctx->prec == MG_FP32_IR || ctx->L < 2 ||
+        ctx->gamma != 1 || ctx->nu1 < 1 || ctx->prec == MG_FP32_IR || ctx->L < 2 || ctx->L > 32 ||
         (ctx->d == 3 && ctx->ncoef > 2))  // the adjoint covers the 7-point M in 3D
         return MG_EINVAL;
     if (cudaSetDevice(ctx->dev) != cudaSuccess) return cuda_fail(cudaGetLastError());
     if (cudaEventRecord(ctx->ev_in, ctx->user) != cudaSuccess || cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0) != cudaSuccess)
         return cuda_fail(cudaGetLastError());
     mg_status st = adj_alloc(ctx, K);
+    if (st == MG_OK)
+        st = ctx->prec == MG_FP64 ? run_adjoint<double>(ctx, K, (const double *)b, (const double *)grad_uK,
+                                                        (double *)grad_b_out, grad_coeffs_out)
+                                  : run_adjoint<float>(ctx, K, (const float *)b, (const float *)grad_uK,
+                                                       (float *)grad_b_out, grad_coeffs_out);
+    // order the caller's stream after the work queued here, on every exit
+    const bool ordered = cudaEventRecord(ctx->ev_out, ctx->s) == cudaSuccess &&
+                         cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0) == cudaSuccess;
     if (st != MG_OK) return st;
-    st = ctx->prec == MG_FP64
-             ? run_adjoint<double>(ctx, K, (const double *)b, (const double *)grad_uK, (double *)grad_b_out, grad_coeffs_out)
-             : run_adjoint<float>(ctx, K, (const float *)b, (const float *)grad_uK, (float *)grad_b_out, grad_coeffs_out);
-    if (st != MG_OK) return st;
-    if (cudaEventRecord(ctx->ev_out, ctx->s) != cudaSuccess || cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0) != cudaSuccess)
-        return cuda_fail(cudaGetLastError());
+    return ordered ? MG_OK : cuda_fail(cudaGetLastError());
+}
+
+extern "C" mg_status mg_adjoint_workspace_bytes(mg_ctx *ctx, int K, unsigned long long *bytes_out)
+{
+    if (!ctx || K < 1 || !bytes_out || ctx->batch) return MG_EINVAL;
+    *bytes_out = adj_bytes(ctx, K);
     return MG_OK;
 }

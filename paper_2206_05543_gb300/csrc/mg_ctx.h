@@ -9,15 +9,24 @@
 
 #include "../../include/mg.h"
 
-// device workspace of the adjoint (allocated on first use)
+// device workspace of the adjoint (allocated on first use for a given K):
+// the cycle inputs u_1 .. u_{K-1} (finest level), and per level the inputs of
+// the sweeps of the cycle being reversed, that level's right-hand side and
+// the adjoint fields; the whole evaluation is recorded into one CUDA graph
 struct AdjointWork {
     int K = 0;
-    std::vector<std::vector<std::vector<void *>>> work;  // [k][level][slot]
-    std::vector<std::vector<void *>> bh;                 // [k][level], level >= 1
-    std::vector<void *> G, GB, T;                        // per level
-    double *partials = nullptr;                          // per-block coefficient partials (3 per block)
-    int npartials = 0;
-    double *acc = nullptr;                               // 3 coefficient gradients (device)
+    std::vector<void *> ck;                    // [k], k = 1 .. K-1 (ck[0] unused: u_0 = 0)
+    std::vector<std::vector<void *>> sw;       // [level][sweep]: outputs of the visit's sweeps
+    std::vector<void *> bh;                    // [level], level >= 1
+    std::vector<void *> G, GB, T;              // per level
+    double *partials = nullptr;                // per-block coefficient partials of every reverse sweep
+    size_t npartials = 0;                      // doubles
+    double *acc = nullptr;                     // 3 coefficient gradients (device)
+    double *h_acc = nullptr;                   // pinned copy
+    cudaGraphExec_t graph = nullptr;
+    unsigned long long nodes = 0;
+    const void *cap_b = nullptr, *cap_g = nullptr, *cap_gb = nullptr;
+    size_t bytes = 0;                          // device bytes of this workspace
     std::vector<void *> owned;
 };
 

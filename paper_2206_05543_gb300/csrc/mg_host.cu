@@ -234,6 +234,10 @@ static void free_graphs(mg_ctx *c)
     if (c->g.meas) cudaGraphExecDestroy(c->g.meas);
     c->g = GraphPair{};
     c->cap_u = c->cap_b = nullptr;
+    if (c->adj && c->adj->graph) {  // the adjoint's graph holds the weights too
+        cudaGraphExecDestroy(c->adj->graph);
+        c->adj->graph = nullptr;
+    }
 }
 
 static void destroy_ctx(mg_ctx *c)

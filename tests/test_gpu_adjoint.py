@@ -162,3 +162,33 @@ def test_plain_fp32_solve():
         assert oracle.residual_norm(u, b) <= 2e-5 * np.linalg.norm(b)
         ref = oracle.solve(b, coeffs.default(d), tol=1e-10)
         assert _rel(u, ref.u) <= 1e-4
+
+
+@pytest.mark.slow
+def test_fp64_adjoint_3d_n512_fits_and_matches_a_directional_difference():
+    """The adjoint at the 3D benchmark size in FP64 (K = 2 V(1,1), 133M
+    unknowns): the workspace (cycle inputs plus one cycle's sweep inputs per
+    level) is about ten finest fields, and <dL/db, v> matches the central
+    difference of L(b) = 1/2 ||u_K(b)||^2 along a random v (L is quadratic
+    in b, so the difference has no truncation error; the bound is the FP64
+    rounding of the two forward evaluations)."""
+    N, K = 512, 2
+    rng = np.random.default_rng(4)
+    b = torch.from_numpy(rng.standard_normal((N - 1,) * 3)).cuda()
+    v = torch.from_numpy(rng.standard_normal((N - 1,) * 3)).cuda()
+    with Solver(3, N) as s:
+        ws = s.adjoint_workspace_bytes(K)
+        field = (N - 1) ** 3 * 8
+        assert ws <= 11 * field, ws / field
+        uK = s.cycles(b, K)
+        gb, gc = s.vcycles_adjoint(b, uK.contiguous(), K)
+        torch.cuda.synchronize()
+        eps = 1e-3
+
+        def loss(bb):
+            u = s.cycles(bb, K)
+            return 0.5 * float(torch.sum(u * u))
+
+        fd = (loss(b + eps * v) - loss(b - eps * v)) / (2 * eps)
+        dd = float(torch.sum(gb * v))
+    assert dd == pytest.approx(fd, rel=1e-6)
