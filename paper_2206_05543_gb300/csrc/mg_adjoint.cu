@@ -80,19 +80,43 @@ adj_sweep3d_kernel(const T *__restrict__ g, T *__restrict__ gout, const T *__res
     const int ig = (oy + 2) * kAGX + (ox + 2);  // in the g region
     const size_t plane = (size_t)n * n;
     double a0 = 0.0, a1 = 0.0;
-    for (int q = z0 - 2; q <= z1 + 1; ++q) {
-        // A. g plane q (2-point halo), u plane q (1-point halo)
+    // the plane loads of step q are issued at step q - 1 (registers), so that
+    // their latency overlaps the work of a step: thread tid owns the region
+    // points tid and tid + 256 (when inside the region)
+    constexpr int kGN = (kAGX * kAGY + kAThreads - 1) / kAThreads, kUN = (kATX * kATY + kAThreads - 1) / kAThreads;
+    T gq[kGN], uq[kUN];
+    auto load_plane = [&](int q) {
         const bool qin = q >= 0 && q < n;
-        for (int i = tid; i < kAGX * kAGY; i += kAThreads) {
+#pragma unroll
+        for (int k = 0; k < kGN; ++k) {
+            const int i = tid + k * kAThreads;
             const int gx = x0 - 2 + i % kAGX, gy = y0 - 2 + i / kAGX;
-            sg[q & 3][i] = qin && gx >= 0 && gx < n && gy >= 0 && gy < n ? g[q * plane + (size_t)gy * n + gx] : T(0);
+            gq[k] = i < kAGX * kAGY && qin && gx >= 0 && gx < n && gy >= 0 && gy < n ? g[q * plane + (size_t)gy * n + gx]
+                                                                                   : T(0);
         }
-        if (!ZERO_U)
-            for (int i = tid; i < kATX * kATY; i += kAThreads) {
+        if (!ZERO_U) {
+#pragma unroll
+            for (int k = 0; k < kUN; ++k) {
+                const int i = tid + k * kAThreads;
                 const int ux = x0 - 1 + i % kATX, uy = y0 - 1 + i / kATX;
-                su[(q + 3) % 3][i] = qin && ux >= 0 && ux < n && uy >= 0 && uy < n ? u[q * plane + (size_t)uy * n + ux]
-                                                                                  : T(0);
+                uq[k] = i < kATX * kATY && qin && ux >= 0 && ux < n && uy >= 0 && uy < n
+                            ? u[q * plane + (size_t)uy * n + ux]
+                            : T(0);
             }
+        }
+    };
+    load_plane(z0 - 2);
+    for (int q = z0 - 2; q <= z1 + 1; ++q) {
+        // A. g plane q (2-point halo), u plane q (1-point halo), then the loads of plane q + 1
+#pragma unroll
+        for (int k = 0; k < kGN; ++k)
+            if (tid + k * kAThreads < kAGX * kAGY) sg[q & 3][tid + k * kAThreads] = gq[k];
+        if (!ZERO_U) {
+#pragma unroll
+            for (int k = 0; k < kUN; ++k)
+                if (tid + k * kAThreads < kATX * kATY) su[(q + 3) % 3][tid + k * kAThreads] = uq[k];
+        }
+        if (q < z1 + 1) load_plane(q + 1);
         __syncthreads();
         // B. t of plane p = q - 1 on the 1-point halo region
         const int p = q - 1;
@@ -179,17 +203,27 @@ adj_sweep2d_kernel(const T *__restrict__ g, T *__restrict__ gout, const T *__res
     const int X = x0 + tid;
     const bool own = X < n;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int q = y0 - 2; q <= y1 + 1; ++q) {
+    // the row loads of step q are issued at step q - 1 (registers)
+    T gq[2], uq[2];
+    auto load_row = [&](int q) {
         const bool qin = q >= 0 && q < n;
-        for (int i = tid; i < kA2G; i += kA2X) {
-            const int gx = x0 - 2 + i;
-            sg[q & 3][i] = qin && gx >= 0 && gx < n ? g[(size_t)q * n + gx] : T(0);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = tid + k * kA2X;
+            const int gx = x0 - 2 + i, ux = x0 - 1 + i;
+            gq[k] = i < kA2G && qin && gx >= 0 && gx < n ? g[(size_t)q * n + gx] : T(0);
+            if (!ZERO_U) uq[k] = i < kA2T && qin && ux >= 0 && ux < n ? u[(size_t)q * n + ux] : T(0);
         }
-        if (!ZERO_U)
-            for (int i = tid; i < kA2T; i += kA2X) {
-                const int ux = x0 - 1 + i;
-                su[(q + 3) % 3][i] = qin && ux >= 0 && ux < n ? u[(size_t)q * n + ux] : T(0);
-            }
+    };
+    load_row(y0 - 2);
+    for (int q = y0 - 2; q <= y1 + 1; ++q) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = tid + k * kA2X;
+            if (i < kA2G) sg[q & 3][i] = gq[k];
+            if (!ZERO_U && i < kA2T) su[(q + 3) % 3][i] = uq[k];
+        }
+        if (q < y1 + 1) load_row(q + 1);
         __syncthreads();
         const int p = q - 1;
         if (p >= y0 - 1) {
