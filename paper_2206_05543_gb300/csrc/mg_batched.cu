@@ -134,7 +134,11 @@ struct BatchSize {
     // first pre-sweep of the later cycles of a refinement iteration: finest
     // levels from the previous cycle's result, coarse levels from zero
     BItem<float> *again = nullptr;
-    int H = 16, Hrr = 8, Hpro = 8;
+    // V(1,1): the two temporally blocked passes (mg_fused2d.cu) per level:
+    // sweep + residual + restriction (fa; fagain for the later cycles of an
+    // iteration), interpolation + correction + sweep (fb)
+    FItem *fa = nullptr, *fagain = nullptr, *fb = nullptr;
+    int H = 16, Hrr = 8, Hpro = 8, Hfa = 16, Hfb = 32;
 };
 
 struct BatchGroup {
@@ -253,6 +257,17 @@ mg_status autotune(mg_ctx *c, BatchWork *w)
         };
         static const int sweep_c[] = {4, 8, 16, 32, 64};
         static const int rr_c[] = {2, 4, 8, 16, 32};
+        if (c->nu1 == 1 && c->nu2 == 1) {
+            static const int fa_c[] = {4, 8, 16, 32, 64};
+            static const int fb_c[] = {8, 16, 32, 64, 128};
+            tune("fused-a", fa_c, 5, S.Hfa, [&](int H) {
+                launch_sweep_restrict2d_pl_batched(S.fa, np, w->active, S.n, H, c->c, c->s);
+            });
+            tune("fused-b", fb_c, 5, S.Hfb, [&](int H) {
+                launch_prolong_sweep2d_pl_batched(S.fb, np, w->active, S.n, H, c->c, c->s);
+            });
+            continue;
+        }
         tune("sweep", sweep_c, 5, S.H, [&](int H) {
             launch_sweep2d_pl_batched(S.pre[0], np, w->active, S.n, H, 1, c->c, c->s);
         });
@@ -275,6 +290,21 @@ cudaError_t record_cycle(mg_ctx *c, BatchWork *w, bool first)
 {
     cudaError_t e;
     const int nu1 = c->nu1, nu2 = c->nu2;
+    if (nu1 == 1 && nu2 == 1) {
+        // V(1,1) in two temporally blocked passes per level size
+        for (BatchSize &S : w->sizes)
+            if ((e = launch_sweep_restrict2d_pl_batched(first ? S.fa : S.fagain, (int)S.probs.size(), w->active, S.n,
+                                                        S.Hfa, c->c, c->s)))
+                return e;
+        if ((e = launch_tail_batched<float>(w->tail_lv, w->tail_ops, w->op_off, w->op_cnt, w->active, w->count, w->d,
+                                            c->c, c->lu, c->s)))
+            return e;
+        for (auto it = w->sizes.rbegin(); it != w->sizes.rend(); ++it)
+            if ((e = launch_prolong_sweep2d_pl_batched(it->fb, (int)it->probs.size(), w->active, it->n, it->Hfb, c->c,
+                                                       c->s)))
+                return e;
+        return cudaSuccess;
+    }
     // descend
     for (BatchSize &S : w->sizes) {
         const int np = (int)S.probs.size();
@@ -485,12 +515,17 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             for (int k = 0; k < nu2; ++k) post.push_back((BItem<float> *)a.take(tb));
             BItem<float> *rr = (BItem<float> *)a.take(tb), *pro = (BItem<float> *)a.take(tb);
             BItem<float> *again = (BItem<float> *)a.take(tb);
+            const size_t fbytes = S.probs.size() * sizeof(FItem);
+            FItem *fa = (FItem *)a.take(fbytes), *fagain = (FItem *)a.take(fbytes), *fb = (FItem *)a.take(fbytes);
             if (real) {
                 S.pre = pre;
                 S.post = post;
                 S.rr = rr;
                 S.pro = pro;
                 S.again = again;
+                S.fa = fa;
+                S.fagain = fagain;
+                S.fb = fb;
             }
         }
         for (BatchGroup &G : w->groups) {
@@ -583,6 +618,19 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             }
             up(S.post[k], tab.data(), np * sizeof(BItem<float>));
         }
+        // the fused V(1,1) passes: the pre-smoothed field in B, the visit's
+        // result in A (as for the unfused V(1,1))
+        std::vector<FItem> fa(np), fagain(np), fb(np);
+        for (size_t j = 0; j < np; ++j) {
+            const int p = S.probs[j], l = S.lev[j];
+            fa[j] = FItem{nullptr, nullptr, w->BH[p][l], w->B[p][l], w->BH[p][l + 1], p, 0};
+            fagain[j] = fa[j];
+            if (l == 0) fagain[j].u = result_buf(w, p, 0, nu1 + nu2);
+            fb[j] = FItem{w->B[p][l], result_buf(w, p, l + 1, nu1 + nu2), w->BH[p][l], w->A[p][l], nullptr, p, 0};
+        }
+        up(S.fa, fa.data(), np * sizeof(FItem));
+        up(S.fagain, fagain.data(), np * sizeof(FItem));
+        up(S.fb, fb.data(), np * sizeof(FItem));
     }
     {
         std::vector<TailLevel> tl((size_t)count * kMaxTailLevels);

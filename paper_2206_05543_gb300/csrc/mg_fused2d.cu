@@ -43,7 +43,6 @@ constexpr int kFC = 4;                 // fine columns per lane
 constexpr int kFOut = 30 * kFC;        // fine columns a warp stores (lanes 1..30)
 constexpr int kFWarps = 4;             // warps per block: adjacent tiles, same rows
 constexpr int kFThreads = 32 * kFWarps;
-constexpr int kFAhead = 2;             // rows of loads in flight ahead of their use
 
 struct Row8 {
     float v[kFC];
@@ -206,20 +205,22 @@ __device__ __forceinline__ void store8(float *base, const Pitch2 &g, int x, int 
 // (the last chunk also row n - 1) and the coarse rows [jc0, jc1).
 // Rings: bh row R and, from a non-zero start, u0 row R + 1 at step R.
 // ---------------------------------------------------------------------------
+// One warp's part of block (bx, by); `ring`: the warp's shared-memory rings
+// (one ring from zero, two otherwise).
 template <bool ZERO_U>
-__global__ void __launch_bounds__(kFThreads)
-sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ bh, float *__restrict__ u1out,
-                        float *__restrict__ bc, Pitch2 g, Pitch2 gc, int Hc, float c0, float c1, float c2)
+__device__ __forceinline__ void sweep_restrict2d_tile(const float *__restrict__ u0, const float *__restrict__ bh,
+                                                      float *__restrict__ u1out, float *__restrict__ bc, Pitch2 g,
+                                                      Pitch2 gc, int Hc, float c0, float c1, float c2, int bx, int by,
+                                                      float4 *ring)
 {
-    extern __shared__ __align__(16) float4 fsm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kFWarps + w;
+    const int tile = bx * kFWarps + w;
     const int n = g.n, nc = gc.n;
     const int x = kFOut * tile - kFC + kFC * lane;
     if (kFOut * tile >= n) return;  // the whole warp leaves together
     const bool owner = lane >= 1 && lane <= 30;
     const unsigned cols = col_bits(x, n);
-    const int jc0 = blockIdx.y * Hc, jc1 = min(jc0 + Hc, nc);
+    const int jc0 = by * Hc, jc1 = min(jc0 + Hc, nc);
     // fine rows of u1 this chunk stores
     const int w0 = 2 * jc0, w1 = jc1 == nc ? n : 2 * jc1;
     // the newest residual row r0 is row R; u1 row R - 1; r1 row R - 2
@@ -227,7 +228,7 @@ sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ 
     // rings: bh row R and (non-zero start) u0 row R + 1 at step R; the
     // prologue issues steps Rfirst .. Rfirst + kFDepth - 1 (one group per step)
     Ring4 rb, ru;
-    rb.init(fsm + (ZERO_U ? 1 : 2) * w * kFSlots * 32, bh, g, x, Rfirst);
+    rb.init(ring, bh, g, x, Rfirst);
     if (!ZERO_U) ru.init(rb.s + kFSlots * 32, u0, g, x, Rfirst - 1);
     for (int k = 0; k < kFDepth; ++k) {
         rb.issue(lane);
@@ -341,29 +342,29 @@ __device__ __forceinline__ Row8 interp_x8(float2 e2)
     return v;
 }
 
+// float4s of shared memory per warp of pass B: u1 and bh rings (float4),
+// the e ring (float2) and, ACC64, the staging row of the FP64 epilogue
+constexpr int kRing4 = kFSlots * 32;
+__host__ __device__ constexpr int warp_f4_b(bool acc64) { return 2 * kRing4 + kRing4 / 2 + (acc64 ? 32 : 0); }
+
+// One warp's part of block (bx, by); `base`: the warp's shared memory.
 template <bool ACC64>
-__global__ void __launch_bounds__(kFThreads)
-prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e, const float *__restrict__ bh,
-                       float *__restrict__ out, double *__restrict__ u64, Pitch2 g, Pitch2 gc, int H, float c0,
-                       float c1, float c2)
+__device__ __forceinline__ void prolong_sweep2d_tile(const float *__restrict__ u1, const float *__restrict__ e,
+                                                     const float *__restrict__ bh, float *__restrict__ out,
+                                                     double *__restrict__ u64, Pitch2 g, Pitch2 gc, int H, float c0,
+                                                     float c1, float c2, int bx, int by, float4 *base)
 {
-    extern __shared__ __align__(16) float4 fsm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kFWarps + w;
+    const int tile = bx * kFWarps + w;
     const int n = g.n;
     const int x = kFOut * tile - kFC + kFC * lane;
     if (kFOut * tile >= n) return;
-    // per warp: u1 and bh rings (float4), the e ring (float2) and, ACC64, the
-    // staging row of the FP64 epilogue
-    constexpr int kRing4 = kFSlots * 32;  // float4s
-    constexpr int kWarpF4 = 2 * kRing4 + kRing4 / 2 + (ACC64 ? 32 : 0);
-    float4 *base = fsm + w * kWarpF4;
     float2 *re = reinterpret_cast<float2 *>(base + 2 * kRing4);  // [slot][lane]
     float *sacc = reinterpret_cast<float *>(base + 2 * kRing4 + kRing4 / 2);
     const bool owner = lane >= 1 && lane <= 30;
     const int k0 = x / 2;
     const int xw = kFOut * tile - kFC;  // column of lane 0's first value
-    const int y0 = blockIdx.y * H, y1 = min(y0 + H, n);
+    const int y0 = by * H, y1 = min(y0 + H, n);
     // the newest corrected row u2 is row Q; residual row Q - 1; output row Q - 2
     const int Qfirst = y0 - 2, Qlast = y1 + 1;
     // coarse row m (0-based) sits at fine row 2m + 1; fine row Q needs the
@@ -474,17 +475,73 @@ prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the warp has left
 }
 
+template <bool ZERO_U>
+__global__ void __launch_bounds__(kFThreads)
+sweep_restrict2d_kernel(const float *__restrict__ u0, const float *__restrict__ bh, float *__restrict__ u1out,
+                        float *__restrict__ bc, Pitch2 g, Pitch2 gc, int Hc, float c0, float c1, float c2)
+{
+    extern __shared__ __align__(16) float4 fsm[];
+    const int w = threadIdx.x >> 5;
+    sweep_restrict2d_tile<ZERO_U>(u0, bh, u1out, bc, g, gc, Hc, c0, c1, c2, blockIdx.x, blockIdx.y,
+                                  fsm + (ZERO_U ? 1 : 2) * w * kFSlots * 32);
+}
+
+template <bool ACC64>
+__global__ void __launch_bounds__(kFThreads)
+prolong_sweep2d_kernel(const float *__restrict__ u1, const float *__restrict__ e, const float *__restrict__ bh,
+                       float *__restrict__ out, double *__restrict__ u64, Pitch2 g, Pitch2 gc, int H, float c0,
+                       float c1, float c2)
+{
+    extern __shared__ __align__(16) float4 fsm[];
+    const int w = threadIdx.x >> 5;
+    prolong_sweep2d_tile<ACC64>(u1, e, bh, out, u64, g, gc, H, c0, c1, c2, blockIdx.x, blockIdx.y,
+                                fsm + w * warp_f4_b(ACC64));
+}
+
+// Batched forms: persistent loops over the (problem, block) items of every
+// problem with a level of size n, skipping inactive problems. Pass A takes
+// each item's start (u == nullptr: from zero) per item; every warp keeps two
+// rings, so that warps of a block that are at different items never share one.
+__global__ void __launch_bounds__(kFThreads)
+sweep_restrict2d_batched(const FItem *__restrict__ tab, int nprob, const int *__restrict__ active, Pitch2 g,
+                         Pitch2 gc, int Hc, int bx, int by, float c0, float c1, float c2)
+{
+    extern __shared__ __align__(16) float4 fsm[];
+    float4 *ring = fsm + 2 * (threadIdx.x >> 5) * kFSlots * 32;
+    const int per = bx * by, total = nprob * per;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int j = it / per, r = it - j * per;
+        const FItem f = tab[j];
+        if (!active[f.problem]) continue;
+        if (f.u)
+            sweep_restrict2d_tile<false>(f.u, f.b, f.out, f.out2, g, gc, Hc, c0, c1, c2, r % bx, r / bx, ring);
+        else
+            sweep_restrict2d_tile<true>(nullptr, f.b, f.out, f.out2, g, gc, Hc, c0, c1, c2, r % bx, r / bx, ring);
+    }
+}
+
+__global__ void __launch_bounds__(kFThreads)
+prolong_sweep2d_batched(const FItem *__restrict__ tab, int nprob, const int *__restrict__ active, Pitch2 g, Pitch2 gc,
+                        int H, int bx, int by, float c0, float c1, float c2)
+{
+    extern __shared__ __align__(16) float4 fsm[];
+    float4 *base = fsm + (threadIdx.x >> 5) * warp_f4_b(false);
+    const int per = bx * by, total = nprob * per;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int j = it / per, r = it - j * per;
+        const FItem f = tab[j];
+        if (!active[f.problem]) continue;
+        prolong_sweep2d_tile<false>(f.u, f.e, f.b, f.out, nullptr, g, gc, H, c0, c1, c2, r % bx, r / bx, base);
+    }
+}
+
 }  // namespace
 
 // tiles of kFOut fine columns, kFWarps per block
 static int fused_tiles(int n) { return (n + kFOut - 1) / kFOut; }
 
 static size_t smem_a(bool zero_u) { return (size_t)kFWarps * (zero_u ? 1 : 2) * kFSlots * 32 * sizeof(float4); }
-static size_t smem_b(bool acc64)
-{
-    const size_t ring4 = (size_t)kFSlots * 32;
-    return (size_t)kFWarps * (2 * ring4 + ring4 / 2 + (acc64 ? 32 : 0)) * sizeof(float4);
-}
+static size_t smem_b(bool acc64) { return (size_t)kFWarps * warp_f4_b(acc64) * sizeof(float4); }
 
 cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *u1, float *bc, int n, const double *c,
                                        cudaStream_t s)
@@ -525,6 +582,46 @@ cudaError_t launch_prolong_sweep2d_pl(const float *u1, const float *e, const flo
     else
         prolong_sweep2d_kernel<false><<<grid, kFThreads, smem_b(false), s>>>(u1, e, bh, out, u64, g, gc, H, c0, c1,
                                                                              c2);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace mg
+
+namespace mg {
+
+static int fused_persistent_grid(const void *fn, size_t smem, long items)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (int)std::max<long>(1, std::min<long>(items, (long)per_sm * num_sms()));
+}
+
+int fused_blocks_x(int n) { return (fused_tiles(n) + kFWarps - 1) / kFWarps; }
+
+cudaError_t launch_sweep_restrict2d_pl_batched(const FItem *tab, int nprob, const int *active, int n, int Hc,
+                                               const double *c, cudaStream_t s)
+{
+    const Pitch2 g = pitch2(n), gc = pitch2((n - 1) / 2);
+    const int bx = fused_blocks_x(n), by = (gc.n + Hc - 1) / Hc;
+    const size_t smem = smem_a(false);
+    const int grid = fused_persistent_grid((const void *)sweep_restrict2d_batched, smem, (long)nprob * bx * by);
+    sweep_restrict2d_batched<<<grid, kFThreads, smem, s>>>(tab, nprob, active, g, gc, Hc, bx, by, (float)c[0],
+                                                           (float)c[1], (float)c[2]);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_sweep2d_pl_batched(const FItem *tab, int nprob, const int *active, int n, int H,
+                                              const double *c, cudaStream_t s)
+{
+    const Pitch2 g = pitch2(n), gc = pitch2((n - 1) / 2);
+    const int bx = fused_blocks_x(n), by = (n + H - 1) / H;
+    const size_t smem = smem_b(false);
+    const int grid = fused_persistent_grid((const void *)prolong_sweep2d_batched, smem, (long)nprob * bx * by);
+    prolong_sweep2d_batched<<<grid, kFThreads, smem, s>>>(tab, nprob, active, g, gc, H, bx, by, (float)c[0],
+                                                          (float)c[1], (float)c[2]);
     count_launch(1);
     return cudaGetLastError();
 }

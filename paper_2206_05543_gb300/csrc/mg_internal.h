@@ -127,6 +127,19 @@ cudaError_t launch_sweep_restrict2d_pl(const float *u0, const float *bh, float *
                                        cudaStream_t s);
 cudaError_t launch_prolong_sweep2d_pl(const float *u1, const float *e, const float *bh, float *out, double *u64, int n,
                                       const double *c, cudaStream_t s);
+// batched forms (one launch per level size across problems)
+struct FItem {
+    const float *u;  // A: start (nullptr: zero); B: the pre-smoothed field
+    const float *e;  // B: the coarse correction
+    const float *b;  // the level's scaled right-hand side
+    float *out;      // A: the smoothed field; B: the visit's result
+    float *out2;     // A: the coarse right-hand side
+    int problem, pad;
+};
+cudaError_t launch_sweep_restrict2d_pl_batched(const FItem *tab, int nprob, const int *active, int n, int Hc,
+                                               const double *c, cudaStream_t s);
+cudaError_t launch_prolong_sweep2d_pl_batched(const FItem *tab, int nprob, const int *active, int n, int H,
+                                              const double *c, cudaStream_t s);
 
 // 3D: element (x, y, z), each in [-1, n], at off + z*plane + y*pitch + x.
 struct Pitch3 {
