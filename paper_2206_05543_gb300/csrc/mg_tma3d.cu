@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 
@@ -545,6 +546,27 @@ bool make_map(CUtensorMap *map, const float *base, const Pitch3 &g, int width, i
 
 }  // namespace
 
+// z-chunks per tile column for a launch of `tiles` tile columns on `slots`
+// resident blocks: the fewest chunks that fill the last wave to >= 95 %
+// (each chunk boundary re-reads a plane or two; a partly filled last wave
+// leaves SMs idle), else the best fill up to 8x the one-wave count
+static int fill_chunks(int tiles, int slots, int max_chunks)
+{
+    const int base = std::max(1, slots / std::max(1, tiles));
+    int best = std::min(base, max_chunks);
+    double best_fill = 0.0;
+    for (int c = 1; c <= std::min(max_chunks, 8 * base); ++c) {
+        const double waves = (double)tiles * c / slots;
+        const double fill = waves / std::ceil(waves);
+        if (fill >= 0.95 && c >= base) return c;
+        if (fill > best_fill + 1e-9) {
+            best_fill = fill;
+            best = c;
+        }
+    }
+    return best;
+}
+
 static cudaError_t sweep3d_tma_any(const float *u, const float *b, float *out, double *u64, int n, const double *c,
                                    int *err, cudaStream_t s)
 {
@@ -571,9 +593,8 @@ static cudaError_t sweep3d_tma_any(const float *u, const float *b, float *out, d
         tu = tb;
     }
     const int bx = (n + kTCols - 1) / kTCols, by = (n + kTTY - 1) / kTTY;
-    // one wave at two blocks per SM; chunks of at least four planes
-    int chunks = std::max(1, 2 * num_sms() / (bx * by));
-    chunks = std::min(chunks, std::max(1, n / 4));
+    // two blocks per SM; chunks of at least four planes, the last wave filled
+    const int chunks = fill_chunks(bx * by, 2 * num_sms(), std::max(1, n / 4));
     const int Z = (n + chunks - 1) / chunks;
     const dim3 grid(bx, by, (n + Z - 1) / Z);
     const float c0 = (float)c[0], c1 = (float)c[1];
@@ -623,9 +644,8 @@ cudaError_t launch_resrestrict3d_tma(const float *u, const float *b, float *bc, 
     CUtensorMap tu, tb;
     if (!make_map(&tu, u, g, kRW, kRUR) || !make_map(&tb, b, g, kRW, kRBR)) return cudaErrorInvalidValue;
     const int bx = (nc + kRX - 1) / kRX, by = (nc + kRY - 1) / kRY;
-    // at most one wave: z-chunks of coarse planes
-    int chunks = std::max(1, resident * num_sms() / (bx * by));
-    chunks = std::min(chunks, std::max(1, nc / 2));
+    // z-chunks of coarse planes (at least two), the last wave filled
+    const int chunks = fill_chunks(bx * by, resident * num_sms(), std::max(1, nc / 2));
     const int Zc = (nc + chunks - 1) / chunks;
     const int inject = take_armed() ? 16 : 0;
     resrestrict3d_tma_kernel<<<dim3(bx, by, (nc + Zc - 1) / Zc), kRThreads, kRSmemBytes, s>>>(tu, tb, bc, g, gc, Zc,
