@@ -30,127 +30,179 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 //   rh = fma(-6, u_p, bh_p) + s          (rh := 0 outside the interior)
 //   E  = ((rh_W + rh_E) + (rh_S + rh_N)) + (rh_D + rh_U)
 //   u' = fma(c1, E, fma(c0, rh_p, u_p))
-// (W/E = x-1/x+1, S/N = y-1/y+1, D/U = z-1/z+1). A block computes rh on a
-// 32x32 tile (output tile 30x30 plus its halo), thread t holding the tile
-// points t, t+256, t+512, t+768 with their z-windows in registers. One
-// barrier per plane: at step zz the u plane zz + 1 goes to the other half of
-// the double buffer next to the residual plane zz, the update of plane zz - 1
-// reads the residual plane written one step earlier, and every global load
-// is issued one step before its use.
+// (W/E = x-1/x+1, S/N = y-1/y+1, D/U = z-1/z+1). A block owns a 32x32 output
+// tile; it forms rh on the tile and on the one-point ring around it (34x34),
+// the u planes it reads cover one more ring (36x36). Thread t = 32 w + lane
+// holds the tile points (lane, w + 8k), k < 4, with their z-windows of u and
+// b in registers; the 132 residual-ring points belong one each to threads
+// t < 132 (with their own z-windows), the 140 points of the outer u ring
+// one each to the last 140 threads (the current plane only). Residual planes
+// go through a ring of three shared planes, so the update of plane zz - 1
+// takes rh(zz - 2) and rh(zz - 1) from shared memory and rh(zz) from the
+// register it was just formed in. One barrier per plane: at step zz the u
+// plane zz + 1 goes to the other half of the double buffer next to residual
+// plane zz, and every global load is issued one step before its use. With
+// 32-wide outputs an n = 2^k - 1 level needs no tile that is almost empty,
+// and every warp of the update has all its lanes busy.
 // ---------------------------------------------------------------------------
+constexpr int kT3 = 32;                  // output tile edge (7-point sweep)
+constexpr int kT3R = kT3 + 2;            // residual tile edge
+constexpr int kT3U = kT3 + 4;            // u plane edge
+constexpr int kT3Ring = 4 * (kT3 + 1);   // residual ring points (132)
+constexpr int kT3Ring2 = 4 * (kT3 + 3);  // outer u ring points (140)
+constexpr int kT3Rows = kS3Threads / kT3;
+static_assert(kT3Ring <= kS3Threads && kT3Ring2 <= kS3Threads, "one ring point per thread");
+static_assert(kT3Rows * kS3Pts == kT3, "four rows per thread");
+
+// point q of the ring at distance d (1 or 2) around the kT3 x kT3 tile,
+// tile-relative; the four sides have kT3 + 2d - 1 points each
+__device__ __forceinline__ void tile_ring_point(int q, int d, int &ri, int &rj)
+{
+    const int len = kT3 + 2 * d - 1, side = q / len, p = q - side * len;
+    if (side == 0) { ri = p - d; rj = -d; }
+    else if (side == 1) { ri = kT3 - 1 + d; rj = p - d; }
+    else if (side == 2) { ri = p - d + 1; rj = kT3 - 1 + d; }
+    else { ri = -d; rj = p - d + 1; }
+}
+
 // One segment: output planes [z0, z1) of tile (tx, ty). Starts and ends with
 // the shared buffers free (the last step of the march ends in a barrier).
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__device__ __forceinline__ void sweep3d_segment(T (&su)[2][kS3U * kS3U], T (&sr)[2][kS3 * kS3],
+__device__ __forceinline__ void sweep3d_segment(T (&su)[2][kT3U * kT3U], T (&sr)[3][kT3R * kT3R],
                                                 const T *__restrict__ u, const T *__restrict__ b,
                                                 T *__restrict__ out, int n, int tx, int ty, int z0, int z1,
                                                 T c0, T c1, int hk, double &acc)
 {
-    const int t = threadIdx.x;
-    const int ex0 = tx * kS3Out - 1, ey0 = ty * kS3Out - 1;
+    const int t = threadIdx.x, lane = t % kT3, w = t / kT3;
+    const int ox0 = tx * kT3, oy0 = ty * kT3;
+    const int px = ox0 + lane;
     const size_t plane = (size_t)n * n;
     const T m6 = in_reg(T(-6));
     c0 = in_reg(c0);
     c1 = in_reg(c1);
 
-    int px[kS3Pts], py[kS3Pts];
-    bool inside[kS3Pts], own[kS3Pts];
-    T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], b_next[kS3Pts], r_m1[kS3Pts], r_0[kS3Pts];
+    bool own[kS3Pts];
+    T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], b_next[kS3Pts];
 #pragma unroll
     for (int k = 0; k < kS3Pts; ++k) {
-        const int i = (t + k * kS3Threads) % kS3, j = (t + k * kS3Threads) / kS3;
-        px[k] = ex0 + i;
-        py[k] = ey0 + j;
-        inside[k] = px[k] >= 0 && px[k] < n && py[k] >= 0 && py[k] < n;
-        own[k] = inside[k] && i >= 1 && i <= kS3Out && j >= 1 && j <= kS3Out;
-        u_prev[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0 - 2);
-        u_cur[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0 - 1);
-        u_next[k] = ZERO_U ? T(0) : get3(u, n, px[k], py[k], z0);
-        b_next[k] = get3(b, n, px[k], py[k], z0 - 1);
-        r_m1[k] = T(0);
-        r_0[k] = T(0);
+        const int py = oy0 + w + kT3Rows * k;
+        own[k] = px < n && py < n;
+        u_prev[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0 - 2);
+        u_cur[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0 - 1);
+        u_next[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0);
+        b_next[k] = get3(b, n, px, py, z0 - 1);
     }
-    // the one-point ring around the 32x32 tile: 4 * 33 = 132 points, one per
-    // thread t < 132 (tile-relative (ri, rj) in [-1, 32])
-    const bool ring = !ZERO_U && t < 4 * (kS3 + 1);
+    // residual ring point of threads t < kT3Ring
+    const bool rr = t < kT3Ring;
     int ri = 0, rj = 0;
-    if (ring) {
-        const int side = t / (kS3 + 1), q = t % (kS3 + 1);
-        if (side == 0) { ri = q - 1; rj = -1; }
-        else if (side == 1) { ri = kS3; rj = q - 1; }
-        else if (side == 2) { ri = q; rj = kS3; }
-        else { ri = -1; rj = q; }
-    }
-    T ring_next = T(0);
-    if (!ZERO_U) {
-#pragma unroll
-        for (int k = 0; k < kS3Pts; ++k) {
-            const int i = px[k] - ex0, j = py[k] - ey0;
-            su[(z0 - 1) & 1][(j + 1) * kS3U + (i + 1)] = u_cur[k];
+    tile_ring_point(rr ? t : 0, 1, ri, rj);
+    const int rx = ox0 + ri, ry = oy0 + rj;
+    const bool r_in = rr && rx >= 0 && rx < n && ry >= 0 && ry < n;
+    T ru_prev = T(0), ru_cur = T(0), ru_next = T(0), rb_next = T(0);
+    if (rr) {
+        if (!ZERO_U) {
+            ru_prev = get3(u, n, rx, ry, z0 - 2);
+            ru_cur = get3(u, n, rx, ry, z0 - 1);
+            ru_next = get3(u, n, rx, ry, z0);
         }
-        if (ring) {
-            su[(z0 - 1) & 1][(rj + 1) * kS3U + (ri + 1)] = get3(u, n, ex0 + ri, ey0 + rj, z0 - 1);
-            ring_next = get3(u, n, ex0 + ri, ey0 + rj, z0);
+        rb_next = get3(b, n, rx, ry, z0 - 1);
+    }
+    // outer u ring point of the last kT3Ring2 threads
+    const bool ro = !ZERO_U && t >= kS3Threads - kT3Ring2;
+    int oi = 0, oj = 0;
+    tile_ring_point(ro ? t - (kS3Threads - kT3Ring2) : 0, 2, oi, oj);
+    T o_next = T(0);
+    if (!ZERO_U) {
+        const int zb = (z0 - 1) & 1;
+#pragma unroll
+        for (int k = 0; k < kS3Pts; ++k) su[zb][(w + kT3Rows * k + 2) * kT3U + lane + 2] = u_cur[k];
+        if (rr) su[zb][(rj + 2) * kT3U + ri + 2] = ru_cur;
+        if (ro) {
+            su[zb][(oj + 2) * kT3U + oi + 2] = get3(u, n, ox0 + oi, oy0 + oj, z0 - 1);
+            o_next = get3(u, n, ox0 + oi, oy0 + oj, z0);
         }
         __syncthreads();
     }
 
+    // residual slots: s0 holds plane zz, s1 plane zz - 1, s2 plane zz - 2
+    int s0 = 0, s1 = 2, s2 = 1;
     for (int zz = z0 - 1; zz <= z1; ++zz) {  // residual plane zz, output plane zz - 1
         const int buf = zz & 1;
+        const bool zin = zz >= 0 && zz < n;
         T r_new[kS3Pts], u_nn[kS3Pts];
-        T ring_nn = T(0);
+        T ru_nn = T(0), o_nn = T(0);
         if (!ZERO_U) {
 #pragma unroll
-            for (int k = 0; k < kS3Pts; ++k) u_nn[k] = get3(u, n, px[k], py[k], zz + 2);
-            if (ring) ring_nn = get3(u, n, ex0 + ri, ey0 + rj, zz + 2);
+            for (int k = 0; k < kS3Pts; ++k) u_nn[k] = get3(u, n, px, oy0 + w + kT3Rows * k, zz + 2);
+            if (rr) ru_nn = get3(u, n, rx, ry, zz + 2);
+            if (ro) o_nn = get3(u, n, ox0 + oi, oy0 + oj, zz + 2);
         }
 #pragma unroll
         for (int k = 0; k < kS3Pts; ++k) {
-            const int i = px[k] - ex0, j = py[k] - ey0;
+            const int j = w + kT3Rows * k;
             T bb = b_next[k];
-            b_next[k] = get3(b, n, px[k], py[k], zz + 1);
+            b_next[k] = get3(b, n, px, oy0 + j, zz + 1);
             if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
             T r;
             if (!ZERO_U) {
-                const T *row = &su[buf][(j + 1) * kS3U + (i + 1)];
-                const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kS3U], row[kS3U])),
+                const T *row = &su[buf][(j + 2) * kT3U + lane + 2];
+                const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kT3U], row[kT3U])),
                                  radd(u_prev[k], u_next[k]));
                 r = radd(rfma(m6, u_cur[k], bb), s);
-                su[1 - buf][(j + 1) * kS3U + (i + 1)] = u_next[k];
+                su[1 - buf][(j + 2) * kT3U + lane + 2] = u_next[k];
             } else {
                 r = bb;
             }
-            if (!(inside[k] && zz >= 0 && zz < n)) r = T(0);
+            if (!(own[k] && zin)) r = T(0);
             if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
             r_new[k] = r;
-            sr[buf][j * kS3 + i] = r;
+            sr[s0][(j + 1) * kT3R + lane + 1] = r;
         }
-        if (ring) su[1 - buf][(rj + 1) * kS3U + (ri + 1)] = ring_next;
+        if (rr) {
+            T bb = rb_next;
+            rb_next = get3(b, n, rx, ry, zz + 1);
+            if (UNSCALED_B) bb = scale2(bb, hk);
+            T r;
+            if (!ZERO_U) {
+                const T *row = &su[buf][(rj + 2) * kT3U + ri + 2];
+                const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kT3U], row[kT3U])), radd(ru_prev, ru_next));
+                r = radd(rfma(m6, ru_cur, bb), s);
+                su[1 - buf][(rj + 2) * kT3U + ri + 2] = ru_next;
+            } else {
+                r = bb;
+            }
+            if (!(r_in && zin)) r = T(0);
+            sr[s0][(rj + 1) * kT3R + ri + 1] = r;
+        }
+        if (ro) su[1 - buf][(oj + 2) * kT3U + oi + 2] = o_next;
         if (zz - 1 >= z0) {
-            const T *rp = sr[1 - buf];  // plane zz - 1, written at the previous step
 #pragma unroll
             for (int k = 0; k < kS3Pts; ++k) {
                 if (!own[k]) continue;
-                const int i = px[k] - ex0, j = py[k] - ey0;
-                const T *row = &rp[j * kS3 + i];
-                const T E = radd(radd(radd(row[-1], row[1]), radd(row[-kS3], row[kS3])),
-                                 radd(r_m1[k], r_new[k]));
-                const T base = ZERO_U ? rmul(c0, r_0[k]) : rfma(c0, r_0[k], u_prev[k]);
-                out[(size_t)(zz - 1) * plane + (size_t)py[k] * n + px[k]] = rfma(c1, E, base);
+                const int j = w + kT3Rows * k, c = (j + 1) * kT3R + lane + 1;
+                const T *row = &sr[s1][c];
+                const T E = radd(radd(radd(row[-1], row[1]), radd(row[-kT3R], row[kT3R])), radd(sr[s2][c], r_new[k]));
+                const T base = ZERO_U ? rmul(c0, row[0]) : rfma(c0, row[0], u_prev[k]);
+                out[(size_t)(zz - 1) * plane + (size_t)(oy0 + j) * n + px] = rfma(c1, E, base);
             }
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kS3Pts; ++k) {
-            r_m1[k] = r_0[k];
-            r_0[k] = r_new[k];
             if (!ZERO_U) {
                 u_prev[k] = u_cur[k];
                 u_cur[k] = u_next[k];
                 u_next[k] = u_nn[k];
             }
         }
-        ring_next = ring_nn;
+        ru_prev = ru_cur;
+        ru_cur = ru_next;
+        ru_next = ru_nn;
+        o_next = o_nn;
+        const int sn = s2;
+        s2 = s1;
+        s1 = s0;
+        s0 = sn;
     }
 }
 
@@ -160,14 +212,14 @@ __device__ __forceinline__ void sweep3d_segment(T (&su)[2][kS3U * kS3U], T (&sr)
 // work, so the launch has no partly filled last wave (with 2 blocks per SM a
 // tile-by-z-chunk grid left up to half of a wave idle). One squared partial
 // sum per block. Resident blocks per SM: FP64 2 (no register cap that forces
-// spills; measured fastest against 1, 3 and 4), FP32 4.
+// spills; measured fastest against 1, 3 and 4), FP32 3 (4 spills).
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __global__ void __launch_bounds__(kS3Threads, sweep3d_blocks_per_sm((int)sizeof(T)))
 sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int bx, long total,
                long per, T c0, T c1, int hk, double *__restrict__ partials)
 {
-    __shared__ T su[2][kS3U * kS3U];
-    __shared__ T sr[2][kS3 * kS3];
+    __shared__ T su[2][kT3U * kT3U];
+    __shared__ T sr[3][kT3R * kT3R];
     double acc = 0.0;
     const long w0 = (long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
     for (long w = w0; w < w1;) {
@@ -631,10 +683,13 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 // ---------------------------------------------------------------------------
 // One block per resident slot, runs of at least 2 planes (small levels need
 // the blocks more than they mind the two extra residual planes of a run).
-S3Plan sweep3d_plan(int n, int elem_bytes)
+// wide: the 27-point sweep's 30-wide tiles, else the 7-point sweep's 32-wide
+// ones; the block count (one norm partial each) depends on which.
+S3Plan sweep3d_plan(int n, int elem_bytes, bool wide)
 {
     S3Plan g;
-    g.bx = (n + kS3Out - 1) / kS3Out;
+    const int edge = wide ? kS3Out : kT3;
+    g.bx = (n + edge - 1) / edge;
     g.total = (long)g.bx * g.bx * n;
     const long most = std::min<long>((long)sweep3d_blocks_per_sm(elem_bytes) * num_sms(), (g.total + 1) / 2);
     g.per = (g.total + most - 1) / most;
@@ -656,10 +711,10 @@ template <typename T>
 cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
                            double *partials, cudaStream_t s)
 {
-    const S3Plan g = sweep3d_plan(n, (int)sizeof(T));
+    const bool wide = sweep_is_wide(3, c);  // 27-point M (edge or corner weights)
+    const S3Plan g = sweep3d_plan(n, (int)sizeof(T), wide);
     const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]), c3 = T(c[3]);
-    const bool wide = c[2] != 0.0 || c[3] != 0.0;  // 27-point M (edge or corner weights)
 #define MG_SWEEP(ZU, UB, NRM)                                                                                     \
     do {                                                                                                          \
         if (wide)                                                                                                 \
