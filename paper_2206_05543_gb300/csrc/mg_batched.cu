@@ -16,7 +16,7 @@
 // One refinement iteration for all active problems:
 //   pre  : r_i = b_i - A u_i in FP64 (one launch per distinct N), written as
 //          the FP32 scaled right-hand side of level 0, per-problem ||r_i||^2,
-//          copied to pinned host memory;
+//          stored by the summing kernel into mapped pinned host memory;
 //   rest : the FP32 V cycle from zero on every level size, then u_i += e_i.
 // The host reads the norms once per iteration, retires converged problems
 // and uploads the new flags before the next launch.
@@ -43,14 +43,19 @@ namespace mg {
 // ---------------------------------------------------------------------------
 // small batched kernels
 // ---------------------------------------------------------------------------
+// per active problem: the sum of its partials into norm2[p] and into the
+// mapped pinned host array h_norm2 (read after the stream synchronises; no
+// device-to-host copy that could queue behind a caller's large copies)
 __global__ void batched_sums(const double *__restrict__ partials, const int *__restrict__ off,
-                             const int *__restrict__ cnt, const int *__restrict__ active, double *__restrict__ norm2)
+                             const int *__restrict__ cnt, const int *__restrict__ active, double *__restrict__ norm2,
+                             double *__restrict__ h_norm2)
 {
     const int p = blockIdx.x;
     if (!active[p]) return;
     double v = 0.0;
     for (int i = threadIdx.x; i < cnt[p]; i += blockDim.x) v += partials[off[p] + i];
-    block_sum_store<256>(v, &norm2[p]);
+    block_sum_store<256>(v, &norm2[p]);  // thread 0 stores it
+    if (threadIdx.x == 0) h_norm2[p] = norm2[p];
 }
 
 struct UpdItem {
@@ -162,7 +167,8 @@ struct BatchWork {
     int *op_off = nullptr, *op_cnt = nullptr;
     double *partials = nullptr;
     int *part_off = nullptr, *part_cnt = nullptr;
-    double *norm2 = nullptr, *h_norm2 = nullptr;
+    double *norm2 = nullptr, *h_norm2 = nullptr;  // h_norm2: mapped pinned
+    double *h_norm2_dev = nullptr;                 // its device address
     int *active = nullptr, *h_active = nullptr;
     UpdItem *upd = nullptr;
     std::vector<UpdItem> upd_host;
@@ -360,10 +366,10 @@ cudaError_t record_pre(mg_ctx *c, BatchWork *w)
         if ((e = launch_residual2d_batched<float>(G.res, (int)G.probs.size(), w->active, G.n, c->s, g.pitch, g.off)))
             return e;
     }
-    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2);
+    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2,
+                                             w->h_norm2_dev);
     count_launch(1);
-    if ((e = cudaGetLastError())) return e;
-    return cudaMemcpyAsync(w->h_norm2, w->norm2, (size_t)w->count * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -569,7 +575,8 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
         mg_destroy(c);
         return cuda_fail(ce);
     }
-    if (cudaMallocHost((void **)&w->h_norm2, count * sizeof(double)) != cudaSuccess ||
+    if (cudaHostAlloc((void **)&w->h_norm2, count * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&w->h_norm2_dev, w->h_norm2, 0) != cudaSuccess ||
         cudaMallocHost((void **)&w->h_active, count * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(c);

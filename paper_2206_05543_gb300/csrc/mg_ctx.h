@@ -57,9 +57,11 @@ struct mg_ctx {
     int npartials = 0;
     // d_norm2[0]: squared norm of the last residual; the word after it
     // (d_err) is set by a kernel whose bounded device-side wait gave up. Both
-    // reach the host together (kNormBytes) in pinned h_norm2.
+    // reach the host together (kNormBytes) in mapped pinned h_norm2, stored
+    // there by the kernel that forms the sum (h_norm2_dev: its device address).
     double *d_norm2 = nullptr;
-    double *h_norm2 = nullptr;  // pinned
+    double *h_norm2 = nullptr;  // mapped pinned
+    unsigned long long *h_norm2_dev = nullptr;
     int *d_err = nullptr;
     GraphPair g;
     const void *cap_u = nullptr, *cap_b = nullptr;

@@ -86,6 +86,32 @@ cudaError_t launch_sum_partials(const double *partials, int np, double *out, cud
     return cudaGetLastError();
 }
 
+// The same sum, and the kNormBytes that start at out (the sum and the error
+// word after it) stored into mapped pinned host memory as well. The host
+// reads them after the stream synchronises. A device-to-host copy would do
+// the same but can queue behind a caller's large copy on a copy engine, and
+// the solve waits for this value every cycle.
+__global__ void sum_partials_host_kernel(const double *__restrict__ p, int np, double *__restrict__ out,
+                                         unsigned long long *__restrict__ host)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) v += p[i];
+    block_sum_store<256>(v, out);  // thread 0 stores out[0]
+    if (threadIdx.x == 0) {
+        const unsigned long long *o = (const unsigned long long *)out;
+        host[0] = o[0];
+        host[1] = o[1];
+    }
+}
+
+static cudaError_t launch_sum_partials_host(const mg_ctx *c, int np, cudaStream_t s)
+{
+    static_assert(kNormBytes == 2 * sizeof(unsigned long long), "sum and error word");
+    sum_partials_host_kernel<<<1, 256, 0, s>>>(c->partials, np, c->d_norm2, c->h_norm2_dev);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void add_to_f64_kernel(double *__restrict__ u, const T *__restrict__ e, size_t np)
 {
@@ -484,8 +510,7 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
                                                 n0, c->partials, c->s);
             if (e) return e;
             const int np = fused ? sweep_partials(d, n0, (int)sizeof(T), c->c) : residual_partials(d, n0);
-            if ((e = launch_sum_partials(c->partials, np, c->d_norm2, c->s))) return e;
-            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, c->s);
+            return launch_sum_partials_host(c, np, c->s);
         });
         if (st != MG_OK) return st;
         if (fused) {
@@ -493,8 +518,7 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
                 cudaError_t e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials,
                                                   c->s);
                 if (e) return e;
-                if ((e = launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s))) return e;
-                return cudaMemcpyAsync(c->h_norm2, c->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, c->s);
+                return launch_sum_partials_host(c, residual_partials(d, n0), c->s);
             });
             if (st != MG_OK) return st;
         }
@@ -536,8 +560,7 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
                                                c->partials, c->s);
             }
             if (e) return e;
-            if ((e = launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s))) return e;
-            return cudaMemcpyAsync(c->h_norm2, c->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, c->s);
+            return launch_sum_partials_host(c, residual_partials(d, n0), c->s);
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
@@ -694,7 +717,9 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
             const int m = d == 2 ? 9 : 27;
             MG_TRYC(cudaMemcpy(c->lu, lu, (size_t)m * m * sizeof(double), cudaMemcpyHostToDevice));
         }
-        MG_TRYC(cudaMallocHost((void **)&c->h_norm2, kNormBytes));
+        MG_TRYC(cudaHostAlloc((void **)&c->h_norm2, kNormBytes, cudaHostAllocMapped));
+        MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_norm2_dev, c->h_norm2, 0));
+        std::memset(c->h_norm2, 0, kNormBytes);
     }
     *out = c;
     return MG_OK;
@@ -934,8 +959,7 @@ mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *no
                                                     n0, ctx->partials, ctx->s)
                         : op_residual<double, double>(ctx->d, (const double *)u, (const double *)b, true,
                                                       (double *)nullptr, n0, ctx->partials, ctx->s);
-    if (!e) e = launch_sum_partials(ctx->partials, residual_partials(ctx->d, n0), ctx->d_norm2, ctx->s);
-    if (!e) e = cudaMemcpyAsync(ctx->h_norm2, ctx->d_norm2, kNormBytes, cudaMemcpyDeviceToHost, ctx->s);
+    if (!e) e = launch_sum_partials_host(ctx, residual_partials(ctx->d, n0), ctx->s);
     st = e ? cuda_fail(e) : sync_ctx(ctx);
     if (st == MG_OK) *norm_out = norm_from_host(ctx);
     const mg_status st2 = leave(ctx);
