@@ -195,14 +195,13 @@ static cudaError_t op_residual(int d, const InT *u, const InT *b, bool unscaled,
     return d == 2 ? launch_residual2d<InT, OutT>(u, b, unscaled, rh, n, partials, s)
                   : launch_residual3d<InT, OutT>(u, b, unscaled, rh, n, partials, s);
 }
-// norm partials of a sweep with weights c
-static int sweep_partials(int d, int n, int elem_bytes, const double *c)
+static int sweep_partials(int d, int n, int elem_bytes)
 {
     if (d == 2) {
         const Grid2 g = sweep2d_grid(n);
         return g.bx * g.by;
     }
-    return sweep3d_plan(n, elem_bytes, sweep_is_wide(d, c)).blocks;
+    return sweep3d_plan(n, elem_bytes).blocks;
 }
 static int residual_partials(int d, int n)
 {
@@ -509,7 +508,7 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
                 e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr,
                                                 n0, c->partials, c->s);
             if (e) return e;
-            const int np = fused ? sweep_partials(d, n0, (int)sizeof(T), c->c) : residual_partials(d, n0);
+            const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
             return launch_sum_partials_host(c, np, c->s);
         });
         if (st != MG_OK) return st;
@@ -699,12 +698,7 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
                 for (void *p : {c->A[l], c->B[l], c->BH[l], c->RH[l]})
                     if (p) MG_TRYC(cudaMemset(p, 0, bytes));
         }
-        // any weights (mg_set_coeffs may switch the 3D sweep between its forms)
-        int np = residual_partials(d, c->n[0]);
-        for (int eb : {4, 8})
-            for (bool wide : {false, true})
-                np = std::max(np, d == 2 ? sweep_partials(2, c->n[0], eb, c->c)
-                                         : sweep3d_plan(c->n[0], eb, wide).blocks);
+        int np = std::max({sweep_partials(d, c->n[0], 8), sweep_partials(d, c->n[0], 4), residual_partials(d, c->n[0])});
         c->npartials = np;
         MG_TRY(dalloc(c, (void **)&c->partials, (size_t)np * sizeof(double)));
         MG_TRY(dalloc(c, (void **)&c->d_norm2, kNormBytes));
@@ -803,13 +797,13 @@ static mg_status op_sweep_t(int d, int n, const double *c, const void *u, const 
     double *partials = nullptr, *sum = nullptr;
     cudaError_t e;
     if (rnorm2) {
-        const int np = sweep_partials(d, n, (int)sizeof(T), c);
+        const int np = sweep_partials(d, n, (int)sizeof(T));
         if ((e = cudaMalloc(&partials, (size_t)np * sizeof(double) + sizeof(double)))) return cuda_fail(e);
         sum = partials + np;
     }
     e = op_sweep<T>(d, (const T *)u, (const T *)bh, unscaled != 0, (T *)out, n, c, partials, s);
     if (!e && rnorm2) {
-        e = launch_sum_partials(partials, sweep_partials(d, n, (int)sizeof(T), c), sum, s);
+        e = launch_sum_partials(partials, sweep_partials(d, n, (int)sizeof(T)), sum, s);
         if (!e) e = cudaMemcpyAsync(rnorm2, sum, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
     }

@@ -57,10 +57,7 @@ struct S3Plan {
     long total, per;
 };
 constexpr int sweep3d_blocks_per_sm(int elem_bytes) { return elem_bytes == 8 ? 2 : 3; }
-// wide: the 27-point sweep's tiling (the launch takes it when c[2] or c[3]
-// is non-zero); the block count, one norm partial each, depends on it
-S3Plan sweep3d_plan(int n, int elem_bytes, bool wide);
-inline bool sweep_is_wide(int d, const double *c) { return d == 3 && (c[2] != 0.0 || c[3] != 0.0); }
+S3Plan sweep3d_plan(int n, int elem_bytes);
 Grid3 residual3d_grid(int n);
 
 // 3D level operators (same conventions as the 2D ones; c = (c0, c1, c2, c3):

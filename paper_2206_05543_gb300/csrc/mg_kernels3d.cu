@@ -12,11 +12,17 @@
 
 namespace mg {
 
-constexpr int kS3 = 32;            // extended residual tile edge (sweep)
-constexpr int kS3Out = kS3 - 2;    // output tile edge (sweep)
-constexpr int kS3U = kS3 + 2;      // u plane edge incl. halo (sweep)
+// SPAI sweeps (7- and 27-point M): output tiles of kT3 x kT3 points
+constexpr int kT3 = 32;                  // output tile edge
+constexpr int kT3R = kT3 + 2;            // residual tile edge (tile + one-point ring)
+constexpr int kT3U = kT3 + 4;            // u plane edge (residual tile + one-point ring)
+constexpr int kT3Ring = 4 * (kT3 + 1);   // residual ring points (132)
+constexpr int kT3Ring2 = 4 * (kT3 + 3);  // outer u ring points (140)
 constexpr int kS3Threads = 256;
-constexpr int kS3Pts = kS3 * kS3 / kS3Threads;  // extended points per thread (4)
+constexpr int kS3Pts = kT3 * kT3 / kS3Threads;  // tile points per thread (4)
+constexpr int kT3Rows = kS3Threads / kT3;
+static_assert(kT3Ring <= kS3Threads && kT3Ring2 <= kS3Threads, "one ring point per thread");
+static_assert(kT3Rows * kS3Pts == kT3, "four rows per thread");
 
 template <typename T>
 __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
@@ -45,15 +51,6 @@ __device__ __forceinline__ T get3(const T *a, int n, int x, int y, int z)
 // 32-wide outputs an n = 2^k - 1 level needs no tile that is almost empty,
 // and every warp of the update has all its lanes busy.
 // ---------------------------------------------------------------------------
-constexpr int kT3 = 32;                  // output tile edge (7-point sweep)
-constexpr int kT3R = kT3 + 2;            // residual tile edge
-constexpr int kT3U = kT3 + 4;            // u plane edge
-constexpr int kT3Ring = 4 * (kT3 + 1);   // residual ring points (132)
-constexpr int kT3Ring2 = 4 * (kT3 + 3);  // outer u ring points (140)
-constexpr int kT3Rows = kS3Threads / kT3;
-static_assert(kT3Ring <= kS3Threads && kT3Ring2 <= kS3Threads, "one ring point per thread");
-static_assert(kT3Rows * kS3Pts == kT3, "four rows per thread");
-
 // point q of the ring at distance d (1 or 2) around the kT3 x kT3 tile,
 // tile-relative; the four sides have kT3 + 2d - 1 points each
 __device__ __forceinline__ void tile_ring_point(int q, int d, int &ri, int &rj)
@@ -245,65 +242,73 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 //   u' = fma(c3, C, fma(c2, E, fma(c1, F, fma(c0, rh_p, u_p))))
 // With c2 = c3 = 0 the face sum F is the 7-point sweep's E; the library uses
 // this kernel only when c2 or c3 is non-zero.
-// Thread t owns column i = t % 32 of the 32x32 residual tile and the four
-// consecutive rows 4 (t / 32) .. + 3: its x-pair sums hp of rows j - 1 ..
-// j + 4 serve P1 and P2 of all four rows. Per output point (rh, P1, P2) of
-// planes z - 1 and z stay in registers, plane z + 1's are formed at the step;
-// the residual plane goes through shared memory once (double-buffered, one
-// barrier per plane), the u plane as in the 7-point sweep.
+// The tiles are those of the 7-point sweep: a block owns a 32x32 output
+// tile, forms rh on it and on the one-point ring around it (threads
+// t < 132, one ring point each) and reads u planes of 36x36. Thread t owns
+// column i = t % 32 of the output tile and the four consecutive rows
+// 4 (t / 32) .. + 3: its x-pair sums hp of rows j - 1 .. j + 4 serve P1 and
+// P2 of all four rows. Per output point (rh, P1, P2) of planes z - 1 and z
+// stay in registers, plane z + 1's are formed at the step; the residual plane
+// goes through shared memory once (double-buffered, one barrier per plane).
 // ---------------------------------------------------------------------------
 template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
-__device__ __forceinline__ void sweep27_segment(T (&su)[2][kS3U * kS3U], T (&sr)[2][kS3 * kS3],
+__device__ __forceinline__ void sweep27_segment(T (&su)[2][kT3U * kT3U], T (&sr)[2][kT3R * kT3R],
                                                 const T *__restrict__ u, const T *__restrict__ b,
                                                 T *__restrict__ out, int n, int tx, int ty, int z0, int z1,
                                                 T c0, T c1, T c2, T c3, int hk, double &acc)
 {
     const int t = threadIdx.x;
-    const int i = t % kS3, j0 = kS3Pts * (t / kS3);
-    const int ex0 = tx * kS3Out - 1, ey0 = ty * kS3Out - 1;
-    const int px = ex0 + i;
+    const int i = t % kT3, j0 = kS3Pts * (t / kT3);
+    const int ox0 = tx * kT3, oy0 = ty * kT3;
+    const int px = ox0 + i;
     const size_t plane = (size_t)n * n;
     const T m6 = in_reg(T(-6));
     c0 = in_reg(c0);
     c1 = in_reg(c1);
     c2 = in_reg(c2);
     c3 = in_reg(c3);
-    const bool col_in = px >= 0 && px < n;
-    const bool col_own = col_in && i >= 1 && i <= kS3Out;
-    // neighbour columns in the residual tile (clamped: only owned columns use them)
-    const int il = i > 0 ? i - 1 : 0, ir = i < kS3 - 1 ? i + 1 : kS3 - 1;
 
-    bool inside[kS3Pts], own[kS3Pts];
+    bool own[kS3Pts];
     T u_prev[kS3Pts], u_cur[kS3Pts], u_next[kS3Pts], b_next[kS3Pts];
     T r_m[kS3Pts], r_c[kS3Pts], p1_m[kS3Pts], p1_c[kS3Pts], p2_m[kS3Pts], p2_c[kS3Pts];
 #pragma unroll
     for (int k = 0; k < kS3Pts; ++k) {
-        const int py = ey0 + j0 + k;
-        inside[k] = col_in && py >= 0 && py < n;
-        own[k] = inside[k] && col_own && j0 + k >= 1 && j0 + k <= kS3Out;
+        const int py = oy0 + j0 + k;
+        own[k] = px < n && py < n;
         u_prev[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0 - 2);
         u_cur[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0 - 1);
         u_next[k] = ZERO_U ? T(0) : get3(u, n, px, py, z0);
         b_next[k] = get3(b, n, px, py, z0 - 1);
         r_m[k] = r_c[k] = p1_m[k] = p1_c[k] = p2_m[k] = p2_c[k] = T(0);
     }
-    // the one-point u ring around the 32x32 tile, one point per thread t < 132
-    const bool ring = !ZERO_U && t < 4 * (kS3 + 1);
+    // residual ring point of threads t < kT3Ring
+    const bool rr = t < kT3Ring;
     int ri = 0, rj = 0;
-    if (ring) {
-        const int side = t / (kS3 + 1), q = t % (kS3 + 1);
-        if (side == 0) { ri = q - 1; rj = -1; }
-        else if (side == 1) { ri = kS3; rj = q - 1; }
-        else if (side == 2) { ri = q; rj = kS3; }
-        else { ri = -1; rj = q; }
+    tile_ring_point(rr ? t : 0, 1, ri, rj);
+    const int rx = ox0 + ri, ry = oy0 + rj;
+    const bool r_in = rr && rx >= 0 && rx < n && ry >= 0 && ry < n;
+    T ru_prev = T(0), ru_cur = T(0), ru_next = T(0), rb_next = T(0);
+    if (rr) {
+        if (!ZERO_U) {
+            ru_prev = get3(u, n, rx, ry, z0 - 2);
+            ru_cur = get3(u, n, rx, ry, z0 - 1);
+            ru_next = get3(u, n, rx, ry, z0);
+        }
+        rb_next = get3(b, n, rx, ry, z0 - 1);
     }
-    T ring_next = T(0);
+    // outer u ring point of the last kT3Ring2 threads
+    const bool ro = !ZERO_U && t >= kS3Threads - kT3Ring2;
+    int oi = 0, oj = 0;
+    tile_ring_point(ro ? t - (kS3Threads - kT3Ring2) : 0, 2, oi, oj);
+    T o_next = T(0);
     if (!ZERO_U) {
+        const int zb = (z0 - 1) & 1;
 #pragma unroll
-        for (int k = 0; k < kS3Pts; ++k) su[(z0 - 1) & 1][(j0 + k + 1) * kS3U + (i + 1)] = u_cur[k];
-        if (ring) {
-            su[(z0 - 1) & 1][(rj + 1) * kS3U + (ri + 1)] = get3(u, n, ex0 + ri, ey0 + rj, z0 - 1);
-            ring_next = get3(u, n, ex0 + ri, ey0 + rj, z0);
+        for (int k = 0; k < kS3Pts; ++k) su[zb][(j0 + k + 2) * kT3U + i + 2] = u_cur[k];
+        if (rr) su[zb][(rj + 2) * kT3U + ri + 2] = ru_cur;
+        if (ro) {
+            su[zb][(oj + 2) * kT3U + oi + 2] = get3(u, n, ox0 + oi, oy0 + oj, z0 - 1);
+            o_next = get3(u, n, ox0 + oi, oy0 + oj, z0);
         }
         __syncthreads();
     }
@@ -312,52 +317,67 @@ __device__ __forceinline__ void sweep27_segment(T (&su)[2][kS3U * kS3U], T (&sr)
         const int buf = zz & 1;
         const bool zin = zz >= 0 && zz < n;
         T r_n[kS3Pts], u_nn[kS3Pts];
-        T ring_nn = T(0);
+        T ru_nn = T(0), o_nn = T(0);
         if (!ZERO_U) {
 #pragma unroll
-            for (int k = 0; k < kS3Pts; ++k) u_nn[k] = get3(u, n, px, ey0 + j0 + k, zz + 2);
-            if (ring) ring_nn = get3(u, n, ex0 + ri, ey0 + rj, zz + 2);
+            for (int k = 0; k < kS3Pts; ++k) u_nn[k] = get3(u, n, px, oy0 + j0 + k, zz + 2);
+            if (rr) ru_nn = get3(u, n, rx, ry, zz + 2);
+            if (ro) o_nn = get3(u, n, ox0 + oi, oy0 + oj, zz + 2);
         }
         // residual of plane zz at the thread's four tile points
         T up = T(0), dn = T(0);
         if (!ZERO_U) {
-            up = su[buf][(j0) * kS3U + (i + 1)];                // row j0 - 1
-            dn = su[buf][(j0 + kS3Pts + 1) * kS3U + (i + 1)];   // row j0 + 4
+            up = su[buf][(j0 + 1) * kT3U + i + 2];           // row j0 - 1
+            dn = su[buf][(j0 + kS3Pts + 2) * kT3U + i + 2];  // row j0 + 4
         }
 #pragma unroll
         for (int k = 0; k < kS3Pts; ++k) {
             T bb = b_next[k];
-            b_next[k] = get3(b, n, px, ey0 + j0 + k, zz + 1);
+            b_next[k] = get3(b, n, px, oy0 + j0 + k, zz + 1);
             if (UNSCALED_B) bb = scale2(bb, hk);  // h^2 b, exact
             T r;
             if (!ZERO_U) {
-                const T *row = &su[buf][(j0 + k + 1) * kS3U + (i + 1)];
+                const T *row = &su[buf][(j0 + k + 2) * kT3U + i + 2];
                 const T us = k == 0 ? up : u_cur[k - 1];
                 const T un = k == kS3Pts - 1 ? dn : u_cur[k + 1];
                 const T s = radd(radd(radd(row[-1], row[1]), radd(us, un)), radd(u_prev[k], u_next[k]));
                 r = radd(rfma(m6, u_cur[k], bb), s);
-                su[1 - buf][(j0 + k + 1) * kS3U + (i + 1)] = u_next[k];
+                su[1 - buf][(j0 + k + 2) * kT3U + i + 2] = u_next[k];
             } else {
                 r = bb;
             }
-            if (!(inside[k] && zin)) r = T(0);
+            if (!(own[k] && zin)) r = T(0);
             if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
             r_n[k] = r;
-            sr[buf][(j0 + k) * kS3 + i] = r;
+            sr[buf][(j0 + k + 1) * kT3R + i + 1] = r;
         }
-        if (ring) su[1 - buf][(rj + 1) * kS3U + (ri + 1)] = ring_next;
+        if (rr) {
+            T bb = rb_next;
+            rb_next = get3(b, n, rx, ry, zz + 1);
+            if (UNSCALED_B) bb = scale2(bb, hk);
+            T r;
+            if (!ZERO_U) {
+                const T *row = &su[buf][(rj + 2) * kT3U + ri + 2];
+                const T s = radd(radd(radd(row[-1], row[1]), radd(row[-kT3U], row[kT3U])), radd(ru_prev, ru_next));
+                r = radd(rfma(m6, ru_cur, bb), s);
+                su[1 - buf][(rj + 2) * kT3U + ri + 2] = ru_next;
+            } else {
+                r = bb;
+            }
+            if (!(r_in && zin)) r = T(0);
+            sr[buf][(rj + 1) * kT3R + ri + 1] = r;
+        }
+        if (ro) su[1 - buf][(oj + 2) * kT3U + oi + 2] = o_next;
         __syncthreads();
-        if (col_own) {
-            // x-pair sums of rows j0 - 1 .. j0 + 4 (rows clamped into the tile:
-            // a clamped row only feeds rows that are not output)
+        {
+            // x-pair sums of rows j0 - 1 .. j0 + 4 of the residual plane
             const T *rp = sr[buf];
             T hp[kS3Pts + 2], rv[kS3Pts + 2];
 #pragma unroll
             for (int q = 0; q < kS3Pts + 2; ++q) {
-                int jr = j0 - 1 + q;
-                jr = jr < 0 ? 0 : (jr > kS3 - 1 ? kS3 - 1 : jr);
-                hp[q] = radd(rp[jr * kS3 + il], rp[jr * kS3 + ir]);
-                rv[q] = q >= 1 && q <= kS3Pts ? r_n[q - 1] : rp[jr * kS3 + i];
+                const T *row = &rp[(j0 + q) * kT3R + i + 1];  // row j0 - 1 + q, column i
+                hp[q] = radd(row[-1], row[1]);
+                rv[q] = q >= 1 && q <= kS3Pts ? r_n[q - 1] : row[0];
             }
 #pragma unroll
             for (int k = 0; k < kS3Pts; ++k) {
@@ -368,7 +388,7 @@ __device__ __forceinline__ void sweep27_segment(T (&su)[2][kS3U * kS3U], T (&sr)
                     const T E = radd(p2_c[k], radd(p1_m[k], p1));
                     const T C = radd(p2_m[k], p2);
                     const T base = ZERO_U ? rmul(c0, r_c[k]) : rfma(c0, r_c[k], u_prev[k]);
-                    out[(size_t)(zz - 1) * plane + (size_t)(ey0 + j0 + k) * n + px] =
+                    out[(size_t)(zz - 1) * plane + (size_t)(oy0 + j0 + k) * n + px] =
                         rfma(c3, C, rfma(c2, E, rfma(c1, F, base)));
                 }
                 p1_m[k] = p1_c[k];
@@ -387,7 +407,10 @@ __device__ __forceinline__ void sweep27_segment(T (&su)[2][kS3U * kS3U], T (&sr)
                 u_next[k] = u_nn[k];
             }
         }
-        ring_next = ring_nn;
+        ru_prev = ru_cur;
+        ru_cur = ru_next;
+        ru_next = ru_nn;
+        o_next = o_nn;
     }
     __syncthreads();  // the next segment refills both buffers
 }
@@ -398,8 +421,8 @@ __global__ void __launch_bounds__(kS3Threads, 1)
 sweep27_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__ out, int n, int bx, long total,
                long per, T c0, T c1, T c2, T c3, int hk, double *__restrict__ partials)
 {
-    __shared__ T su[2][kS3U * kS3U];
-    __shared__ T sr[2][kS3 * kS3];
+    __shared__ T su[2][kT3U * kT3U];
+    __shared__ T sr[2][kT3R * kT3R];
     double acc = 0.0;
     const long w0 = (long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
     for (long w = w0; w < w1;) {
@@ -683,13 +706,11 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
 // ---------------------------------------------------------------------------
 // One block per resident slot, runs of at least 2 planes (small levels need
 // the blocks more than they mind the two extra residual planes of a run).
-// wide: the 27-point sweep's 30-wide tiles, else the 7-point sweep's 32-wide
-// ones; the block count (one norm partial each) depends on which.
-S3Plan sweep3d_plan(int n, int elem_bytes, bool wide)
+// The 7- and 27-point sweeps share the tiles and the plan.
+S3Plan sweep3d_plan(int n, int elem_bytes)
 {
     S3Plan g;
-    const int edge = wide ? kS3Out : kT3;
-    g.bx = (n + edge - 1) / edge;
+    g.bx = (n + kT3 - 1) / kT3;
     g.total = (long)g.bx * g.bx * n;
     const long most = std::min<long>((long)sweep3d_blocks_per_sm(elem_bytes) * num_sms(), (g.total + 1) / 2);
     g.per = (g.total + most - 1) / most;
@@ -711,8 +732,8 @@ template <typename T>
 cudaError_t launch_sweep3d(const T *u, const T *b, bool unscaled, T *out, int n, const double *c,
                            double *partials, cudaStream_t s)
 {
-    const bool wide = sweep_is_wide(3, c);  // 27-point M (edge or corner weights)
-    const S3Plan g = sweep3d_plan(n, (int)sizeof(T), wide);
+    const bool wide = c[2] != 0.0 || c[3] != 0.0;  // 27-point M (edge or corner weights)
+    const S3Plan g = sweep3d_plan(n, (int)sizeof(T));
     const int hk = h2_exponent(n);
     const T c0 = T(c[0]), c1 = T(c[1]), c2 = T(c[2]), c3 = T(c[3]);
 #define MG_SWEEP(ZU, UB, NRM)                                                                                     \

@@ -60,7 +60,7 @@ int partials_needed(int d, int n, int elem_bytes)
         const mg::Grid2 g = mg::sweep2d_grid(n);
         return g.bx * g.by;
     }
-    return mg::sweep3d_plan(n, elem_bytes, false).blocks;  // 7-point M only (ncoeffs <= 2)
+    return mg::sweep3d_plan(n, elem_bytes).blocks;
 }
 
 template <typename T>
