@@ -79,10 +79,27 @@ __global__ void batched_update(const UpdItem *__restrict__ tab, const int *__res
     const int y0 = blockIdx.x * rows;
     if (y0 >= it.n) return;
     const int y1 = min(y0 + rows, it.n);
+    constexpr int kUnroll = 4;  // loads in flight per thread and row
     for (int y = y0; y < y1; ++y) {
         double *ur = it.u + (long long)y * it.n;
         const float *er = it.e + it.off + (long long)y * it.pitch;
-        for (int x = threadIdx.x; x < it.n; x += blockDim.x) ur[x] = __dadd_rn(ur[x], widen(er[x]));
+        for (int x0 = threadIdx.x; x0 < it.n; x0 += kUnroll * blockDim.x) {
+            double uv[kUnroll];
+            float ev[kUnroll];
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const int x = x0 + q * blockDim.x;
+                if (x < it.n) {
+                    uv[q] = ur[x];
+                    ev[q] = er[x];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const int x = x0 + q * blockDim.x;
+                if (x < it.n) ur[x] = __dadd_rn(uv[q], widen(ev[q]));
+            }
+        }
     }
 }
 
@@ -167,6 +184,8 @@ struct BatchWork {
     int *op_off = nullptr, *op_cnt = nullptr;
     double *partials = nullptr;
     int *part_off = nullptr, *part_cnt = nullptr;
+    BResGroup *rgroups = nullptr;  // the groups for the one-launch residual, descending n
+    int res_items = 0;
     double *norm2 = nullptr, *h_norm2 = nullptr;  // h_norm2: mapped pinned
     double *h_norm2_dev = nullptr;                 // its device address
     int *active = nullptr, *h_active = nullptr;
@@ -360,12 +379,8 @@ cudaError_t record_rest(mg_ctx *c, BatchWork *w)
 cudaError_t record_pre(mg_ctx *c, BatchWork *w)
 {
     cudaError_t e;
-    for (BatchGroup &G : w->groups)
-    {
-        const Pitch2 g = pitch2(G.n);
-        if ((e = launch_residual2d_batched<float>(G.res, (int)G.probs.size(), w->active, G.n, c->s, g.pitch, g.off)))
-            return e;
-    }
+    if ((e = launch_residual2d_batched_all(w->rgroups, (int)w->groups.size(), w->res_items, w->active, c->s)))
+        return e;
     batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2,
                                              w->h_norm2_dev);
     count_launch(1);
@@ -538,6 +553,8 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             BRes<float> *r = (BRes<float> *)a.take(G.probs.size() * sizeof(BRes<float>));
             if (real) G.res = r;
         }
+        BResGroup *rg = (BResGroup *)a.take(w->groups.size() * sizeof(BResGroup));
+        if (real) w->rgroups = rg;
         TailLevel *tl = (TailLevel *)a.take((size_t)count * kMaxTailLevels * sizeof(TailLevel));
         TailOp *to = (TailOp *)a.take(ops_all.size() * sizeof(TailOp));
         int *oo = (int *)a.take(count * sizeof(int)), *oc = (int *)a.take(count * sizeof(int));
@@ -664,6 +681,19 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             const int p = G.probs[j];
             G.host[j] = BRes<float>{nullptr, nullptr, w->BH[p][0], w->partials + part_off[p], p, 0};
         }
+    }
+    {
+        // groups of the one-launch residual, descending n
+        std::vector<BResGroup> rg;
+        int items = 0;
+        for (auto it = w->groups.rbegin(); it != w->groups.rend(); ++it) {
+            const Pitch2 g = pitch2(it->n);
+            BResGroup q{it->res, g.pitch, g.off, it->n, 0, 0, 0, 0, items};
+            items += residual2d_batched_group(q, (int)it->probs.size());
+            rg.push_back(q);
+        }
+        w->res_items = items;
+        errs.push_back(cudaMemcpy(w->rgroups, rg.data(), rg.size() * sizeof(BResGroup), cudaMemcpyHostToDevice));
     }
     w->upd_host.resize(count);
     for (int p = 0; p < count; ++p) {

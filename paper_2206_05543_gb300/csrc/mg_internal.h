@@ -93,6 +93,19 @@ struct BRes {  // FP64 residual of one problem's caller arrays
 template <typename OutT>
 cudaError_t launch_residual2d_batched(const BRes<OutT> *tab, int nprob, const int *active, int n, cudaStream_t s,
                                       long opitch = 0, long ooff = 0);
+// The batched FP64 residual of every finest size in one persistent launch:
+// group g holds the problems whose finest level has n points per axis (table
+// tab), its items are item0 .. item0 + nprob * bx * by - 1, written to the
+// padded FP32 layout (pitch, off) of that size. Groups in descending n.
+struct BResGroup {
+    const BRes<float> *tab;
+    long pitch, off;
+    int n, H, bx, by, hk, item0;
+};
+// fills g's launch geometry from g.n; returns its item count for nprob problems
+int residual2d_batched_group(BResGroup &g, int nprob);
+cudaError_t launch_residual2d_batched_all(const BResGroup *groups, int ngroups, int items, const int *active,
+                                          cudaStream_t s);
 int residual2d_batched_tiles(int n);
 // mode 0: every item from its u; 1: from zero; 2: per item (u == nullptr: from zero)
 cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, int mode,

@@ -462,6 +462,25 @@ residual2d_batched(const BRes<OutT> *__restrict__ tab, int nprob, const int *__r
     }
 }
 
+// All sizes in one launch: the item's group is found by a scan over the few
+// groups' first items (descending n: the large items are handed out first).
+__global__ void __launch_bounds__(kSweepThreads / 2, 12)
+residual2d_batched_all(const BResGroup *__restrict__ groups, int ngroups, int total, const int *__restrict__ active)
+{
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        int gi = 0;
+        while (gi + 1 < ngroups && it >= groups[gi + 1].item0) ++gi;
+        const BResGroup G = groups[gi];
+        const int local = it - G.item0, per = G.bx * G.by;
+        const int j = local / per, r = local - j * per;
+        const BRes<float> e = G.tab[j];
+        if (active[e.problem])
+            residual2d_tile<double, float>(e.u, e.b, e.out, G.n, G.H, G.hk, true, r % G.bx, r / G.bx, e.partials + r,
+                                           G.pitch, G.off);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -575,6 +594,25 @@ int residual2d_batched_tiles(int n)
 {
     const Grid2 g = residual2d_batched_grid(n);
     return g.bx * g.by;
+}
+
+int residual2d_batched_group(BResGroup &g, int nprob)
+{
+    const Grid2 q = residual2d_batched_grid(g.n);
+    g.H = q.H;
+    g.bx = q.bx;
+    g.by = q.by;
+    g.hk = h2_exponent(g.n);
+    return nprob * q.bx * q.by;
+}
+
+cudaError_t launch_residual2d_batched_all(const BResGroup *groups, int ngroups, int items, const int *active,
+                                          cudaStream_t s)
+{
+    const int grid = persistent_grid((const void *)residual2d_batched_all, kSweepThreads / 2, items);
+    residual2d_batched_all<<<grid, kSweepThreads / 2, 0, s>>>(groups, ngroups, items, active);
+    count_launch(1);
+    return cudaGetLastError();
 }
 
 template <typename OutT>
