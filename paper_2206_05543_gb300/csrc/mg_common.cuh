@@ -105,6 +105,116 @@ __device__ __forceinline__ OutT to_out(InT x)
         return x;
 }
 
+// ---------------------------------------------------------------------------
+// Sum of squares of FP64 values without FP64 arithmetic per term. The kernels
+// that form an FP64 residual also return its squared 2-norm, and one DFMA
+// per point for it was a thirteenth (sweep) to a sixth (refinement residual)
+// of the work of a pipe that bounds them. Each normal r = (h + l) 2^(ex-1023)
+// is split by integer operations into h = 1.f[51..29] (exact in FP32) and
+// l = f[28..6] 2^-46 (exact in FP32; the last six fraction bits are dropped,
+// 2^-46 of r); r^2 2^-2(ex-1023) = h^2 + 2hl (+ l^2, below 2^-45, dropped) is
+// the FP32 pair (p, q) = (h h, fma(2h, l, fma(h, h, -p))). It is added to a
+// float-float accumulator that carries its own power-of-two exponent (that of
+// the largest term so far), so no magnitude under- or overflows. The caller
+// flushes it (widened exactly, scaled on the exponent field, added to an FP64
+// total) at a loop boundary of its own, at most every 32 terms, which keeps a
+// counter out of the registers. Relative error of a thread's sum: about
+// 2^-44 per term plus 2^-47 per addition (all terms are positive). Zeros and
+// binary64 subnormals, whose squares are zero in FP64 as well, add nothing;
+// an infinity or a NaN makes the sum NaN. The FP32 operations are written as
+// intrinsics so that no contraction changes the two-sum.
+// ---------------------------------------------------------------------------
+constexpr int kSqNoExp = -8192;
+
+struct SqSum {
+    double total = 0.0;        // flushed part
+    float hi = 0.f, lo = 0.f;  // pending part (hi + lo) 2^e
+    int e = kSqNoExp;
+};
+
+__device__ __forceinline__ float sq_pow2f(int k)  // 2^k for -126 <= k <= 0
+{
+    return __int_as_float((k + 127) << 23);
+}
+
+// 2^k as a binary64 for -1022 <= k <= 1023
+__device__ __forceinline__ double sq_pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// v 2^k for a positive normal v: on the exponent field (exact) while the
+// result is normal; below that by two hardware multiplies, rounding into the
+// subnormal range as an FP64 square there would; infinity above
+__device__ __forceinline__ double sq_ldexp(double v, int k)
+{
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff) + k;
+    if (e >= 0x7ff) return __longlong_as_double(0x7ff0000000000000LL);
+    if (e <= 0) {
+        const int k1 = k / 2;  // k >= -2044 (a square's exponent): both factors are normal
+        return __dmul_rn(__dmul_rn(v, sq_pow2d(max(k1, -1022))), sq_pow2d(max(k - k1, -1022)));
+    }
+    return __longlong_as_double((b & ~(0x7ffLL << 52)) | ((long long)e << 52));
+}
+
+__device__ __forceinline__ void sq_flush(SqSum &a)
+{
+    if (a.hi > 0.f) a.total = __dadd_rn(a.total, sq_ldexp(__dadd_rn(widen(a.hi), widen(a.lo)), a.e));
+    a.hi = 0.f;
+    a.lo = 0.f;
+    a.e = kSqNoExp;
+}
+
+__device__ __forceinline__ void sq_add(SqSum &a, double r)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+    const int ex = (int)(bits >> 52) & 0x7ff;
+    if (ex == 0) return;  // zero or subnormal
+    if (ex == 0x7ff) {    // infinity or NaN
+        a.total = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const float h = __int_as_float(0x3f800000 | (int)((bits >> 29) & 0x7fffffu));
+    const float m = __fsub_rn(__int_as_float(0x4b000000 | (int)((bits >> 6) & 0x7fffffu)), 8388608.f);
+    const float l = __fmul_rn(m, 0x1p-46f);
+    const float p = __fmul_rn(h, h);
+    float tq = __fmaf_rn(__fadd_rn(h, h), l, __fmaf_rn(h, h, -p));
+    float tp = p;
+    const int et = 2 * (ex - 1023);
+    if (et > a.e) {  // the accumulator moves to the new exponent
+        const float sc = sq_pow2f(max(a.e - et, -126));
+        a.hi = __fmul_rn(a.hi, sc);
+        a.lo = __fmul_rn(a.lo, sc);
+        a.e = et;
+    } else {
+        const float sc = sq_pow2f(max(et - a.e, -126));
+        tp = __fmul_rn(tp, sc);
+        tq = __fmul_rn(tq, sc);
+    }
+    // (hi, lo) += (tp, tq): two-sum of the heads, tails added, renormalised
+    const float sh = __fadd_rn(a.hi, tp);
+    const float bv = __fsub_rn(sh, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(sh, bv)), __fsub_rn(tp, bv));
+    const float tl = __fadd_rn(__fadd_rn(err, a.lo), tq);
+    a.hi = __fadd_rn(sh, tl);
+    a.lo = __fsub_rn(tl, __fsub_rn(a.hi, sh));
+}
+__device__ __forceinline__ void sq_add(SqSum &a, float r) { sq_add(a, widen(r)); }
+
+__device__ __forceinline__ double sq_value(SqSum &a)
+{
+    sq_flush(a);
+    return a.total;
+}
+
+// The same interface with one FP64 FMA per term, for kernels whose register
+// budget the accumulator above would overrun (they spill with it)
+struct Fp64Sum {
+    double total = 0.0;
+};
+__device__ __forceinline__ void sq_add(Fp64Sum &a, double r) { a.total = fma(r, r, a.total); }
+__device__ __forceinline__ void sq_add(Fp64Sum &a, float r) { sq_add(a, widen(r)); }
+__device__ __forceinline__ void sq_flush(Fp64Sum &) {}
+__device__ __forceinline__ double sq_value(Fp64Sum &a) { return a.total; }
+
 // x * 2^k for a power-of-two scale, done on the exponent field with integer
 // instructions when x and the result are normal numbers (then the product is
 // exact, so the result equals __dmul_rn(x, 2^k) bit for bit); zeros,

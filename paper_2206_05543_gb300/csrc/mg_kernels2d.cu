@@ -88,7 +88,7 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) bcur[k] = get(b, y0 - 1, xc0 + k);
-    double acc = 0.0;
+    SqSum acc;
     for (int j = y0 - 1; j <= y1; ++j) {
         const int buf = j & 1;
         T f[K], r[K];
@@ -124,9 +124,10 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (!(in[k] && jin)) r[k] = T(0);
-            if (NORM && own[k] && j >= y0 && j < y1) acc = fma(to_out<double>(r[k]), to_out<double>(r[k]), acc);
+            if (NORM && own[k] && j >= y0 && j < y1) sq_add(acc, r[k]);
             sr[buf][K * t + k + 1] = r[k];
         }
+        if (NORM && (j & 15) == 15) sq_flush(acc);  // at most 32 terms pending
         __syncthreads();
         T p[K];
         {
@@ -162,7 +163,7 @@ __device__ __forceinline__ void sweep2d_tile(const T *__restrict__ u, const T *_
         }
         hn = hnn;
     }
-    if (NORM) block_sum_store<NT>(acc, partial);
+    if (NORM) block_sum_store<NT>(sq_value(acc), partial);
 }
 
 // 128 threads, two columns each; the occupancy bound (10 blocks per SM)
@@ -355,9 +356,10 @@ prolong2d_kernel(const T *__restrict__ e, T *__restrict__ u, int n, int Hc)
 // as in the sweep, written as OutT (the cycle's precision) together with one
 // partial sum of rh^2 per block. Same layout as the sweep: 128 threads, two
 // adjacent columns each (columns 1 .. 254 of the strip are written), one
-// barrier per row, loads one step ahead.
+// barrier per row, loads one step ahead. Acc: the squared-norm accumulator
+// (SqSum off the FP64 pipe; Fp64Sum where registers are short).
 // ---------------------------------------------------------------------------
-template <typename InT, typename OutT>
+template <typename InT, typename OutT, typename Acc = SqSum>
 __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const InT *__restrict__ b,
                                                 OutT *__restrict__ rh_out, int n, int H, int hk, bool unscaled,
                                                 int tbx, int tby, double *__restrict__ partial, long opitch = 0,
@@ -387,7 +389,7 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
     if (rt) su[y0 & 1][kSweepThreads + 1] = get(u, y0, xb + 1);
     InT fa_next = get(b, y0, xa), fb_next = get(b, y0, xb);
     __syncthreads();
-    double acc = 0.0;
+    Acc acc;
     for (int j = y0; j < y1; ++j) {
         const int buf = j & 1;
         InT fa = fa_next, fb = fb_next;
@@ -405,13 +407,14 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
             rb = radd(rfma(InT(-4), bc, fb), radd(radd(ac, su[buf][2 * t + 3]), radd(bp, bn)));
         }
         if (owna) {
-            acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
+            sq_add(acc, ra);
             if (rh_out) rh_out[opitch ? ooff + j * opitch + xa : (long)j * ld + xa] = to_out<OutT>(ra);
         }
         if (ownb) {
-            acc = fma(to_out<double>(rb), to_out<double>(rb), acc);
+            sq_add(acc, rb);
             if (rh_out) rh_out[opitch ? ooff + j * opitch + xb : (long)j * ld + xb] = to_out<OutT>(rb);
         }
+        if ((j & 15) == 15) sq_flush(acc);  // at most 32 terms pending
         su[1 - buf][2 * t + 1] = an;
         su[1 - buf][2 * t + 2] = bn;
         if (lt) su[1 - buf][0] = hn;
@@ -425,7 +428,7 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
         bn = bnn;
         hn = hnn;
     }
-    if (partial) block_sum_store<NT>(acc, partial);
+    if (partial) block_sum_store<NT>(sq_value(acc), partial);
 }
 
 // at most 12 blocks per SM (measured fastest for the FP64 form)
@@ -456,8 +459,8 @@ residual2d_batched(const BRes<OutT> *__restrict__ tab, int nprob, const int *__r
         const int j = it / per, r = it - j * per;
         const BRes<OutT> e = tab[j];
         if (active[e.problem])
-            residual2d_tile<double, OutT>(e.u, e.b, e.out, n, H, hk, true, r % bx, r / bx, e.partials + r, opitch,
-                                          ooff);
+            residual2d_tile<double, OutT, Fp64Sum>(e.u, e.b, e.out, n, H, hk, true, r % bx, r / bx, e.partials + r,
+                                                   opitch, ooff);
         __syncthreads();
     }
 }
@@ -475,8 +478,8 @@ residual2d_batched_all(const BResGroup *__restrict__ groups, int ngroups, int to
         const int j = local / per, r = local - j * per;
         const BRes<float> e = G.tab[j];
         if (active[e.problem])
-            residual2d_tile<double, float>(e.u, e.b, e.out, G.n, G.H, G.hk, true, r % G.bx, r / G.bx, e.partials + r,
-                                           G.pitch, G.off);
+            residual2d_tile<double, float, Fp64Sum>(e.u, e.b, e.out, G.n, G.H, G.hk, true, r % G.bx, r / G.bx,
+                                                    e.partials + r, G.pitch, G.off);
         __syncthreads();
     }
 }

@@ -68,7 +68,7 @@ template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __device__ __forceinline__ void sweep3d_segment(T (&su)[2][kT3U * kT3U], T (&sr)[3][kT3R * kT3R],
                                                 const T *__restrict__ u, const T *__restrict__ b,
                                                 T *__restrict__ out, int n, int tx, int ty, int z0, int z1,
-                                                T c0, T c1, int hk, double &acc)
+                                                T c0, T c1, int hk, SqSum &acc)
 {
     const int t = threadIdx.x, lane = t % kT3, w = t / kT3;
     const int ox0 = tx * kT3, oy0 = ty * kT3;
@@ -151,10 +151,11 @@ __device__ __forceinline__ void sweep3d_segment(T (&su)[2][kT3U * kT3U], T (&sr)
                 r = bb;
             }
             if (!(own[k] && zin)) r = T(0);
-            if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
+            if (NORM && own[k] && zz >= z0 && zz < z1) sq_add(acc, r);
             r_new[k] = r;
             sr[s0][(j + 1) * kT3R + lane + 1] = r;
         }
+        if (NORM && (zz & 7) == 7) sq_flush(acc);  // at most 32 terms pending
         if (rr) {
             T bb = rb_next;
             rb_next = get3(b, n, rx, ry, zz + 1);
@@ -217,7 +218,7 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 {
     __shared__ T su[2][kT3U * kT3U];
     __shared__ T sr[3][kT3R * kT3R];
-    double acc = 0.0;
+    SqSum acc;
     const long w0 = (long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
     for (long w = w0; w < w1;) {
         const int tile = (int)(w / n), z0 = (int)(w - (long)tile * n);
@@ -226,7 +227,7 @@ sweep3d_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
                                                      hk, acc);
         w += z1 - z0;
     }
-    if (NORM) block_sum_store<kS3Threads>(acc, &partials[blockIdx.x]);
+    if (NORM) block_sum_store<kS3Threads>(sq_value(acc), &partials[blockIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,7 +256,7 @@ template <typename T, bool ZERO_U, bool UNSCALED_B, bool NORM>
 __device__ __forceinline__ void sweep27_segment(T (&su)[2][kT3U * kT3U], T (&sr)[2][kT3R * kT3R],
                                                 const T *__restrict__ u, const T *__restrict__ b,
                                                 T *__restrict__ out, int n, int tx, int ty, int z0, int z1,
-                                                T c0, T c1, T c2, T c3, int hk, double &acc)
+                                                T c0, T c1, T c2, T c3, int hk, SqSum &acc)
 {
     const int t = threadIdx.x;
     const int i = t % kT3, j0 = kS3Pts * (t / kT3);
@@ -347,10 +348,11 @@ __device__ __forceinline__ void sweep27_segment(T (&su)[2][kT3U * kT3U], T (&sr)
                 r = bb;
             }
             if (!(own[k] && zin)) r = T(0);
-            if (NORM && own[k] && zz >= z0 && zz < z1) acc = fma(to_out<double>(r), to_out<double>(r), acc);
+            if (NORM && own[k] && zz >= z0 && zz < z1) sq_add(acc, r);
             r_n[k] = r;
             sr[buf][(j0 + k + 1) * kT3R + i + 1] = r;
         }
+        if (NORM && (zz & 7) == 7) sq_flush(acc);  // at most 32 terms pending
         if (rr) {
             T bb = rb_next;
             rb_next = get3(b, n, rx, ry, zz + 1);
@@ -423,7 +425,7 @@ sweep27_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
 {
     __shared__ T su[2][kT3U * kT3U];
     __shared__ T sr[2][kT3R * kT3R];
-    double acc = 0.0;
+    SqSum acc;
     const long w0 = (long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
     for (long w = w0; w < w1;) {
         const int tile = (int)(w / n), z0 = (int)(w - (long)tile * n);
@@ -432,7 +434,7 @@ sweep27_kernel(const T *__restrict__ u, const T *__restrict__ b, T *__restrict__
                                                      c3, hk, acc);
         w += z1 - z0;
     }
-    if (NORM) block_sum_store<kS3Threads>(acc, &partials[blockIdx.x]);
+    if (NORM) block_sum_store<kS3Threads>(sq_value(acc), &partials[blockIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -623,7 +625,7 @@ constexpr int kQRing = 2 * kQX + 2 * kQY;  // 144 ring points, one per thread t 
 
 // at most 6 blocks per SM (42 registers; measured fastest for the FP64 form)
 template <typename InT, typename OutT>
-__global__ void __launch_bounds__(kQThreads, 6)
+__global__ void __launch_bounds__(kQThreads, 5)
 residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out, int n,
                   int Z, int hk, bool unscaled, double *__restrict__ partials, long opitch, long oplane, long ooff)
 {
@@ -656,7 +658,7 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         ring_next = get3(u, n, X0 + ri, Y0 + rj, z0 + 1);
     }
     __syncthreads();
-    double acc = 0.0;
+    SqSum acc;
     for (int z = z0; z < z1; ++z) {
         const int buf = z & 1;
         InT fa = fa_next, fb = fb_next;
@@ -674,17 +676,18 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         const InT ra = radd(rfma(InT(-6), ac, fa), sa);
         const InT rb = radd(rfma(InT(-6), bc, fb), sb);
         if (owna) {
-            acc = fma(to_out<double>(ra), to_out<double>(ra), acc);
+            sq_add(acc, ra);
             if (rh_out)
                 rh_out[opitch ? ooff + z * oplane + (long)y * opitch + xa : ((long)z * n + y) * n + xa] =
                     to_out<OutT>(ra);
         }
         if (ownb) {
-            acc = fma(to_out<double>(rb), to_out<double>(rb), acc);
+            sq_add(acc, rb);
             if (rh_out)
                 rh_out[opitch ? ooff + z * oplane + (long)y * opitch + xb : ((long)z * n + y) * n + xb] =
                     to_out<OutT>(rb);
         }
+        if ((z & 15) == 15) sq_flush(acc);  // at most 32 terms pending
         su[1 - buf][ia] = an;
         su[1 - buf][ia + 1] = bn;
         if (ring) su[1 - buf][ir] = ring_next;
@@ -698,7 +701,7 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         ring_next = ring_nn;
     }
     if (partials)
-        block_sum_store<kQThreads>(acc, &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
+        block_sum_store<kQThreads>(sq_value(acc), &partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x]);
 }
 
 // ---------------------------------------------------------------------------

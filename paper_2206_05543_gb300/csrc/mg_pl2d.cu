@@ -73,7 +73,7 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
     }
     bn = row4(Bp, y0 - 1, x);
     if (lt || rt) hb = row1(Bp, y0 - 1, xh);
-    double acc = 0.0;
+    SqSum acc;
     // refinement epilogue: each warp stages its 128 FP32 results in shared
     // memory and lane l updates the FP64 columns xw + l + 32 k (k < 4), so
     // every FP64 access of the warp covers 256 contiguous bytes; the FP64
@@ -121,7 +121,8 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
             if (!(jin && x + k < n)) c4(r, k) = 0.f;
         if ((lt || rt) && !(jin && xh >= 0 && xh < n)) rh = 0.f;
         if (NORM && j >= y0 && j < y1)
-            for (int k = 0; k < 4; ++k) acc = fma(widen(c4(r, k)), widen(c4(r, k)), acc);
+            for (int k = 0; k < 4; ++k) sq_add(acc, c4(r, k));
+        if (NORM && (j & 7) == 7) sq_flush(acc);  // at most 32 terms pending
         st4(&sr[buf][4 + 4 * t], r);
         if (lt) sr[buf][3] = rh;
         if (rt) sr[buf][kPLCols + 4] = rh;
@@ -165,7 +166,7 @@ __device__ __forceinline__ void sweep2d_pl_tile(const float *__restrict__ u, con
         if (ACC64)
             for (int k = 0; k < 4; ++k) u64c[k] = u64n[k];
     }
-    if (NORM) block_sum_store<kPLThreads>(acc, partial);
+    if (NORM) block_sum_store<kPLThreads>(sq_value(acc), partial);
 }
 
 template <bool ZERO_U, bool NORM>
