@@ -490,11 +490,14 @@ residual2d_batched_all(const BResGroup *__restrict__ groups, int ngroups, int to
 
 constexpr int kBatchedResidualRows = 32;
 
+// Row chunks sized for about one wave of resident blocks (10 per SM, the
+// occupancy bound of the sweep and the restriction); fewer, taller chunks
+// save prologue rows but measured slower (8 or fewer per SM), more did not help
 Grid2 sweep2d_grid(int n)
 {
     Grid2 g;
     g.bx = (n + kSweepCols - 1) / kSweepCols;
-    g.H = chunk_rows(g.bx, n, 8 * num_sms(), 2, 64);
+    g.H = chunk_rows(g.bx, n, 10 * num_sms(), 2, 64);
     g.by = (n + g.H - 1) / g.H;
     return g;
 }
@@ -533,7 +536,7 @@ cudaError_t launch_resrestrict2d(const T *u, const T *b, bool unscaled, T *bc, i
 {
     const int nc = (n - 1) / 2;
     const int bx = (nc + kRestrictCols - 1) / kRestrictCols;
-    const int Hc = chunk_rows(bx, nc, 8 * num_sms(), 1, 32);
+    const int Hc = chunk_rows(bx, nc, 10 * num_sms(), 1, 32);
     const dim3 grid(bx, (nc + Hc - 1) / Hc);
     const int hk = h2_exponent(n);
     if (unscaled)
