@@ -342,6 +342,12 @@ __device__ __forceinline__ Row8 interp_x8(float2 e2)
     return v;
 }
 
+constexpr int kF64Lead = 2;  // steps between the L2 prefetch and the load of an FP64 row (2, 4, 8: 2 fastest)
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // float4s of shared memory per warp of pass B: u1 and bh rings (float4),
 // the e ring (float2) and, ACC64, the staging row of the FP64 epilogue
 constexpr int kRing4 = kFSlots * 32;
@@ -432,6 +438,14 @@ __device__ __forceinline__ void prolong_sweep2d_tile(const float *__restrict__ u
 #pragma unroll
             for (int q = 0; q < kFC; ++q) a64[q] = a64n[q];
             load64(Q - 1, a64n);
+            // the FP64 row kF64Lead steps on into L2: the one-step register
+            // load above then waits for L2 instead of DRAM (lanes 0..7 touch
+            // one 128-byte line each of the warp's 960 bytes)
+            const int jp = Q - 1 + kF64Lead;
+            if (lane < 8 && jp >= y0 && jp < y1) {
+                const int col = min(max(xw + 16 * lane, 0), n - 1);
+                prefetch_l2(u64 + (long)jp * n + col);
+            }
         }
         issue_step(Q + kFDepth);
         // here vcur = x pass of coarse row mQ + 1, vprev = of mQ

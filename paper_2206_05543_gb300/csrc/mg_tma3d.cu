@@ -111,6 +111,7 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map
 // ACC64 (the last post-sweep of a refinement cycle): instead of storing the
 // FP32 result, add it to the caller's FP64 solution (compact n^3 array),
 // whose values are loaded at the start of the step that updates them.
+constexpr int kF64Lead = 2;  // planes between the L2 prefetch and the load of an FP64 row (2 and 4 alike)
 template <bool ZERO_U, bool ACC64 = false>
 __global__ void __launch_bounds__(kTThreads + 32, 2)
 sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant__ CUtensorMap tb,
@@ -206,6 +207,11 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
             const double *ur = u64 + ((long)(zz - 1) * n + yr) * n + x0 + lane;
             for (int k = 0; k < 4; ++k)
                 if (x0 + lane + 32 * k < n) u64v[k] = ur[32 * k];
+            // the row of plane zz - 1 + kF64Lead into L2 (lanes 0..7: one
+            // 128-byte line each of the warp's 1 KB), for the load above later
+            const int zp = zz - 1 + kF64Lead;
+            if (lane < 8 && zp < z1)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(u64 + ((long)zp * n + yr) * n + min(x0 + 16 * lane, n - 1)));
         }
         // A. scaled residual of plane zz (zero outside the interior)
         const unsigned m = (zz >= 0 && zz < n) ? xmask : 0u;
