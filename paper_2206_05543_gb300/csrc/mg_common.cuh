@@ -215,6 +215,10 @@ __device__ __forceinline__ void sq_add(Fp64Sum &a, float r) { sq_add(a, widen(r)
 __device__ __forceinline__ void sq_flush(Fp64Sum &) {}
 __device__ __forceinline__ double sq_value(Fp64Sum &a) { return a.total; }
 
+// fetch the 128-byte line at p into L2 (no register result, no fault on a
+// valid address); callers pass addresses inside their arrays
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // x * 2^k for a power-of-two scale, done on the exponent field with integer
 // instructions when x and the result are normal numbers (then the product is
 // exact, so the result equals __dmul_rn(x, 2^k) bit for bit); zeros,

@@ -343,10 +343,6 @@ __device__ __forceinline__ Row8 interp_x8(float2 e2)
 }
 
 constexpr int kF64Lead = 2;  // steps between the L2 prefetch and the load of an FP64 row (2, 4, 8: 2 fastest)
-__device__ __forceinline__ void prefetch_l2(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 
 // float4s of shared memory per warp of pass B: u1 and bh rings (float4),
 // the e ring (float2) and, ACC64, the staging row of the FP64 epilogue

@@ -211,7 +211,7 @@ sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tu, const __grid_constant
             // 128-byte line each of the warp's 1 KB), for the load above later
             const int zp = zz - 1 + kF64Lead;
             if (lane < 8 && zp < z1)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(u64 + ((long)zp * n + yr) * n + min(x0 + 16 * lane, n - 1)));
+                prefetch_l2(u64 + ((long)zp * n + yr) * n + min(x0 + 16 * lane, n - 1));
         }
         // A. scaled residual of plane zz (zero outside the interior)
         const unsigned m = (zz >= 0 && zz < n) ? xmask : 0u;
