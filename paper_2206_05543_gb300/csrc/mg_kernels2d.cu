@@ -431,14 +431,17 @@ __device__ __forceinline__ void residual2d_tile(const InT *__restrict__ u, const
     if (partial) block_sum_store<NT>(sq_value(acc), partial);
 }
 
-// at most 12 blocks per SM (measured fastest for the FP64 form)
-template <typename InT, typename OutT>
+// at most 12 blocks per SM (measured fastest for the FP64 form); UNSC and
+// PAD (padded output layout) are compile-time so that the inlined tile
+// carries neither choice in registers
+template <typename InT, typename OutT, bool UNSC, bool PAD>
 __global__ void __launch_bounds__(kSweepThreads / 2, 12)
 residual2d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__restrict__ rh_out,
-                  int n, int H, int hk, bool unscaled, double *__restrict__ partials, long opitch, long ooff)
+                  int n, int H, int hk, double *__restrict__ partials, long opitch, long ooff)
 {
-    residual2d_tile<InT, OutT>(u, b, rh_out, n, H, hk, unscaled, blockIdx.x, blockIdx.y,
-                               partials ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr, opitch, ooff);
+    residual2d_tile<InT, OutT>(u, b, rh_out, n, H, hk, UNSC, blockIdx.x, blockIdx.y,
+                               partials ? &partials[blockIdx.y * gridDim.x + blockIdx.x] : nullptr,
+                               PAD ? opitch : 0, PAD ? ooff : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -564,8 +567,21 @@ cudaError_t launch_residual2d(const InT *u, const InT *b, bool unscaled, OutT *r
                               cudaStream_t s, long out_pitch, long out_off)
 {
     const Grid2 g = sweep2d_grid(n);
-    residual2d_kernel<InT, OutT><<<dim3(g.bx, g.by), kSweepThreads / 2, 0, s>>>(u, b, rh, n, g.H, h2_exponent(n),
-                                                                           unscaled, partials, out_pitch, out_off);
+    const dim3 grid(g.bx, g.by);
+    const int hk = h2_exponent(n);
+    const bool pad = out_pitch != 0;
+    if (unscaled && pad)
+        residual2d_kernel<InT, OutT, true, true><<<grid, kSweepThreads / 2, 0, s>>>(u, b, rh, n, g.H, hk, partials,
+                                                                                  out_pitch, out_off);
+    else if (unscaled)
+        residual2d_kernel<InT, OutT, true, false><<<grid, kSweepThreads / 2, 0, s>>>(u, b, rh, n, g.H, hk, partials,
+                                                                                   out_pitch, out_off);
+    else if (pad)
+        residual2d_kernel<InT, OutT, false, true><<<grid, kSweepThreads / 2, 0, s>>>(u, b, rh, n, g.H, hk, partials,
+                                                                                   out_pitch, out_off);
+    else
+        residual2d_kernel<InT, OutT, false, false><<<grid, kSweepThreads / 2, 0, s>>>(u, b, rh, n, g.H, hk, partials,
+                                                                                    out_pitch, out_off);
     count_launch(1);
     return cudaGetLastError();
 }
