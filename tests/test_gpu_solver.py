@@ -89,6 +89,17 @@ def test_3d_sine_and_jacobi():
     _parity(3, 32, inputs.uniform(3, 32, 3), name="jacobi", max_cycles=80)
 
 
+@pytest.mark.parametrize("N", [16, 64])
+def test_3d_w_cycles_and_random_start(N):
+    """W(1+0) and W(2,2) in 3D with M7 and the paper's uniform (0,1)
+    initial guess (Sec. 4, Example 3 compares V and W cycles): iterates,
+    cycle counts and histories against the oracle."""
+    b = inputs.uniform(3, N, 5)
+    u0 = np.random.default_rng(11).uniform(0.0, 1.0, b.shape)
+    _parity(3, N, b, nu1=1, nu2=0, gamma=2, u0=u0, max_cycles=80)
+    _parity(3, N, b, nu1=2, nu2=2, gamma=2)
+
+
 def test_final_measurement_guess_that_misses():
     """The solver replaces the speculative pre-sweep by a residual-norm-only
     pass when the last convergence factor, carried one cycle forward, puts the
@@ -166,7 +177,8 @@ def test_invalid_arguments_raise():
             s.solve(dev(np.zeros((64, 64))))
 
 
-@pytest.mark.parametrize("d,N,nu,tol_u", [(2, 256, 1, 1e-8), (2, 1024, 1, 1e-8), (3, 32, 2, 1e-8), (3, 64, 2, 1e-8)])
+@pytest.mark.parametrize("d,N,nu,tol_u", [(2, 256, 1, 1e-8), (2, 1024, 1, 1e-8), (3, 32, 2, 1e-8), (3, 64, 2, 1e-8),
+                                          (3, 64, 1, 1e-8), (3, 128, 1, 1e-8)])
 def test_mixed_precision_refinement(d, N, nu, tol_u):
     """FP32 cycle inside FP64 refinement reaches the FP64 tolerance 1e-10.
     Check: the oracle's FP64 residual of the result and the distance to the
