@@ -658,6 +658,9 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         ring_next = get3(u, n, X0 + ri, Y0 + rj, z0 + 1);
     }
     __syncthreads();
+    // -6 from a register: a DFMA with a constant-bank operand issues at the
+    // DADD rate (measured 2D: no gain, its register budget is tighter)
+    const InT m6 = in_reg(InT(-6));
     SqSum acc;
     for (int z = z0; z < z1; ++z) {
         const int buf = z & 1;
@@ -673,8 +676,8 @@ residual3d_kernel(const InT *__restrict__ u, const InT *__restrict__ b, OutT *__
         const InT *P = su[buf];
         const InT sa = radd(radd(radd(P[ia - 1], bc), radd(P[ia - kQW], P[ia + kQW])), radd(ap, an));
         const InT sb = radd(radd(radd(ac, P[ia + 2]), radd(P[ia + 1 - kQW], P[ia + 1 + kQW])), radd(bp, bn));
-        const InT ra = radd(rfma(InT(-6), ac, fa), sa);
-        const InT rb = radd(rfma(InT(-6), bc, fb), sb);
+        const InT ra = radd(rfma(m6, ac, fa), sa);
+        const InT rb = radd(rfma(m6, bc, fb), sb);
         if (owna) {
             sq_add(acc, ra);
             if (rh_out)
