@@ -336,10 +336,11 @@ ROWS = ["2d64", "2d8192-mixed", "2d8192-mixed2", "3d512-fp64", "3d512-mixed", "3
         "adjoint128", "2d8192-m5", "2d8192-jacobi", "3d512-jacobi", "3d512-m27", "3d512-m27-v22"]
 
 
-def time_workload(name, torch, warmup=2, steps=3, keep=None):
-    """Best of `steps` timed runs after `warmup`; for solver workloads also the
-    final relative residual (FP64, from the library) and, when `keep` is a
-    dict, the last solution under keep[name] (compared after timing)."""
+def time_workload(name, torch, warmup=2, steps=5, keep=None):
+    """Median of `steps` timed runs (CUDA events) after `warmup` (the best run
+    as ms_min); for solver workloads also the final relative residual (FP64,
+    from the library) and, when `keep` is a dict, the last solution under
+    keep[name] (compared after timing)."""
     step, unknowns, desc, close = make_workload(name, torch)
     for _ in range(warmup):
         step()
@@ -352,8 +353,9 @@ def time_workload(name, torch, warmup=2, steps=3, keep=None):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    ms = min(times)
-    r = {"workload": desc, "ms": ms, "cycles": cycles, "dof_per_s": unknowns * cycles / (ms * 1e-3)}
+    ms = statistics.median(times)
+    r = {"workload": desc, "ms": ms, "ms_min": min(times), "cycles": cycles,
+         "dof_per_s": unknowns * cycles / (ms * 1e-3)}
     last = getattr(step, "last", None)
     if last:
         r["final_relres"] = last["relres"]
@@ -563,6 +565,7 @@ def run_ours(args):
                          "fp64_rates_ops_per_sm_clk": {k: round(v[0], 4) for k, v in rates.items()},
                          "fp64_rates_sm_mhz": {k: round(v[1], 1) for k, v in rates.items()},
                          "hbm_gbs": sweep_gbs, "hbm_frac": sweep_gbs / peaks["hbm_gbs"],
+                         "hbm_frac_nominal_7900": sweep_gbs / 7900.0,
                          "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
                          "ms_per_launch": sweep_s * 1e3},
             # the whole solve against the algorithmic bytes of its cycles
