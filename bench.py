@@ -242,8 +242,7 @@ def make_workload(name, torch):
         last = {}
 
         def step():  # V-cycles run
-            u.zero_()
-            info = s.solve(b, u, tol=TOL, max_cycles=100)
+            info = s.solve(b, u, tol=TOL, max_cycles=100, zero_start=True)
             last.update(u=u, relres=info.relres)
             return info.cycles * inner
         step.last = last
@@ -261,8 +260,7 @@ def make_workload(name, torch):
         last = {}
 
         def step():  # V-cycles run
-            u.zero_()
-            info = s.solve(b, u, tol=TOL, max_cycles=100)
+            info = s.solve(b, u, tol=TOL, max_cycles=100, zero_start=True)
             last.update(u=u, relres=info.relres)
             return info.cycles * inner
         step.last = last
@@ -302,8 +300,7 @@ def make_workload(name, torch):
         s = Solver(d_, n_, w, nu1=nu, nu2=nu, precision="fp64")
 
         def step():
-            u.zero_()
-            info = s.solve(b, u, tol=TOL, max_cycles=200)
+            info = s.solve(b, u, tol=TOL, max_cycles=200, zero_start=True)
             return info.cycles
         label = "M5" if name.endswith("-m5") else "weighted Jacobi"
         return step, (n_ - 1) ** d_, f"{d_}D N={n_} fp64 V({nu},{nu}) {label} to 1e-10", s.close
@@ -316,8 +313,7 @@ def make_workload(name, torch):
         s = Solver(3, 512, smoothers.M27, nu1=nu, nu2=nu, precision="fp64")
 
         def step():
-            u.zero_()
-            info = s.solve(b, u, tol=TOL, max_cycles=100)
+            info = s.solve(b, u, tol=TOL, max_cycles=100, zero_start=True)
             return info.cycles
         return step, 511 ** 3, f"3D N=512 fp64 V({nu},{nu}) 27-point LFA-optimal M to 1e-10", s.close
     if name == "adjoint128":
@@ -390,9 +386,8 @@ def run_ours(args):
     u = torch.zeros_like(b)
     solver = Solver(D, N, smoothers.M9, nu1=NU1, nu2=NU2, precision="fp64")
 
-    def one_solve():
-        u.zero_()
-        return solver.solve(b, u, tol=TOL, max_cycles=100)
+    def one_solve():  # from u = 0 (u is output only: MG_SOLVE_ZERO_START)
+        return solver.solve(b, u, tol=TOL, max_cycles=100, zero_start=True)
 
     for _ in range(args.warmup):
         info = one_solve()
@@ -455,8 +450,7 @@ def run_ours(args):
                 cs.wait_event(in_free)
                 b_stage.copy_(b_host, non_blocking=True)
                 in_ready.record(cs)
-        u.zero_()
-        info = solver.solve(b_dev, u, tol=TOL, max_cycles=100)
+        info = solver.solve(b_dev, u, tol=TOL, max_cycles=100, zero_start=True)
         e2e_cycles += info.cycles
         if k > 0:
             stream.wait_event(out_free)  # the previous result has left u_stage

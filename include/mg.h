@@ -100,6 +100,17 @@ mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b);
 mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
                    double *relres_out, double *hist_out);
 
+/* mg_solve with options. flags: 0 or MG_SOLVE_ZERO_START: the initial guess
+ * is zero and u is output only (its prior contents are never read). The
+ * first cycle then starts with the from-zero form of its first operation (a
+ * sweep of u = 0, or for MG_FP32_IR the residual h^2 b rounded to FP32 once),
+ * which gives the same iterates as a solve from an explicitly zeroed u (up to
+ * the sign of exact zeros) without the FP64 work of A u_0. Other bits:
+ * MG_EINVAL. */
+#define MG_SOLVE_ZERO_START 1u
+mg_status mg_solve_ex(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
+                      int *cycles_out, double *relres_out, double *hist_out);
+
 /* ||b - A_h u||_2 of device arrays u, b (context's type, norm accumulated in
  * FP64); result in *norm_out (HOST). */
 mg_status mg_residual_norm(mg_ctx *ctx, const void *u, const void *b, double *norm_out);

@@ -18,6 +18,7 @@ from . import smoothers
 
 MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOCONV, MG_ENAN, MG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 MG_FP64, MG_FP32_IR, MG_FP32 = 0, 1, 2
+MG_SOLVE_ZERO_START = 1
 PRECISIONS = {"fp64": MG_FP64, "fp32_ir": MG_FP32_IR, "mixed": MG_FP32_IR, "fp32": MG_FP32}
 
 _lock = threading.Lock()
@@ -32,6 +33,7 @@ SIGNATURES = {
     "mg_setup_ex": (_I, [_I, _I, _DP, _I, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
     "mg_vcycle": (_I, [_P, _P, _P]),
     "mg_solve": (_I, [_P, _P, _P, _D, _I, _IP, _DP, _DP]),
+    "mg_solve_ex": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, _IP, _DP, _DP]),
     "mg_residual_norm": (_I, [_P, _P, _P, _DP]),
     "mg_destroy": (None, [_P]),
     "mg_op_sweep": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _DP, _P]),
@@ -250,16 +252,21 @@ class Solver:
         _check(lib().mg_vcycle(self._ctx, pu, pb), "mg_vcycle")
         return u
 
-    def solve(self, b, u=None, tol: float = 1e-10, max_cycles: int = 100) -> SolveInfo:
+    def solve(self, b, u=None, tol: float = 1e-10, max_cycles: int = 100, zero_start=None) -> SolveInfo:
+        """Solve from the initial guess in u; u None: from zero into a new
+        array. zero_start (default: u is None): the initial guess is zero and
+        u is output only (MG_SOLVE_ZERO_START)."""
         torch = _torch()
+        if zero_start is None:
+            zero_start = u is None
         if u is None:
-            u = torch.zeros(self.shape, dtype=self.dtype, device=b.device)
+            u = torch.empty(self.shape, dtype=self.dtype, device=b.device)
         pu, pb = self._args(u, b)
         hist = np.zeros(max_cycles + 1)
         cyc = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
-        st = lib().mg_solve(self._ctx, pb, pu, float(tol), int(max_cycles), ctypes.byref(cyc), ctypes.byref(rel),
-                            hist.ctypes.data_as(_DP))
+        st = lib().mg_solve_ex(self._ctx, pb, pu, float(tol), int(max_cycles), MG_SOLVE_ZERO_START if zero_start else 0,
+                               ctypes.byref(cyc), ctypes.byref(rel), hist.ctypes.data_as(_DP))
         _check(st, "mg_solve", ok=(MG_OK, MG_ENOCONV, MG_ENAN))
         return SolveInfo(u, st, cyc.value, rel.value, hist[: cyc.value + 1].copy())
 

@@ -35,7 +35,8 @@ struct BatchWork;  // mg_batched.cu
 struct GraphPair {
     cudaGraphExec_t pre = nullptr, rest = nullptr;
     cudaGraphExec_t meas = nullptr;  // residual norm only (plain cycles with a fused pre graph)
-    unsigned long long pre_nodes = 0, rest_nodes = 0, meas_nodes = 0;
+    cudaGraphExec_t pre0 = nullptr;  // the first pre graph of a solve from u = 0 (u not read)
+    unsigned long long pre_nodes = 0, rest_nodes = 0, meas_nodes = 0, pre0_nodes = 0;
 };
 
 struct mg_ctx {

@@ -104,10 +104,55 @@ __global__ void sum_partials_host_kernel(const double *__restrict__ p, int np, d
     }
 }
 
+// The first refinement residual of a solve from u = 0: rh = h^2 b rounded to
+// FP32 once, the value the FP64 residual kernel forms there (fma(-2d, 0, h^2 b)
+// plus a zero neighbour sum, which turns -0 into +0), written to the padded
+// level-0 layout, with the squared norm of h^2 b: one partial per block.
+template <int D>
+__global__ void __launch_bounds__(256) refine_rhs_zero_kernel(const double *__restrict__ b, float *__restrict__ rh,
+                                                               int n, int hk, long pitch, long plane, long off,
+                                                               double *__restrict__ partials)
+{
+    SqSum acc;
+    const long np = D == 2 ? (long)n * n : (long)n * n * n;
+    int cnt = 0;
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < np; i += (long)gridDim.x * 256L) {
+        double r = scale2(b[i], hk);
+        if ((__double_as_longlong(r) << 1) == 0) r = 0.0;  // -0 -> +0
+        sq_add(acc, r);
+        if (++cnt == 32) {
+            sq_flush(acc);
+            cnt = 0;
+        }
+        const long x = i % n, yz = i / n;
+        rh[D == 2 ? off + yz * pitch + x : off + (yz / n) * plane + (yz % n) * pitch + x] = narrow_rn(r);
+    }
+    block_sum_store<256>(sq_value(acc), &partials[blockIdx.x]);
+}
+
 static cudaError_t launch_sum_partials_host(const mg_ctx *c, int np, cudaStream_t s)
 {
     static_assert(kNormBytes == 2 * sizeof(unsigned long long), "sum and error word");
     sum_partials_host_kernel<<<1, 256, 0, s>>>(c->partials, np, c->d_norm2, c->h_norm2_dev);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// refine_rhs_zero_kernel over the context's level 0 (padded FP32 rhs BH[0]);
+// nb: the blocks launched (partials to sum), at most the context's partials
+static cudaError_t launch_refine_rhs_zero(const mg_ctx *c, const double *b, int &nb)
+{
+    const int n = c->n[0];
+    nb = std::max(1, std::min(c->npartials, 8 * num_sms()));
+    const int hk = h2_exponent(n);
+    if (c->d == 2) {
+        const Pitch2 g = pitch2(n);
+        refine_rhs_zero_kernel<2><<<nb, 256, 0, c->s>>>(b, (float *)c->BH[0], n, hk, g.pitch, 0, g.off, c->partials);
+    } else {
+        const Pitch3 g = pitch3(n);
+        refine_rhs_zero_kernel<3><<<nb, 256, 0, c->s>>>(b, (float *)c->BH[0], n, hk, g.pitch, g.plane, g.off,
+                                                         c->partials);
+    }
     count_launch(1);
     return cudaGetLastError();
 }
@@ -261,6 +306,7 @@ static void free_graphs(mg_ctx *c)
     if (c->g.pre) cudaGraphExecDestroy(c->g.pre);
     if (c->g.rest) cudaGraphExecDestroy(c->g.rest);
     if (c->g.meas) cudaGraphExecDestroy(c->g.meas);
+    if (c->g.pre0) cudaGraphExecDestroy(c->g.pre0);
     c->g = GraphPair{};
     c->cap_u = c->cap_b = nullptr;
     if (c->adj && c->adj->graph) {  // the adjoint's graph holds the weights too
@@ -512,6 +558,22 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
             return launch_sum_partials_host(c, np, c->s);
         });
         if (st != MG_OK) return st;
+        // solve from u = 0: the first pre-sweep in its from-zero form (u is
+        // not read; the rest of the cycle writes it); without a fused
+        // pre-sweep, u is zeroed and the pre graph's residual follows
+        st = capture(c, &c->g.pre0, &c->g.pre0_nodes, [&]() -> cudaError_t {
+            cudaError_t e;
+            if (fused) {
+                e = op_sweep<T>(d, (const T *)nullptr, (const T *)b, true, (T *)c->B[0], n0, c->c, c->partials, c->s);
+            } else {
+                e = cudaMemsetAsync(u, 0, npoints(d, n0) * sizeof(T), c->s);
+                if (!e) e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
+            }
+            if (e) return e;
+            const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
+            return launch_sum_partials_host(c, np, c->s);
+        });
+        if (st != MG_OK) return st;
         if (fused) {
             st = capture(c, &c->g.meas, &c->g.meas_nodes, [&]() -> cudaError_t {
                 cudaError_t e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials,
@@ -560,6 +622,16 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
             }
             if (e) return e;
             return launch_sum_partials_host(c, residual_partials(d, n0), c->s);
+        });
+        if (st != MG_OK) return st;
+        // solve from u = 0: u zeroed (the FP64 updates add into it) and the
+        // first residual is h^2 b itself, rounded to FP32, without FP64 work
+        st = capture(c, &c->g.pre0, &c->g.pre0_nodes, [&]() -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(u, 0, np0 * sizeof(double), c->s);
+            int nb = 0;
+            if (!e) e = launch_refine_rhs_zero(c, (const double *)b, nb);
+            if (e) return e;
+            return launch_sum_partials_host(c, nb, c->s);
         });
         if (st != MG_OK) return st;
         st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
@@ -858,12 +930,14 @@ static mg_status sync_ctx(mg_ctx *ctx)
 }
 
 // the cycle loop of mg_solve, between enter() and leave()
-static mg_status solve_loop(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
-                            double *relres_out, double *hist_out)
+static mg_status solve_loop(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, bool zero_start,
+                            int *cycles_out, double *relres_out, double *hist_out)
 {
     mg_status st;
     if ((st = record(ctx, u, b)) != MG_OK) return st;
-    if ((st = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return st;
+    if ((st = zero_start ? launch_graph(ctx, ctx->g.pre0, ctx->g.pre0_nodes)
+                         : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK)
+        return st;
     if ((st = sync_ctx(ctx)) != MG_OK) return st;
     const double r0 = norm_from_host(ctx);
     double rk = r0, rprev = 0.0;
@@ -901,20 +975,34 @@ static mg_status solve_loop(mg_ctx *ctx, const void *b, void *u, double tol, int
             if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
         }
     }
+    if (zero_start && k == 0) {
+        // no cycle ran (zero rhs, max_cycles = 0, a non-finite r0): u is the
+        // zero initial guess, which a zero start never wrote
+        const size_t bytes = npoints(ctx->d, ctx->n[0]) * (ctx->prec == MG_FP32 ? sizeof(float) : sizeof(double));
+        if (cudaMemsetAsync(u, 0, bytes, ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    }
     if (cycles_out) *cycles_out = k;
     if (relres_out) *relres_out = r0 > 0.0 ? rk / r0 : 0.0;
     return st;
 }
 
+mg_status mg_solve_ex(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
+                      int *cycles_out, double *relres_out, double *hist_out)
+{
+    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch || (flags & ~MG_SOLVE_ZERO_START))
+        return MG_EINVAL;
+    mg_status st = enter(ctx);
+    if (st != MG_OK) return st;
+    st = solve_loop(ctx, b, u, tol, max_cycles, (flags & MG_SOLVE_ZERO_START) != 0, cycles_out, relres_out,
+                    hist_out);
+    const mg_status st2 = leave(ctx);
+    return st != MG_OK ? st : st2;
+}
+
 mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
                    double *relres_out, double *hist_out)
 {
-    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch) return MG_EINVAL;
-    mg_status st = enter(ctx);
-    if (st != MG_OK) return st;
-    st = solve_loop(ctx, b, u, tol, max_cycles, cycles_out, relres_out, hist_out);
-    const mg_status st2 = leave(ctx);
-    return st != MG_OK ? st : st2;
+    return mg_solve_ex(ctx, b, u, tol, max_cycles, 0u, cycles_out, relres_out, hist_out);
 }
 
 mg_status mg_set_coeffs(mg_ctx *ctx, const double *spai_coeffs, int ncoeffs)

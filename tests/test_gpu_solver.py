@@ -9,6 +9,8 @@ of the result, recomputed by the oracle, must be <= tol * ||b||, and the
 solution must match the oracle's FP64 solution to the accuracy the common
 stopping rule allows (bound stated in each test).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -318,3 +320,38 @@ def _fma(a, b, c):
     """a * b + c rounded once (exact rational arithmetic, then the nearest double)."""
     from fractions import Fraction
     return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+@pytest.mark.parametrize("d,N,prec,nu", [(2, 128, "fp64", 1), (2, 1024, "fp64", 1), (3, 32, "fp64", 2),
+                                         (3, 64, "fp64", 2), (2, 256, "fp32", 1), (3, 32, "fp32", 2),
+                                         (2, 256, "fp32_ir", 1), (2, 8, "fp32_ir", 1), (3, 64, "fp32_ir", 2),
+                                         (3, 64, "fp32_ir", 1), (2, 4, "fp64", 1)])
+def test_zero_start_equals_an_explicit_zero_initial_guess(d, N, prec, nu):
+    """MG_SOLVE_ZERO_START: u is output only (here filled with NaN before the
+    call) and the solve runs the from-zero form of its first operation; the
+    iterates, cycle count and history equal those of a solve from an
+    explicitly zeroed u bit for bit (FP64: also the oracle's)."""
+    b = inputs.uniform(d, N, 21)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    bt = torch.from_numpy(b).to("cuda", dt)
+    with Solver(d, N, nu1=nu, nu2=nu, precision=prec) as s:
+        ref = s.solve(bt, torch.zeros_like(bt), tol=1e-10 if prec != "fp32" else 1e-5, max_cycles=60)
+        garbage = torch.full_like(bt, float("nan"))
+        got = s.solve(bt, garbage, tol=1e-10 if prec != "fp32" else 1e-5, max_cycles=60, zero_start=True)
+        new = s.solve(bt, tol=1e-10 if prec != "fp32" else 1e-5, max_cycles=60)  # u None: zero start
+    assert got.status == ref.status and got.cycles == ref.cycles
+    assert torch.equal(got.u, ref.u) and torch.equal(new.u, ref.u)
+    np.testing.assert_allclose(got.hist, ref.hist, rtol=1e-12, atol=0)
+    if prec == "fp64":
+        w = coeffs.default(d)
+        o = oracle.solve(b, w, tol=1e-10, max_cycles=60, nu1=nu, nu2=nu)
+        assert got.cycles == o.cycles and np.array_equal(host(got.u), o.u)
+        np.testing.assert_allclose(got.hist, o.hist, rtol=1e-12, atol=0)
+
+
+def test_solve_ex_rejects_unknown_flags():
+    b = torch.zeros((31, 31), dtype=torch.float64, device="cuda")
+    with Solver(2, 32) as s:
+        st = binding.lib().mg_solve_ex(s._ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(b.data_ptr()), 1e-10,
+                                       10, 2, None, None, None)
+    assert st == binding.MG_EINVAL
