@@ -159,6 +159,13 @@ mg_status mg_setup_batched(int d, int count, const int *Ns, const double *spai_c
 mg_status mg_solve_batched(mg_ctx *ctx, const void *const *b, void *const *u, double tol, int max_cycles,
                            int *cycles_out, double *relres_out);
 
+/* mg_solve_batched with options (see mg_solve_ex): MG_SOLVE_ZERO_START: every
+ * initial guess is zero and the u[i] are output only; the first residuals
+ * are h^2 b_i rounded to FP32 without FP64 work. Same iterates as from
+ * explicitly zeroed u[i] (up to the sign of exact zeros). */
+mg_status mg_solve_batched_ex(mg_ctx *ctx, const void *const *b, void *const *u, double tol, int max_cycles,
+                              unsigned flags, int *cycles_out, double *relres_out);
+
 /* ---------------------------------------------------------------------- */
 /* adjoint of K cycles                                                    */
 /* ---------------------------------------------------------------------- */

@@ -47,6 +47,7 @@ SIGNATURES = {
     "mg_set_refinement_cycles": (_I, [_P, _I]),
     "mg_setup_batched": (_I, [_I, _I, _IP, _DP, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
     "mg_solve_batched": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _IP, _DP]),
+    "mg_solve_batched_ex": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.c_uint, _IP, _DP]),
     "mg_vcycles_adjoint": (_I, [_P, _I, _P, _P, _P, _DP]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_cuda_error": (ctypes.c_char_p, []),
@@ -319,13 +320,17 @@ class BatchedSolver:
         _check(lib().mg_set_refinement_cycles(self._ctx, int(cycles)), "mg_set_refinement_cycles")
         self.refinement_cycles = int(cycles)
 
-    def solve(self, bs, us=None, tol: float = 1e-10, max_cycles: int = 100):
-        """Returns (us, status, cycles per problem, relres per problem)."""
+    def solve(self, bs, us=None, tol: float = 1e-10, max_cycles: int = 100, zero_start=None):
+        """Returns (us, status, cycles per problem, relres per problem). us
+        None: from zero into new arrays. zero_start (default: us is None):
+        every initial guess is zero and the us are output only."""
         torch = _torch()
         if len(bs) != self.count:
             raise ValueError(f"expected {self.count} right-hand sides")
+        if zero_start is None:
+            zero_start = us is None
         if us is None:
-            us = [torch.zeros_like(b) for b in bs]
+            us = [torch.empty_like(b) for b in bs]
         pb = (ctypes.c_void_p * self.count)()
         pu = (ctypes.c_void_p * self.count)()
         for i, (b, u, N) in enumerate(zip(bs, us, self.Ns)):
@@ -333,7 +338,8 @@ class BatchedSolver:
             pu[i] = _dev_ptr(u, torch.float64, (N - 1, N - 1), f"u[{i}]").value
         cyc = (ctypes.c_int * self.count)()
         rel = (ctypes.c_double * self.count)()
-        st = lib().mg_solve_batched(self._ctx, pb, pu, float(tol), int(max_cycles), cyc, rel)
+        st = lib().mg_solve_batched_ex(self._ctx, pb, pu, float(tol), int(max_cycles),
+                                       MG_SOLVE_ZERO_START if zero_start else 0, cyc, rel)
         _check(st, "mg_solve_batched", ok=(MG_OK, MG_ENOCONV, MG_ENAN))
         return us, st, list(cyc), list(rel)
 

@@ -103,6 +103,17 @@ __global__ void batched_update(const UpdItem *__restrict__ tab, const int *__res
     }
 }
 
+// u_i = 0 for problem blockIdx.y, chunk blockIdx.x (a solve from zero)
+__global__ void batched_zero(const UpdItem *__restrict__ tab)
+{
+    const UpdItem it = tab[blockIdx.y];
+    const int rows = max(1, kUpdChunk / it.n);
+    const int y0 = blockIdx.x * rows;
+    if (y0 >= it.n) return;
+    const long i1 = (long)min(y0 + rows, it.n) * it.n;
+    for (long i = (long)y0 * it.n + threadIdx.x; i < i1; i += blockDim.x) it.u[i] = 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // autotune cache
 // ---------------------------------------------------------------------------
@@ -193,8 +204,8 @@ struct BatchWork {
     std::vector<UpdItem> upd_host;
     int upd_chunks = 1;
     char *arena = nullptr;
-    cudaGraphExec_t pre = nullptr, rest = nullptr;
-    unsigned long long pre_nodes = 0, rest_nodes = 0;
+    cudaGraphExec_t pre = nullptr, rest = nullptr, pre0 = nullptr;  // pre0: the first pre of a zero start
+    unsigned long long pre_nodes = 0, rest_nodes = 0, pre0_nodes = 0;
     std::vector<const void *> cap_u, cap_b;
 };
 
@@ -376,6 +387,21 @@ cudaError_t record_rest(mg_ctx *c, BatchWork *w)
     return cudaGetLastError();
 }
 
+// a solve from u = 0: every u_i zeroed (the FP64 updates add into it), the
+// first residual h^2 b_i rounded to FP32 without FP64 work
+cudaError_t record_pre0(mg_ctx *c, BatchWork *w)
+{
+    cudaError_t e;
+    batched_zero<<<dim3(w->upd_chunks, w->count), 256, 0, c->s>>>(w->upd);
+    count_launch(1);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_residual2d_batched_zero(w->rgroups, (int)w->groups.size(), w->res_items, c->s))) return e;
+    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2,
+                                             w->h_norm2_dev);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t record_pre(mg_ctx *c, BatchWork *w)
 {
     cudaError_t e;
@@ -414,6 +440,7 @@ void free_batch(mg_ctx *c)
     BatchWork *w = c->batch;
     if (!w) return;
     if (w->pre) cudaGraphExecDestroy(w->pre);
+    if (w->pre0) cudaGraphExecDestroy(w->pre0);
     if (w->rest) cudaGraphExecDestroy(w->rest);
     if (w->arena) cudaFree(w->arena);
     if (w->h_norm2) cudaFreeHost(w->h_norm2);
@@ -715,6 +742,7 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
     st = autotune(c, w);
     if (st == MG_OK) st = capture_graph(c, &w->rest, &w->rest_nodes, [&]() { return record_rest(c, w); });
     if (st == MG_OK) st = capture_graph(c, &w->pre, &w->pre_nodes, [&]() { return record_pre(c, w); });
+    if (st == MG_OK) st = capture_graph(c, &w->pre0, &w->pre0_nodes, [&]() { return record_pre0(c, w); });
     if (st != MG_OK) {
         mg_destroy(c);
         return st;
@@ -726,7 +754,15 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
 extern "C" mg_status mg_solve_batched(mg_ctx *ctx, const void *const *b, void *const *u, double tol, int max_cycles,
                                       int *cycles_out, double *relres_out)
 {
-    if (!ctx || !ctx->batch || !b || !u || max_cycles < 0 || !(tol >= 0.0)) return MG_EINVAL;
+    return mg_solve_batched_ex(ctx, b, u, tol, max_cycles, 0u, cycles_out, relres_out);
+}
+
+extern "C" mg_status mg_solve_batched_ex(mg_ctx *ctx, const void *const *b, void *const *u, double tol,
+                                         int max_cycles, unsigned flags, int *cycles_out, double *relres_out)
+{
+    if (!ctx || !ctx->batch || !b || !u || max_cycles < 0 || !(tol >= 0.0) || (flags & ~MG_SOLVE_ZERO_START))
+        return MG_EINVAL;
+    const bool zero_start = (flags & MG_SOLVE_ZERO_START) != 0;
     BatchWork *w = ctx->batch;
     const int count = w->count;
     for (int p = 0; p < count; ++p)
@@ -761,10 +797,10 @@ extern "C" mg_status mg_solve_batched(mg_ctx *ctx, const void *const *b, void *c
     auto upload_flags = [&]() {
         return cudaMemcpyAsync(w->active, w->h_active, count * sizeof(int), cudaMemcpyHostToDevice, ctx->s);
     };
-    if (upload_flags() != cudaSuccess || cudaGraphLaunch(w->pre, ctx->s) != cudaSuccess ||
+    if (upload_flags() != cudaSuccess || cudaGraphLaunch(zero_start ? w->pre0 : w->pre, ctx->s) != cudaSuccess ||
         cudaStreamSynchronize(ctx->s) != cudaSuccess)
         return cuda_fail(cudaGetLastError());
-    count_launch(w->pre_nodes);
+    count_launch(zero_start ? w->pre0_nodes : w->pre_nodes);
     for (int k = 0;; ++k) {
         int nactive = 0;
         for (int p = 0; p < count; ++p) {

@@ -106,6 +106,8 @@ struct BResGroup {
 int residual2d_batched_group(BResGroup &g, int nprob);
 cudaError_t launch_residual2d_batched_all(const BResGroup *groups, int ngroups, int items, const int *active,
                                           cudaStream_t s);
+// the same items for u = 0 (rh = h^2 b rounded to FP32, norm partials), every problem
+cudaError_t launch_residual2d_batched_zero(const BResGroup *groups, int ngroups, int items, cudaStream_t s);
 int residual2d_batched_tiles(int n);
 // mode 0: every item from its u; 1: from zero; 2: per item (u == nullptr: from zero)
 cudaError_t launch_sweep2d_pl_batched(const BItem<float> *tab, int nprob, const int *active, int n, int H, int mode,

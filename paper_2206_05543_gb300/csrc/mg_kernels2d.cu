@@ -487,6 +487,42 @@ residual2d_batched_all(const BResGroup *__restrict__ groups, int ngroups, int to
     }
 }
 
+// The same items for a solve from u = 0: the residual of every tile is h^2 b
+// itself (the residual kernel's value for u = 0: fma(-4, 0, h^2 b) plus a
+// zero neighbour sum, which turns -0 into +0), rounded to FP32 once, with
+// the tile's squared-norm partial; no FP64 arithmetic per point.
+__global__ void __launch_bounds__(kSweepThreads / 2)
+residual2d_batched_zero(const BResGroup *__restrict__ groups, int ngroups, int total)
+{
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        int gi = 0;
+        while (gi + 1 < ngroups && it >= groups[gi + 1].item0) ++gi;
+        const BResGroup G = groups[gi];
+        const int local = it - G.item0, per = G.bx * G.by;
+        const int j = local / per, r = local - j * per;
+        const BRes<float> e = G.tab[j];
+        const int tbx = r % G.bx, tby = r / G.bx, n = G.n;
+        const int x0 = tbx * kSweepCols, x1 = min(x0 + kSweepCols, n);
+        const int y0 = tby * G.H, y1 = min(y0 + G.H, n);
+        SqSum acc;
+        int cnt = 0;
+        for (int y = y0; y < y1; ++y) {
+            for (int x = x0 + (int)threadIdx.x; x < x1; x += blockDim.x) {
+                double v = scale2(e.b[(long)y * n + x], G.hk);
+                if ((__double_as_longlong(v) << 1) == 0) v = 0.0;  // -0 -> +0
+                sq_add(acc, v);
+                e.out[G.off + (long)y * G.pitch + x] = narrow_rn(v);
+            }
+            if (++cnt == 16) {  // at most 32 terms pending
+                sq_flush(acc);
+                cnt = 0;
+            }
+        }
+        block_sum_store<kSweepThreads / 2>(sq_value(acc), e.partials + r);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -626,6 +662,14 @@ int residual2d_batched_group(BResGroup &g, int nprob)
     g.by = q.by;
     g.hk = h2_exponent(g.n);
     return nprob * q.bx * q.by;
+}
+
+cudaError_t launch_residual2d_batched_zero(const BResGroup *groups, int ngroups, int items, cudaStream_t s)
+{
+    const int grid = persistent_grid((const void *)residual2d_batched_zero, kSweepThreads / 2, items);
+    residual2d_batched_zero<<<grid, kSweepThreads / 2, 0, s>>>(groups, ngroups, items);
+    count_launch(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_residual2d_batched_all(const BResGroup *groups, int ngroups, int items, const int *active,

@@ -96,3 +96,23 @@ def test_batched_several_cycles_needs_no_tail_finest_level():
         with pytest.raises(MGError):
             bsolver.set_refinement_cycles(2)
         bsolver.set_refinement_cycles(1)
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_batched_zero_start_equals_explicit_zero_initial_guesses(inner):
+    """MG_SOLVE_ZERO_START on a batch: the us are output only (filled with NaN
+    before the call); iterates, cycle counts and relative residuals equal
+    those of the solve from explicitly zeroed us bit for bit."""
+    Ns = [64, 128, 256, 64, 512, 128, 32, 32]
+    bs = [torch.from_numpy(b).cuda() for b in inputs.batch_rhs(Ns, 3)]
+    with BatchedSolver(Ns, nu1=1, nu2=1) as s:
+        if inner > 1:
+            s.set_refinement_cycles(inner)
+        ref, st_r, cyc_r, rel_r = s.solve(bs, [torch.zeros_like(b) for b in bs], tol=1e-10)
+        got, st_g, cyc_g, rel_g = s.solve(bs, [torch.full_like(b, float("nan")) for b in bs], tol=1e-10,
+                                          zero_start=True)
+        new, _, cyc_n, _ = s.solve(bs, tol=1e-10)  # us None: zero start
+    assert st_g == st_r and cyc_g == cyc_r and cyc_n == cyc_r
+    for a, r, c in zip(got, ref, new):
+        assert torch.equal(a, r) and torch.equal(c, r)
+    np.testing.assert_allclose(rel_g, rel_r, rtol=1e-12, atol=0)
