@@ -423,46 +423,59 @@ def run_ours(args):
     value = UNKNOWNS * total_cycles / (ms * 1e-3)
 
     # end to end through the public API, every step: its b from pinned host
-    # memory to the device, the solve, its u back to pinned host memory. The
-    # copies of step k+1's input and of step k-1's result run on a copy
-    # stream while step k solves (staging buffers, one device-to-device copy
-    # each way on the solve stream), as a serving loop would pipeline them.
+    # memory to the device, the solve, its u back to pinned host memory, its
+    # outcome (mg_solve_info) written by the device into pinned host memory.
+    # Two device slots of (b, u) alternate: step k+1's input is copied in and
+    # step k-1's result copied out on a copy stream while step k solves
+    # (mg_solve_async: the solve, stop test included, is queued without
+    # synchronising; the context keeps the graphs of both slots).
     u_host = torch.empty_like(b_host).pin_memory()
-    b_dev, b_stage, u_stage = torch.empty_like(b), torch.empty_like(b), torch.empty_like(b)
+    slots_b = [torch.empty_like(b) for _ in range(2)]
+    slots_u = [torch.empty_like(b) for _ in range(2)]
+    infos = [torch.zeros(24, dtype=torch.uint8, pin_memory=True) for _ in range(args.steps)]
+    for sb, su in zip(slots_b, slots_u):  # record both slots' graphs before timing
+        sb.copy_(b)
+        solver.solve_async(sb, su, tol=TOL, max_cycles=100, zero_start=True, info_buf=infos[0]).result()
     cs = torch.cuda.Stream()
-    in_ready, in_free, out_ready, out_free = (torch.cuda.Event() for _ in range(4))
+    in_ready = [torch.cuda.Event() for _ in range(2)]
+    solved = [torch.cuda.Event() for _ in range(2)]
+    out_done = [torch.cuda.Event() for _ in range(2)]
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     with torch.cuda.stream(cs):  # step 0's input
         cs.wait_event(f0)
-        b_stage.copy_(b_host, non_blocking=True)
-        in_ready.record(cs)
-    e2e_cycles = 0
+        slots_b[0].copy_(b_host, non_blocking=True)
+        in_ready[0].record(cs)
+    pending = []
     for k in range(args.steps):
-        stream.wait_event(in_ready)
-        b_dev.copy_(b_stage, non_blocking=True)
-        in_free.record(stream)
+        sl = k % 2
         if k + 1 < args.steps:
-            with torch.cuda.stream(cs):  # the next step's input, during this solve
-                cs.wait_event(in_free)
-                b_stage.copy_(b_host, non_blocking=True)
-                in_ready.record(cs)
-        info = solver.solve(b_dev, u, tol=TOL, max_cycles=100, zero_start=True)
-        e2e_cycles += info.cycles
-        if k > 0:
-            stream.wait_event(out_free)  # the previous result has left u_stage
-        u_stage.copy_(u, non_blocking=True)
-        out_ready.record(stream)
+            with torch.cuda.stream(cs):  # the next step's input, once step k-1 stopped reading its slot
+                if k >= 1:
+                    cs.wait_event(solved[1 - sl])
+                slots_b[1 - sl].copy_(b_host, non_blocking=True)
+                in_ready[1 - sl].record(cs)
+        stream.wait_event(in_ready[sl])
+        if k >= 2:
+            stream.wait_event(out_done[sl])  # step k-2's result has left this slot
+        pending.append(solver.solve_async(slots_b[sl], slots_u[sl], tol=TOL, max_cycles=100, zero_start=True,
+                                          info_buf=infos[k]))
+        solved[sl].record(stream)
         with torch.cuda.stream(cs):  # this step's result, during the next solve
-            cs.wait_event(out_ready)
-            u_host.copy_(u_stage, non_blocking=True)
-            out_free.record(cs)
+            cs.wait_event(solved[sl])
+            u_host.copy_(slots_u[sl], non_blocking=True)
+            out_done[sl].record(cs)
     stream.wait_stream(cs)
     f1.record(stream)
     barrier()
     clocks.stop()
     e2e_ms = f0.elapsed_time(f1)
+    e2e_cycles = 0
+    for p in pending:
+        r = p.result()
+        assert r.converged, r.status
+        e2e_cycles += r.cycles
     e2e_value = world * UNKNOWNS * e2e_cycles / (e2e_ms * 1e-3)
 
     # dominant kernel: the finest-level FP64 sweep, timed alone on the stream
@@ -568,7 +581,7 @@ def run_ours(args):
                 "frac_measured_hbm": eff_lo / peaks["hbm_gbs"], "frac_nominal_7900": eff_lo / NOMINAL_HBM_GBS,
                 "note": "FP64 ALU-bound: the cycle's bytes are not its limit"},
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": b.numel() * 8,
-                    "d2h_bytes_per_step": u.numel() * 8},
+                    "d2h_bytes_per_step": u.numel() * 8 + 24},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "rows": rows,

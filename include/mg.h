@@ -94,9 +94,13 @@ mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b);
  * or max_cycles cycles ran (Sec. 4). b, u: device arrays of the context's
  * type (see mg_vcycle); residual norms are accumulated in FP64. cycles_out,
  * relres_out (= ||r_k||/||r_0||): nullable HOST pointers. hist_out: nullable
- * HOST array of max_cycles + 1 doubles receiving ||r_k||_2, k = 0..cycles.
+ * HOST array of max_cycles + 1 doubles receiving ||r_k||_2, k = 0..cycles
+ * (with hist_out, max_cycles above 2^20: MG_EINVAL).
  * Returns MG_OK, MG_ENOCONV (u and outputs still written) or MG_ENAN.
- * Synchronises the stream once per cycle. */
+ * The cycles and the stop test run on the device (a CUDA graph whose
+ * conditional loop node repeats the cycle while a one-thread kernel finds the
+ * test unmet); the call synchronises with the context's stream once per
+ * solve. */
 mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
                    double *relres_out, double *hist_out);
 
@@ -110,6 +114,29 @@ mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycl
 #define MG_SOLVE_ZERO_START 1u
 mg_status mg_solve_ex(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
                       int *cycles_out, double *relres_out, double *hist_out);
+
+/* The outcome of a solve, as the device writes it. */
+typedef struct mg_solve_info {
+    double r0;   /* ||b - A u_0||_2 */
+    double rk;   /* ||b - A u_k||_2 after the last cycle (relres = rk / r0) */
+    int cycles;  /* k */
+    int status;  /* MG_OK, MG_ENOCONV, MG_ENAN or MG_ETIMEOUT */
+} mg_solve_info;
+
+/* mg_solve_ex without any synchronisation: the whole solve, its stop test
+ * included, is queued on the context's stream (after the work queued on the
+ * caller's stream so far; the caller's stream waits for it) and the call
+ * returns. info: DEVICE-ACCESSIBLE memory (device memory, or page-locked host
+ * memory on a system with unified addressing), written when the solve ends;
+ * it must stay valid until then. hist: nullable device-accessible array of
+ * max_cycles + 1 doubles (||r_k||_2, k = 0..cycles; max_cycles above 2^20
+ * with a history: MG_EINVAL). The return value reports errors found before
+ * queueing (arguments, graph recording); the solve's own status is
+ * info->status. Solves queued back to back on one context run one after the
+ * other; their arrays may differ (the graphs of the last few (u, b) pairs
+ * are kept). */
+mg_status mg_solve_async(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
+                         mg_solve_info *info, double *hist);
 
 /* ||b - A_h u||_2 of device arrays u, b (context's type, norm accumulated in
  * FP64); result in *norm_out (HOST). */
@@ -293,7 +320,9 @@ mg_status mg_op_sweep_norm_noalloc(int d, int n, mg_prec prec, const double *spa
 const char *mg_strerror(mg_status status);
 const char *mg_last_cuda_error(void);
 /* Number of kernels the library launched (directly or as graph nodes)
- * since the process started; graph replays count every node. */
+ * since the process started; graph replays count every node. The kernels of
+ * a solve's device-side cycle loop are counted by the device and appear here
+ * once they have run. */
 unsigned long long mg_kernel_launch_count(void);
 
 /* Measured issue rate of the FP64 pipe on the current device, for the

@@ -34,6 +34,7 @@ SIGNATURES = {
     "mg_vcycle": (_I, [_P, _P, _P]),
     "mg_solve": (_I, [_P, _P, _P, _D, _I, _IP, _DP, _DP]),
     "mg_solve_ex": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, _IP, _DP, _DP]),
+    "mg_solve_async": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, _P, _P]),
     "mg_residual_norm": (_I, [_P, _P, _P, _DP]),
     "mg_destroy": (None, [_P]),
     "mg_op_sweep": (_I, [_I, _I, _I, _DP, _I, _P, _P, _I, _P, _DP, _P]),
@@ -163,6 +164,30 @@ class SolveInfo:
         return float((self.hist[k] / self.hist[0]) ** (1.0 / k)) if k > 0 else 0.0
 
 
+class MGSolveInfo(ctypes.Structure):
+    """mg_solve_info of include/mg.h."""
+    _fields_ = [("r0", ctypes.c_double), ("rk", ctypes.c_double), ("cycles", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class PendingSolve:
+    """A solve queued by Solver.solve_async. The solver's stream (and so the
+    torch stream it was created on) is ordered after the solve; result()
+    waits for that stream and returns the SolveInfo."""
+
+    def __init__(self, u, info_buf, hist, stream):
+        self.u, self._buf, self._hist, self._stream = u, info_buf, hist, stream
+
+    def _info(self) -> MGSolveInfo:
+        return MGSolveInfo.from_address(self._buf.data_ptr())
+
+    def result(self) -> SolveInfo:
+        self._stream.synchronize()
+        r = self._info()
+        _check(r.status, "mg_solve_async", ok=(MG_OK, MG_ENOCONV, MG_ENAN))
+        hist = None if self._hist is None else self._hist[: r.cycles + 1].cpu().numpy().copy()
+        return SolveInfo(self.u, r.status, r.cycles, r.rk / r.r0 if r.r0 > 0 else 0.0, hist)
+
+
 class Solver:
     """Multigrid solver for A_h u = b on (0,1)^d, h = 1/N (one CUDA context object).
 
@@ -270,6 +295,28 @@ class Solver:
                                ctypes.byref(cyc), ctypes.byref(rel), hist.ctypes.data_as(_DP))
         _check(st, "mg_solve", ok=(MG_OK, MG_ENOCONV, MG_ENAN))
         return SolveInfo(u, st, cyc.value, rel.value, hist[: cyc.value + 1].copy())
+
+    def solve_async(self, b, u=None, tol: float = 1e-10, max_cycles: int = 100, zero_start=None,
+                    info_buf=None, history: bool = False) -> PendingSolve:
+        """Queue a solve (mg_solve_async) without synchronising. info_buf: a
+        page-locked host tensor of at least 24 bytes to receive the outcome
+        (allocated when None); history: also record ||r_k|| on the device."""
+        torch = _torch()
+        if zero_start is None:
+            zero_start = u is None
+        if u is None:
+            u = torch.empty(self.shape, dtype=self.dtype, device=b.device)
+        if info_buf is None:
+            info_buf = torch.zeros(ctypes.sizeof(MGSolveInfo), dtype=torch.uint8, pin_memory=True)
+        if not info_buf.is_pinned() or info_buf.numel() * info_buf.element_size() < ctypes.sizeof(MGSolveInfo):
+            raise ValueError("info_buf: a page-locked host tensor of at least 24 bytes")
+        hist = torch.zeros(max_cycles + 1, dtype=torch.float64, device=b.device) if history else None
+        pu, pb = self._args(u, b)
+        _check(lib().mg_solve_async(self._ctx, pb, pu, float(tol), int(max_cycles),
+                                    MG_SOLVE_ZERO_START if zero_start else 0, ctypes.c_void_p(info_buf.data_ptr()),
+                                    ctypes.c_void_p(hist.data_ptr()) if hist is not None else None),
+               "mg_solve_async")
+        return PendingSolve(u, info_buf, hist, self._stream)
 
     def residual_norm(self, u, b) -> float:
         pu, pb = self._args(u, b)

@@ -199,7 +199,8 @@ struct BatchWork {
     int res_items = 0;
     double *norm2 = nullptr, *h_norm2 = nullptr;  // h_norm2: mapped pinned
     double *h_norm2_dev = nullptr;                 // its device address
-    int *active = nullptr, *h_active = nullptr;
+    int *active = nullptr, *h_active = nullptr;  // h_active: mapped pinned
+    int *h_active_dev = nullptr;
     UpdItem *upd = nullptr;
     std::vector<UpdItem> upd_host;
     int upd_chunks = 1;
@@ -356,7 +357,7 @@ cudaError_t record_cycle(mg_ctx *c, BatchWork *w, bool first)
             for (size_t j = 0; j < S.probs.size(); ++j) {
                 const int p = S.probs[j], l = S.lev[j];
                 const size_t bytes = pitch2_floats(S.n) * sizeof(float);
-                if ((e = cudaMemsetAsync(w->A[p][l], 0, bytes, c->s))) return e;
+                if ((e = launch_zero_words(w->A[p][l], bytes, c->s))) return e;
             }
         }
         if ((e = launch_resrestrict2d_pl_batched(S.rr, np, w->active, S.n, S.Hrr, c->s))) return e;
@@ -621,7 +622,8 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
     }
     if (cudaHostAlloc((void **)&w->h_norm2, count * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void **)&w->h_norm2_dev, w->h_norm2, 0) != cudaSuccess ||
-        cudaMallocHost((void **)&w->h_active, count * sizeof(int)) != cudaSuccess) {
+        cudaHostAlloc((void **)&w->h_active, count * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&w->h_active_dev, w->h_active, 0) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(c);
         return MG_ENOMEM;
@@ -795,7 +797,9 @@ extern "C" mg_status mg_solve_batched_ex(mg_ctx *ctx, const void *const *b, void
     std::vector<int> cyc(count, 0), state(count, 0);  // 0 active, 1 converged, 2 out of cycles, 3 NaN
     for (int p = 0; p < count; ++p) w->h_active[p] = 1;
     auto upload_flags = [&]() {
-        return cudaMemcpyAsync(w->active, w->h_active, count * sizeof(int), cudaMemcpyHostToDevice, ctx->s);
+        // a kernel reads the flags from mapped memory: a copy engine could
+        // queue this behind a caller's large transfer
+        return launch_copy_words(w->active, w->h_active_dev, count * sizeof(int), ctx->s);
     };
     if (upload_flags() != cudaSuccess || cudaGraphLaunch(zero_start ? w->pre0 : w->pre, ctx->s) != cudaSuccess ||
         cudaStreamSynchronize(ctx->s) != cudaSuccess)

@@ -36,7 +36,30 @@ struct GraphPair {
     cudaGraphExec_t pre = nullptr, rest = nullptr;
     cudaGraphExec_t meas = nullptr;  // residual norm only (plain cycles with a fused pre graph)
     cudaGraphExec_t pre0 = nullptr;  // the first pre graph of a solve from u = 0 (u not read)
+    // the cycle loop of a solve with its stop test on the device: conditional
+    // nodes around rest, the norm step and one loop kernel per cycle
+    cudaGraphExec_t loop = nullptr;
     unsigned long long pre_nodes = 0, rest_nodes = 0, meas_nodes = 0, pre0_nodes = 0;
+    const void *cap_u = nullptr, *cap_b = nullptr;  // the arrays the graphs were recorded for
+};
+
+// The arguments of one solve, stored on the device by a kernel launched
+// before the solve's graphs (stream-ordered, so solves queued back to back
+// on one context do not share them).
+struct LoopArgs {
+    double tol;
+    double *hist;          // device-accessible history, or null
+    mg_solve_info *info;   // device-accessible result
+    int max_cycles;
+    int zero_start;
+};
+
+// the device-side loop's working state (device memory, one per context)
+struct LoopState {
+    LoopArgs a;
+    double r0, rk, rprev;
+    int k, status, guessing, guess, rerun;
+    unsigned long long launched;  // kernels the loop graphs ran on this context
 };
 
 struct mg_ctx {
@@ -64,8 +87,15 @@ struct mg_ctx {
     double *h_norm2 = nullptr;  // mapped pinned
     unsigned long long *h_norm2_dev = nullptr;
     int *d_err = nullptr;
-    GraphPair g;
-    const void *cap_u = nullptr, *cap_b = nullptr;
+    LoopState *d_loop = nullptr;
+    // mapped pinned: the result of a synchronous solve, its history
+    // (hist_cap doubles), and the count of kernels the loop graphs ran
+    mg_solve_info *h_info = nullptr, *h_info_dev = nullptr;
+    double *h_hist = nullptr, *h_hist_dev = nullptr;
+    int hist_cap = 0;
+    unsigned long long *h_launched = nullptr, *h_launched_dev = nullptr;
+    GraphPair g;                  // the graphs for the arrays of the last call
+    std::vector<GraphPair> other; // graphs recorded for other arrays, oldest first
     std::vector<void *> owned;  // device allocations to free
     AdjointWork *adj = nullptr;
     BatchWork *batch = nullptr;  // set for batched contexts
@@ -83,4 +113,13 @@ mg_status batch_set_inner(mg_ctx *c, int inner);
 // *nodes receives the number of kernels it launches per replay.
 mg_status capture_graph(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nodes,
                         const std::function<cudaError_t()> &body);
+// Capture the work issued by body() on the context's stream into graph g
+// after the nodes in deps; on return deps holds the nodes the work ends with;
+// *nodes (nullable) receives the number of kernels it launches.
+cudaError_t capture_into(mg_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t> &deps,
+                         const std::function<cudaError_t()> &body, unsigned long long *nodes);
+// Add a conditional node of the given type to g after deps (then deps =
+// {node}); bodies[0 .. size-1] receive its body graphs.
+cudaError_t add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, unsigned size, cudaGraph_t *bodies);
 }  // namespace mg

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -86,6 +87,44 @@ cudaError_t launch_sum_partials(const double *partials, int np, double *out, cud
     return cudaGetLastError();
 }
 
+// dst = src (src null: dst = 0) over n 4-byte words; 16-byte vectors where
+// both pointers allow them
+__global__ void __launch_bounds__(256) words_kernel(unsigned *__restrict__ dst, const unsigned *__restrict__ src,
+                                                    size_t n, int vec)
+{
+    const size_t stride = (size_t)gridDim.x * 256;
+    size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (vec) {
+        const size_t n4 = n / 4;
+        uint4 *d4 = (uint4 *)dst;
+        const uint4 *s4 = (const uint4 *)src;
+        for (size_t j = i; j < n4; j += stride) d4[j] = src ? s4[j] : make_uint4(0, 0, 0, 0);
+        for (size_t j = n4 * 4 + i; j < n; j += stride) dst[j] = src ? src[j] : 0u;
+    } else {
+        for (size_t j = i; j < n; j += stride) dst[j] = src ? src[j] : 0u;
+    }
+}
+
+static cudaError_t launch_words(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes % 4 || ((uintptr_t)dst | (uintptr_t)src) % 4) return cudaErrorInvalidValue;
+    const size_t n = bytes / 4;
+    if (!n) return cudaSuccess;
+    const int vec = ((uintptr_t)dst | (uintptr_t)src) % 16 == 0;
+    const size_t want = (n / (vec ? 4 : 1) + 255) / 256;
+    const int blocks = (int)std::min<size_t>(std::max<size_t>(want, 1), (size_t)8 * num_sms());
+    words_kernel<<<blocks, 256, 0, s>>>((unsigned *)dst, (const unsigned *)src, n, vec);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_words(void *p, size_t bytes, cudaStream_t s) { return launch_words(p, nullptr, bytes, s); }
+
+cudaError_t launch_copy_words(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return launch_words(dst, src, bytes, s);
+}
+
 // The same sum, and the kNormBytes that start at out (the sum and the error
 // word after it) stored into mapped pinned host memory as well. The host
 // reads them after the stream synchronises. A device-to-host copy would do
@@ -136,6 +175,117 @@ static cudaError_t launch_sum_partials_host(const mg_ctx *c, int np, cudaStream_
     sum_partials_host_kernel<<<1, 256, 0, s>>>(c->partials, np, c->d_norm2, c->h_norm2_dev);
     count_launch(1);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// the cycle loop of a solve on the device: the stop test ||r_k|| <= tol ||r_0||
+// of Sec. 4 decided by one-thread kernels that set the condition values of the
+// loop graph's conditional nodes, so that a solve synchronises with the host
+// once instead of once per cycle. Every decision is the host loop's, in the
+// same IEEE double arithmetic (round to nearest, no contraction).
+// ---------------------------------------------------------------------------
+// ||r||_2 = sqrt(sum rh^2) / h^2 from the summed squares, formed as
+// sqrt(s) * N * N
+__device__ __forceinline__ double loop_norm(const double *norm2, double nd)
+{
+    return __dmul_rn(__dmul_rn(__dsqrt_rn(norm2[0]), nd), nd);
+}
+
+// whether another cycle runs; MG_ENOCONV once max_cycles cycles ran
+__device__ __forceinline__ bool loop_continue(LoopState &s)
+{
+    if (s.status != MG_OK || s.rk <= __dmul_rn(s.a.tol, s.r0)) return false;
+    if (s.k == s.a.max_cycles) {
+        s.status = MG_ENOCONV;
+        return false;
+    }
+    return true;
+}
+
+// whether the coming cycle ends with the norm-only graph: the last
+// convergence factor, carried one cycle forward, puts its residual under the
+// tolerance
+__device__ __forceinline__ bool loop_guess(const LoopState &s)
+{
+    return s.guessing && s.k >= 1 && s.rprev > 0.0 &&
+           __dmul_rn(s.rk, __ddiv_rn(s.rk, s.rprev)) <= __dmul_rn(s.a.tol, s.r0);
+}
+
+// The solve's outcome and the launch count, stored once when the loop ends:
+// while the loop runs, nothing is written to host memory (a kernel's writes
+// to host memory must land before the next kernel starts, and they can wait
+// behind a large transfer a caller runs meanwhile on the same link).
+__device__ __forceinline__ void loop_finish(const LoopState &s, unsigned long long *launched)
+{
+    mg_solve_info *info = s.a.info;
+    info->r0 = s.r0;
+    info->rk = s.rk;
+    info->cycles = s.k;
+    info->status = s.status;
+    *launched = s.launched;
+}
+
+__device__ __forceinline__ bool wait_expired(const int *err) { return *(volatile const int *)err != 0; }
+
+// a solve's arguments, by value, stored for its loop graph
+__global__ void loop_args_kernel(LoopState *st, LoopArgs a) { st->a = a; }
+
+// after the first pre graph: r_0, the history's first entry, the loop's
+// state; zero_u is set when a solve from u = 0 runs no cycle (u would stay
+// unwritten otherwise)
+__global__ void loop_init_kernel(LoopState *st, const double *norm2, const int *err, double nd, int guessing,
+                                 cudaGraphConditionalHandle loop, cudaGraphConditionalHandle zero_u,
+                                 unsigned long long *launched)
+{
+    LoopState s = *st;
+    s.r0 = s.rk = loop_norm(norm2, nd);
+    s.rprev = 0.0;
+    s.k = s.guess = s.rerun = 0;
+    s.guessing = guessing;
+    s.status = wait_expired(err) ? MG_ETIMEOUT : (isfinite(s.r0) ? MG_OK : MG_ENAN);
+    if (s.a.hist) s.a.hist[0] = s.r0;
+    const bool more = loop_continue(s);
+    const bool zero = s.a.zero_start && !more;
+    s.launched += zero ? 2 : 1;  // this kernel and the zeroing of u
+    *st = s;
+    if (!more) loop_finish(s, launched);
+    cudaGraphSetConditional(zero_u, zero ? 1u : 0u);
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
+// The end of a cycle: the count, the history, NaN, a wrong guess (the pre
+// graph runs at the start of the next cycle and guessing stops for this
+// solve), the stop test, and the choice of the next cycle's last graph.
+// n_rest, n_pre, n_meas: kernels of those graphs; has_meas: the body chooses
+// between the pre and norm-only graphs (else it always runs pre).
+__global__ void loop_after_kernel(LoopState *st, const double *norm2, const int *err, double nd, int has_meas,
+                                  unsigned n_rest, unsigned n_pre, unsigned n_meas, cudaGraphConditionalHandle loop,
+                                  cudaGraphConditionalHandle rerun_pre, cudaGraphConditionalHandle use_meas,
+                                  unsigned long long *launched)
+{
+    LoopState s = *st;
+    s.launched += 1 + n_rest + (s.rerun ? n_pre : 0) + (s.guess ? n_meas : n_pre);
+    s.rerun = 0;
+    if (wait_expired(err)) {
+        s.status = MG_ETIMEOUT;
+    } else {
+        ++s.k;
+        s.rprev = s.rk;
+        s.rk = loop_norm(norm2, nd);
+        if (s.a.hist) s.a.hist[s.k] = s.rk;
+        if (!isfinite(s.rk)) s.status = MG_ENAN;
+        s.rerun = s.status == MG_OK && s.guess && !(s.rk <= __dmul_rn(s.a.tol, s.r0)) && s.k < s.a.max_cycles;
+        if (s.rerun) s.guessing = 0;
+    }
+    const bool more = loop_continue(s);
+    s.guess = more && loop_guess(s);
+    *st = s;
+    if (!more) loop_finish(s, launched);
+    if (has_meas) {
+        cudaGraphSetConditional(rerun_pre, s.rerun ? 1u : 0u);
+        cudaGraphSetConditional(use_meas, s.guess ? 1u : 0u);
+    }
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
 }
 
 // refine_rhs_zero_kernel over the context's level 0 (padded FP32 rhs BH[0]);
@@ -297,18 +447,97 @@ mg_status capture_graph(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *nod
     return MG_OK;
 }
 
+// Capture the work issued by body() on the context's stream into graph g,
+// after the nodes in deps; on return deps holds the nodes the work ends with.
+cudaError_t capture_into(mg_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t> &deps,
+                         const std::function<cudaError_t()> &body, unsigned long long *nodes)
+{
+    cudaError_t e = cudaStreamBeginCaptureToGraph(c->s, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                                  deps.size(), cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    unsigned long long counter = 0;
+    g_capture_counter = &counter;
+    e = body();
+    g_capture_counter = nullptr;
+    if (nodes) *nodes = counter;
+    if (e == cudaSuccess) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *tail = nullptr;
+        size_t ntail = 0;
+        e = cudaStreamGetCaptureInfo(c->s, &cs, nullptr, nullptr, &tail, nullptr, &ntail);
+        if (e == cudaSuccess) deps.assign(tail, tail + ntail);
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->s, &out);
+    return e != cudaSuccess ? e : e2;
+}
+
+// Add a conditional node of the given type after deps (then deps = {node});
+// bodies[0 .. size-1] receive its body graphs.
+cudaError_t add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, unsigned size, cudaGraph_t *bodies)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    cudaGraphNode_t node = nullptr;
+    const cudaError_t e = cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
+    if (e != cudaSuccess) return e;
+    for (unsigned i = 0; i < size; ++i) bodies[i] = p.conditional.phGraph_out[i];
+    deps.assign(1, node);
+    return cudaSuccess;
+}
+
 }  // namespace mg
 
 using namespace mg;
 
+// Contexts whose device-side loops count their kernels in mapped memory;
+// mg_kernel_launch_count adds their counts, and a destroyed context's count
+// moves into g_launches.
+static std::mutex g_reg_mu;
+static std::vector<mg_ctx *> g_reg;
+
+static void register_ctx(mg_ctx *c)
+{
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    g_reg.push_back(c);
+}
+
+static void unregister_ctx(mg_ctx *c)
+{
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    for (size_t i = 0; i < g_reg.size(); ++i)
+        if (g_reg[i] == c) {
+            g_reg.erase(g_reg.begin() + (long)i);
+            if (c->h_launched) g_launches += *(volatile unsigned long long *)c->h_launched;
+            return;
+        }
+}
+
+static unsigned long long registered_launches()
+{
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    unsigned long long n = 0;
+    for (mg_ctx *c : g_reg) n += *(volatile unsigned long long *)c->h_launched;
+    return n;
+}
+
+// (an executable graph still running when destroyed is freed when it ends)
+static void destroy_set(GraphPair &g)
+{
+    for (cudaGraphExec_t x : {g.pre, g.rest, g.meas, g.pre0, g.loop})
+        if (x) cudaGraphExecDestroy(x);
+    g = GraphPair{};
+}
+
 static void free_graphs(mg_ctx *c)
 {
-    if (c->g.pre) cudaGraphExecDestroy(c->g.pre);
-    if (c->g.rest) cudaGraphExecDestroy(c->g.rest);
-    if (c->g.meas) cudaGraphExecDestroy(c->g.meas);
-    if (c->g.pre0) cudaGraphExecDestroy(c->g.pre0);
-    c->g = GraphPair{};
-    c->cap_u = c->cap_b = nullptr;
+    destroy_set(c->g);
+    for (GraphPair &g : c->other) destroy_set(g);
+    c->other.clear();
     if (c->adj && c->adj->graph) {  // the adjoint's graph holds the weights too
         cudaGraphExecDestroy(c->adj->graph);
         c->adj->graph = nullptr;
@@ -322,7 +551,11 @@ static void destroy_ctx(mg_ctx *c)
     free_adjoint(c);
     free_graphs(c);
     for (void *p : c->owned) cudaFree(p);
+    unregister_ctx(c);
     if (c->h_norm2) cudaFreeHost(c->h_norm2);
+    if (c->h_info) cudaFreeHost(c->h_info);
+    if (c->h_hist) cudaFreeHost(c->h_hist);
+    if (c->h_launched) cudaFreeHost(c->h_launched);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->s) cudaStreamDestroy(c->s);
@@ -498,7 +731,7 @@ struct Recorder {
             zero = false;
         }
         if (zero) {
-            e = cudaMemsetAsync(buf[cur], 0, bytes(l), c->s);
+            e = launch_zero_words(buf[cur], bytes(l), c->s);
             if (e) return e;
         }
         e = resrestrict(buf[cur], BH(l), unsc(l), (T *)c->BH[l + 1], n);
@@ -524,7 +757,7 @@ struct Recorder {
             cur = 1 - cur;
         }
         if (cur != 0) {
-            e = cudaMemcpyAsync(buf[0], buf[1], bytes(l), cudaMemcpyDeviceToDevice, c->s);
+            e = launch_copy_words(buf[0], buf[1], bytes(l), c->s);
             if (e) return e;
         }
         return cudaSuccess;
@@ -537,76 +770,154 @@ static mg_status capture(mg_ctx *c, cudaGraphExec_t *out, unsigned long long *no
     return mg::capture_graph(c, out, nodes, std::function<cudaError_t()>(body));
 }
 
+using CaptureFn = std::function<cudaError_t()>;
+
+// The graphs of a solve. pre: the residual norm of u (with a fused pre-sweep
+// when the cycle starts with one); pre0: the same for u = 0 without reading
+// u; meas: the norm alone (only with a fused pre-sweep); rest: the rest of the
+// cycle. loop: the cycle loop with its stop test on the device,
+//   init -> [IF zero_u: u = 0] -> WHILE loop { [IF rerun_pre: pre] -> rest ->
+//           [IF use_meas: meas ELSE pre] -> after }
+// (without meas: WHILE loop { rest -> pre -> after }), where the one-thread
+// kernels init and after set the condition values.
+static mg_status record_graphs(mg_ctx *c, void *u, const CaptureFn &pre, const CaptureFn &pre0,
+                               const CaptureFn *meas, const CaptureFn &rest)
+{
+    cudaGraph_t G = nullptr;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    if (e) return cuda_fail(e);
+    const double nd = (double)c->N;
+    const int has_meas = meas != nullptr;
+    const size_t ubytes = npoints(c->d, c->n[0]) * (c->prec == MG_FP32 ? sizeof(float) : sizeof(double));
+    auto build = [&]() -> cudaError_t {
+        // every handle belongs to the top graph and is reset at each launch
+        cudaGraphConditionalHandle loop, zero_u, rerun_pre = 0, use_meas = 0;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
+        if (!e) e = cudaGraphConditionalHandleCreate(&zero_u, G, 0, cudaGraphCondAssignDefault);
+        if (!e && has_meas) e = cudaGraphConditionalHandleCreate(&rerun_pre, G, 0, cudaGraphCondAssignDefault);
+        if (!e && has_meas) e = cudaGraphConditionalHandleCreate(&use_meas, G, 0, cudaGraphCondAssignDefault);
+        std::vector<cudaGraphNode_t> top, body, none;
+        if (!e) e = capture_into(c, G, top, [&]() {
+            loop_init_kernel<<<1, 1, 0, c->s>>>(c->d_loop, c->d_norm2, c->d_err, nd, has_meas, loop, zero_u,
+                                                c->h_launched_dev);
+            return cudaGetLastError();
+        }, nullptr);
+        cudaGraph_t Z = nullptr, B = nullptr;
+        if (!e) e = add_conditional(G, top, zero_u, cudaGraphCondTypeIf, 1, &Z);
+        if (!e) e = capture_into(c, Z, none, [&]() { return launch_zero_words(u, ubytes, c->s); }, nullptr);
+        if (!e) e = add_conditional(G, top, loop, cudaGraphCondTypeWhile, 1, &B);
+        unsigned long long n_rest = 0, n_pre = 0, n_meas = 0;
+        if (!e && has_meas) {
+            cudaGraph_t R = nullptr;  // a wrong guess: the pre graph after all
+            e = add_conditional(B, body, rerun_pre, cudaGraphCondTypeIf, 1, &R);
+            none.clear();
+            if (!e) e = capture_into(c, R, none, pre, nullptr);
+        }
+        if (!e) e = capture_into(c, B, body, rest, &n_rest);
+        if (!e && has_meas) {
+            cudaGraph_t two[2] = {nullptr, nullptr};  // [0]: condition set, [1]: else
+            e = add_conditional(B, body, use_meas, cudaGraphCondTypeIf, 2, two);
+            none.clear();
+            if (!e) e = capture_into(c, two[0], none, *meas, &n_meas);
+            none.clear();
+            if (!e) e = capture_into(c, two[1], none, pre, &n_pre);
+        } else if (!e) {
+            e = capture_into(c, B, body, pre, &n_pre);
+        }
+        if (!e) e = capture_into(c, B, body, [&]() {
+            loop_after_kernel<<<1, 1, 0, c->s>>>(c->d_loop, c->d_norm2, c->d_err, nd, has_meas, (unsigned)n_rest,
+                                                 (unsigned)n_pre, (unsigned)n_meas, loop, rerun_pre, use_meas,
+                                                 c->h_launched_dev);
+            return cudaGetLastError();
+        }, nullptr);
+        if (!e) e = cudaGraphInstantiate(&c->g.loop, G, 0);
+        return e;
+    };
+    e = build();
+    cudaGraphDestroy(G);
+    if (e) return cuda_fail(e);
+    // the same work as plain graphs (mg_vcycle, and the first pre graph of a
+    // solve), recorded after the loop's copies
+    mg_status st;
+    if ((st = capture(c, &c->g.pre, &c->g.pre_nodes, pre)) != MG_OK) return st;
+    if ((st = capture(c, &c->g.pre0, &c->g.pre0_nodes, pre0)) != MG_OK) return st;
+    if (meas && (st = capture(c, &c->g.meas, &c->g.meas_nodes, *meas)) != MG_OK) return st;
+    return capture(c, &c->g.rest, &c->g.rest_nodes, rest);
+}
+
 // Plain cycles in precision T on the caller's arrays (level 0 = caller's u, b).
 template <typename T>
 static mg_status record_plain(mg_ctx *c, void *u, const void *b)
 {
     const int d = c->d, n0 = c->n[0];
-    mg_status st;
-        Recorder<T> R{c, (const T *)b, true, (T *)u};
-        const bool fused = c->nu1 >= 1 && c->lt > 0;
-        st = capture(c, &c->g.pre, &c->g.pre_nodes, [&]() -> cudaError_t {
-            cudaError_t e;
-            if (fused)
-                e = op_sweep<T>(d, (const T *)u, (const T *)b, true, (T *)c->B[0], n0, c->c,
-                                     c->partials, c->s);
-            else
-                e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr,
-                                                n0, c->partials, c->s);
-            if (e) return e;
-            const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
-            return launch_sum_partials_host(c, np, c->s);
-        });
-        if (st != MG_OK) return st;
-        // solve from u = 0: the first pre-sweep in its from-zero form (u is
-        // not read; the rest of the cycle writes it); without a fused
-        // pre-sweep, u is zeroed and the pre graph's residual follows
-        st = capture(c, &c->g.pre0, &c->g.pre0_nodes, [&]() -> cudaError_t {
-            cudaError_t e;
-            if (fused) {
-                e = op_sweep<T>(d, (const T *)nullptr, (const T *)b, true, (T *)c->B[0], n0, c->c, c->partials, c->s);
-            } else {
-                e = cudaMemsetAsync(u, 0, npoints(d, n0) * sizeof(T), c->s);
-                if (!e) e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
-            }
-            if (e) return e;
-            const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
-            return launch_sum_partials_host(c, np, c->s);
-        });
-        if (st != MG_OK) return st;
+    Recorder<T> R{c, (const T *)b, true, (T *)u};
+    const bool fused = c->nu1 >= 1 && c->lt > 0;
+    const CaptureFn pre = [&]() -> cudaError_t {
+        cudaError_t e;
+        if (fused)
+            e = op_sweep<T>(d, (const T *)u, (const T *)b, true, (T *)c->B[0], n0, c->c, c->partials, c->s);
+        else
+            e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
+        if (e) return e;
+        const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
+        return launch_sum_partials(c->partials, np, c->d_norm2, c->s);
+    };
+    // solve from u = 0: the first pre-sweep in its from-zero form (u is not
+    // read; the rest of the cycle writes it); without a fused pre-sweep, u is
+    // zeroed and the pre graph's residual follows
+    const CaptureFn pre0 = [&]() -> cudaError_t {
+        cudaError_t e;
         if (fused) {
-            st = capture(c, &c->g.meas, &c->g.meas_nodes, [&]() -> cudaError_t {
-                cudaError_t e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials,
-                                                  c->s);
-                if (e) return e;
-                return launch_sum_partials_host(c, residual_partials(d, n0), c->s);
-            });
-            if (st != MG_OK) return st;
+            e = op_sweep<T>(d, (const T *)nullptr, (const T *)b, true, (T *)c->B[0], n0, c->c, c->partials, c->s);
+        } else {
+            e = launch_zero_words(u, npoints(d, n0) * sizeof(T), c->s);
+            if (!e) e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
         }
-        st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t { return R.visit(0, false, fused); });
-        if (st != MG_OK) return st;
-    return MG_OK;
+        if (e) return e;
+        const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
+        return launch_sum_partials(c->partials, np, c->d_norm2, c->s);
+    };
+    const CaptureFn meas = [&]() -> cudaError_t {
+        cudaError_t e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
+        if (e) return e;
+        return launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s);
+    };
+    const CaptureFn rest = [&]() -> cudaError_t { return R.visit(0, false, fused); };
+    return record_graphs(c, u, pre, pre0, fused ? &meas : nullptr, rest);
 }
 
-// Record the pre/rest graphs for the caller's arrays u and b.
+// graph sets kept per context: the current one and this many others
+constexpr size_t kOtherGraphSets = 3;
+
+// Make c->g the graphs for the caller's arrays u and b: the current set, a
+// kept one, or a new recording (the oldest kept set is dropped).
 static mg_status record(mg_ctx *c, void *u, const void *b)
 {
-    if (c->g.pre && c->cap_u == u && c->cap_b == b) return MG_OK;
-    free_graphs(c);
+    if (c->g.pre && c->g.cap_u == u && c->g.cap_b == b) return MG_OK;
+    if (c->g.pre) c->other.push_back(c->g);
+    c->g = GraphPair{};
+    for (size_t i = 0; i < c->other.size(); ++i)
+        if (c->other[i].cap_u == u && c->other[i].cap_b == b) {
+            c->g = c->other[i];
+            c->other.erase(c->other.begin() + (long)i);
+            return MG_OK;
+        }
+    while (c->other.size() > kOtherGraphSets) {
+        destroy_set(c->other.front());
+        c->other.erase(c->other.begin());
+    }
     const int d = c->d, n0 = c->n[0];
     const size_t np0 = npoints(d, n0);
     mg_status st;
     if (c->prec == MG_FP64) {
         st = record_plain<double>(c, u, b);
-        if (st != MG_OK) return st;
     } else if (c->prec == MG_FP32) {
         st = record_plain<float>(c, u, b);
-        if (st != MG_OK) return st;
     } else {
         // refinement: FP64 residual -> FP32 scaled rhs of level 0; FP32 cycle
         // from zero; u += e in FP64
         Recorder<float> R{c, (const float *)c->BH[0], false, (float *)c->A[0]};
-        st = capture(c, &c->g.pre, &c->g.pre_nodes, [&]() -> cudaError_t {
+        const CaptureFn pre = [&]() -> cudaError_t {
             cudaError_t e;
             if (c->pl && d == 2) {
                 const Pitch2 g = pitch2(n0);
@@ -621,21 +932,20 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
                                                c->partials, c->s);
             }
             if (e) return e;
-            return launch_sum_partials_host(c, residual_partials(d, n0), c->s);
-        });
-        if (st != MG_OK) return st;
+            return launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s);
+        };
         // solve from u = 0: u zeroed (the FP64 updates add into it) and the
         // first residual is h^2 b itself, rounded to FP32, without FP64 work
-        st = capture(c, &c->g.pre0, &c->g.pre0_nodes, [&]() -> cudaError_t {
-            cudaError_t e = cudaMemsetAsync(u, 0, np0 * sizeof(double), c->s);
+        const CaptureFn pre0 = [&]() -> cudaError_t {
+            cudaError_t e = launch_zero_words(u, np0 * sizeof(double), c->s);
             int nb = 0;
             if (!e) e = launch_refine_rhs_zero(c, (const double *)b, nb);
             if (e) return e;
-            return launch_sum_partials_host(c, nb, c->s);
-        });
-        if (st != MG_OK) return st;
-        st = capture(c, &c->g.rest, &c->g.rest_nodes, [&]() -> cudaError_t {
+            return launch_sum_partials(c->partials, nb, c->d_norm2, c->s);
+        };
+        const CaptureFn rest = [&]() -> cudaError_t {
             cudaError_t e = cudaSuccess;
+            R.fused_update = false;
             for (int k = 0; k < c->inner && !e; ++k) {
                 // only the last cycle of the iteration may fuse the FP64 update
                 R.acc64 = k == c->inner - 1 ? (double *)u : nullptr;
@@ -645,11 +955,15 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
             if (c->pl && d == 2) return launch_add_pl2d((double *)u, (const float *)c->A[0], n0, c->s);
             if (c->pl) return launch_add_pl3d((double *)u, (const float *)c->A[0], n0, c->s);
             return launch_add_to_f64<float>((double *)u, (const float *)c->A[0], np0, c->s);
-        });
-        if (st != MG_OK) return st;
+        };
+        st = record_graphs(c, u, pre, pre0, nullptr, rest);
     }
-    c->cap_u = u;
-    c->cap_b = b;
+    if (st != MG_OK) {
+        destroy_set(c->g);
+        return st;
+    }
+    c->g.cap_u = u;
+    c->g.cap_b = b;
     return MG_OK;
 }
 
@@ -660,7 +974,7 @@ static mg_status enter(mg_ctx *c)
     MG_CUDA(cudaSetDevice(c->dev));
     MG_CUDA(cudaEventRecord(c->ev_in, c->user));
     MG_CUDA(cudaStreamWaitEvent(c->s, c->ev_in, 0));
-    MG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
+    MG_CUDA(launch_zero_words(c->d_err, sizeof(int), c->s));
     return MG_OK;
 }
 
@@ -687,14 +1001,19 @@ static double norm_from_host(mg_ctx *c)
 // a kernel of this call gave up on a bounded wait (bit 0); bit 1: its drain
 // of the copies still in flight gave up too, so a copy may have landed after
 // the block ended and the context's buffers are no longer trustworthy
-static bool timed_out(const mg_ctx *c)
+static bool timed_out_word(int e)
 {
-    int e;
-    std::memcpy(&e, c->h_norm2 + 1, sizeof e);
     if (e & 2)
         snprintf(g_last_error, sizeof g_last_error,
                  "a bounded device wait and the drain of its copies both expired: destroy the context");
     return e != 0;
+}
+
+static bool timed_out(const mg_ctx *c)
+{
+    int e;
+    std::memcpy(&e, c->h_norm2 + 1, sizeof e);
+    return timed_out_word(e);
 }
 
 static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int nu1, int nu2, int gamma,
@@ -786,6 +1105,15 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
         MG_TRYC(cudaHostAlloc((void **)&c->h_norm2, kNormBytes, cudaHostAllocMapped));
         MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_norm2_dev, c->h_norm2, 0));
         std::memset(c->h_norm2, 0, kNormBytes);
+        MG_TRYC(cudaHostAlloc((void **)&c->h_info, sizeof(mg_solve_info), cudaHostAllocMapped));
+        MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_info_dev, c->h_info, 0));
+        std::memset(c->h_info, 0, sizeof(mg_solve_info));
+        MG_TRYC(cudaHostAlloc((void **)&c->h_launched, sizeof(unsigned long long), cudaHostAllocMapped));
+        MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_launched_dev, c->h_launched, 0));
+        *c->h_launched = 0;
+        MG_TRY(dalloc(c, (void **)&c->d_loop, sizeof(LoopState)));
+        MG_TRYC(cudaMemset(c->d_loop, 0, sizeof(LoopState)));
+        register_ctx(c);
     }
     *out = c;
     return MG_OK;
@@ -929,72 +1257,101 @@ static mg_status sync_ctx(mg_ctx *ctx)
     return timed_out(ctx) ? MG_ETIMEOUT : MG_OK;
 }
 
-// the cycle loop of mg_solve, between enter() and leave()
+// the history lives in mapped pinned memory: at most this many cycles
+constexpr int kMaxHistCycles = 1 << 20;
+
+// a mapped history of at least n doubles for the device loop
+static mg_status hist_reserve(mg_ctx *c, int n)
+{
+    if (n <= c->hist_cap) return MG_OK;
+    if (c->h_hist) cudaFreeHost(c->h_hist);
+    c->h_hist = c->h_hist_dev = nullptr;
+    c->hist_cap = 0;
+    const int cap = std::max(n, 128);
+    MG_CUDA(cudaHostAlloc((void **)&c->h_hist, (size_t)cap * sizeof(double), cudaHostAllocMapped));
+    MG_CUDA(cudaHostGetDevicePointer((void **)&c->h_hist_dev, c->h_hist, 0));
+    c->hist_cap = cap;
+    return MG_OK;
+}
+
+// Queue one solve on the context's stream, between enter() and leave(): its
+// arguments (by value, in a kernel's parameters), the first pre graph, and
+// the loop graph, which runs the cycles and the stop test on the device. The
+// pre graph smooths the next cycle's input speculatively while it measures
+// the residual, so the measurement that ends the solve would pay for a sweep
+// nobody uses: when the last convergence factor, carried one cycle forward,
+// puts the coming residual under the tolerance, the cycle ends with the
+// norm-only graph instead; if the guess was wrong, the pre graph runs after
+// it and guessing stops for this solve. Either way u, the cycle count and
+// the history are those of the speculative schedule.
+static mg_status queue_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, bool zero_start,
+                             mg_solve_info *info, double *hist)
+{
+    mg_status st;
+    if ((st = record(ctx, u, b)) != MG_OK) return st;
+    LoopArgs a;
+    a.tol = tol;
+    a.hist = hist;
+    a.info = info;
+    a.max_cycles = max_cycles;
+    a.zero_start = zero_start ? 1 : 0;
+    loop_args_kernel<<<1, 1, 0, ctx->s>>>(ctx->d_loop, a);
+    count_launch(1);
+    MG_CUDA(cudaGetLastError());
+    if ((st = zero_start ? launch_graph(ctx, ctx->g.pre0, ctx->g.pre0_nodes)
+                         : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK)
+        return st;
+    MG_CUDA(cudaGraphLaunch(ctx->g.loop, ctx->s));
+    return MG_OK;
+}
+
+// mg_solve_ex between enter() and leave(): the queued solve, one
+// synchronisation, the result from mapped memory
 static mg_status solve_loop(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, bool zero_start,
                             int *cycles_out, double *relres_out, double *hist_out)
 {
     mg_status st;
-    if ((st = record(ctx, u, b)) != MG_OK) return st;
-    if ((st = zero_start ? launch_graph(ctx, ctx->g.pre0, ctx->g.pre0_nodes)
-                         : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK)
+    if (hist_out && (st = hist_reserve(ctx, max_cycles + 1)) != MG_OK) return st;
+    if ((st = queue_solve(ctx, b, u, tol, max_cycles, zero_start, ctx->h_info_dev,
+                          hist_out ? ctx->h_hist_dev : nullptr)) != MG_OK)
         return st;
-    if ((st = sync_ctx(ctx)) != MG_OK) return st;
-    const double r0 = norm_from_host(ctx);
-    double rk = r0, rprev = 0.0;
-    int k = 0;
-    if (hist_out) hist_out[0] = r0;
-    st = std::isfinite(r0) ? MG_OK : MG_ENAN;
-    // The pre graph smooths the next cycle's input speculatively while it
-    // measures the residual, so the measurement that ends the solve would pay
-    // for a sweep nobody uses. When the last convergence factor, carried one
-    // cycle forward, puts the coming residual under the tolerance, that
-    // cycle is followed by the residual-norm-only graph instead; if the guess
-    // was wrong, the pre graph runs after it and guessing stops for this
-    // solve. Either way u, the cycle count and the history are those of the
-    // speculative schedule.
-    bool guessing = ctx->g.meas != nullptr;
-    while (st == MG_OK && !(rk <= tol * r0)) {
-        if (k == max_cycles) {
-            st = MG_ENOCONV;
-            break;
-        }
-        const bool guess = guessing && k >= 1 && rprev > 0.0 && rk * (rk / rprev) <= tol * r0;
-        mg_status ls;
-        if ((ls = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return ls;
-        ls = guess ? launch_graph(ctx, ctx->g.meas, ctx->g.meas_nodes) : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes);
-        if (ls != MG_OK) return ls;
-        if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
-        ++k;
-        rprev = rk;
-        rk = norm_from_host(ctx);
-        if (hist_out) hist_out[k] = rk;
-        if (!std::isfinite(rk)) st = MG_ENAN;
-        if (st == MG_OK && guess && !(rk <= tol * r0) && k < max_cycles) {
-            guessing = false;
-            if ((ls = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return ls;
-            if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
-        }
+    MG_CUDA(cudaStreamSynchronize(ctx->s));
+    mg_solve_info r;
+    std::memcpy(&r, ctx->h_info, sizeof r);
+    if (r.status == MG_ETIMEOUT) {
+        int e = 0;  // the expiry bits, for the message
+        if (cudaMemcpy(&e, ctx->d_err, sizeof e, cudaMemcpyDeviceToHost) == cudaSuccess) timed_out_word(e);
+        return MG_ETIMEOUT;
     }
-    if (zero_start && k == 0) {
-        // no cycle ran (zero rhs, max_cycles = 0, a non-finite r0): u is the
-        // zero initial guess, which a zero start never wrote
-        const size_t bytes = npoints(ctx->d, ctx->n[0]) * (ctx->prec == MG_FP32 ? sizeof(float) : sizeof(double));
-        if (cudaMemsetAsync(u, 0, bytes, ctx->s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-    }
-    if (cycles_out) *cycles_out = k;
-    if (relres_out) *relres_out = r0 > 0.0 ? rk / r0 : 0.0;
-    return st;
+    if (hist_out) std::memcpy(hist_out, ctx->h_hist, (size_t)(r.cycles + 1) * sizeof(double));
+    if (cycles_out) *cycles_out = r.cycles;
+    if (relres_out) *relres_out = r.r0 > 0.0 ? r.rk / r.r0 : 0.0;
+    return (mg_status)r.status;
 }
 
 mg_status mg_solve_ex(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
                       int *cycles_out, double *relres_out, double *hist_out)
 {
-    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch || (flags & ~MG_SOLVE_ZERO_START))
+    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch || (flags & ~MG_SOLVE_ZERO_START) ||
+        (hist_out && max_cycles > kMaxHistCycles))
         return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
     st = solve_loop(ctx, b, u, tol, max_cycles, (flags & MG_SOLVE_ZERO_START) != 0, cycles_out, relres_out,
                     hist_out);
+    const mg_status st2 = leave(ctx);
+    return st != MG_OK ? st : st2;
+}
+
+mg_status mg_solve_async(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
+                         mg_solve_info *info, double *hist)
+{
+    if (!ctx || !u || !b || !info || max_cycles < 0 || !(tol >= 0.0) || ctx->batch ||
+        (flags & ~MG_SOLVE_ZERO_START) || (hist && max_cycles > kMaxHistCycles))
+        return MG_EINVAL;
+    mg_status st = enter(ctx);
+    if (st != MG_OK) return st;
+    st = queue_solve(ctx, b, u, tol, max_cycles, (flags & MG_SOLVE_ZERO_START) != 0, info, hist);
     const mg_status st2 = leave(ctx);
     return st != MG_OK ? st : st2;
 }
@@ -1236,6 +1593,6 @@ const char *mg_strerror(mg_status s)
 
 const char *mg_last_cuda_error(void) { return g_last_error; }
 
-unsigned long long mg_kernel_launch_count(void) { return g_launches.load(); }
+unsigned long long mg_kernel_launch_count(void) { return g_launches.load() + registered_launches(); }
 
 }  // extern "C"

@@ -221,6 +221,12 @@ void coarse_inverse(int d, double *inv);
 
 // ---- small helpers (mg_host.cu) -------------------------------------------
 cudaError_t launch_sum_partials(const double *partials, int np, double *out, cudaStream_t s);
+// Zero / copy `bytes` (a multiple of 4; 4-byte aligned pointers) with a
+// kernel. The solve paths use these instead of cudaMemsetAsync and
+// cudaMemcpyAsync, which a copy engine may run and queue behind a caller's
+// large host transfer on the same engine.
+cudaError_t launch_zero_words(void *p, size_t bytes, cudaStream_t s);
+cudaError_t launch_copy_words(void *dst, const void *src, size_t bytes, cudaStream_t s);
 template <typename T>
 cudaError_t launch_add_to_f64(double *u, const T *e, size_t np, cudaStream_t s);
 template <typename T>

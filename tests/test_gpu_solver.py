@@ -355,3 +355,78 @@ def test_solve_ex_rejects_unknown_flags():
         st = binding.lib().mg_solve_ex(s._ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(b.data_ptr()), 1e-10,
                                        10, 2, None, None, None)
     assert st == binding.MG_EINVAL
+
+
+def test_device_loop_limits_and_optional_outputs():
+    """The cycle loop runs on the device: a solve with tol = 0 runs exactly
+    max_cycles cycles with the oracle's history; the outputs are optional;
+    a history longer than the loop can hold is refused."""
+    b = inputs.uniform(2, 64, 21)
+    w = coeffs.default(2)
+    ref = oracle.solve(b, w, tol=0.0, max_cycles=30)
+    assert ref.status == MG_ENOCONV and ref.cycles == 30
+    with Solver(2, 64) as s:
+        info = s.solve(dev(b), tol=0.0, max_cycles=30)
+        assert info.status == MG_ENOCONV and info.cycles == 30
+        np.testing.assert_allclose(info.hist, ref.hist, rtol=1e-12, atol=0)
+        assert np.array_equal(host(info.u), ref.u)
+        bt = dev(b)
+        u = torch.empty_like(bt)
+        cyc = ctypes.c_int(-1)
+        lib = binding.lib()
+        st = lib.mg_solve_ex(s._ctx, ctypes.c_void_p(bt.data_ptr()), ctypes.c_void_p(u.data_ptr()), 1e-10, 100,
+                             binding.MG_SOLVE_ZERO_START, ctypes.byref(cyc), None, None)
+        o = oracle.solve(b, w, tol=1e-10, max_cycles=100)
+        assert st == MG_OK and cyc.value == o.cycles
+        assert np.array_equal(host(u), o.u)
+        # no outputs at all; a limit far above the cycles needed
+        st = lib.mg_solve_ex(s._ctx, ctypes.c_void_p(bt.data_ptr()), ctypes.c_void_p(u.data_ptr()), 1e-10,
+                             1 << 30, binding.MG_SOLVE_ZERO_START, None, None, None)
+        assert st == MG_OK and np.array_equal(host(u), o.u)
+        hist = np.zeros(4)
+        st = lib.mg_solve_ex(s._ctx, ctypes.c_void_p(bt.data_ptr()), ctypes.c_void_p(u.data_ptr()), 1e-10,
+                             (1 << 20) + 1, 0, None, None, hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert st == binding.MG_EINVAL
+
+
+def test_async_solves_queued_back_to_back():
+    """mg_solve_async: solves queued on one context without synchronising,
+    over more (u, b) pairs than the context keeps graphs for, each equal to
+    the oracle's solve (u bit for bit, cycles, history within the norm
+    tolerance); a zero right-hand side from a zero start leaves u = 0."""
+    w = coeffs.default(2)
+    bs = [inputs.uniform(2, 64, 40 + i) for i in range(6)]
+    bs[3] = np.zeros_like(bs[3])
+    refs = [oracle.solve(b, w, tol=1e-10, max_cycles=60) for b in bs]
+    with Solver(2, 64) as s:
+        bds = [dev(b) for b in bs]
+        us = [torch.full_like(bd, 7.0) for bd in bds]  # garbage: every solve starts from zero
+        pend = [s.solve_async(bd, u, tol=1e-10, max_cycles=60, zero_start=True, history=True)
+                for bd, u in zip(bds, us)]
+        # the same pairs again: graphs kept or re-recorded, results unchanged
+        pend += [s.solve_async(bds[i], us[i], tol=1e-10, max_cycles=60, zero_start=True, history=True)
+                 for i in (0, 5, 2)]
+        for i, p in zip(list(range(6)) + [0, 5, 2], pend):
+            r = p.result()
+            ref = refs[i]
+            assert r.status == ref.status and r.cycles == ref.cycles
+            np.testing.assert_allclose(r.hist, ref.hist, rtol=1e-12, atol=0)
+            assert np.array_equal(host(p.u), ref.u)
+        assert not host(us[3]).any()
+
+
+@pytest.mark.parametrize("d,N,prec,nu", [(2, 128, "fp32_ir", 1), (3, 32, "fp32_ir", 2), (3, 32, "fp64", 2)])
+def test_async_equals_sync(d, N, prec, nu):
+    b = inputs.uniform(d, N, 50)
+    with Solver(d, N, nu1=nu, nu2=nu, precision=prec) as s:
+        bd = dev(b)
+        sync = s.solve(bd, tol=1e-10, max_cycles=60)
+        us = host(sync.u)
+        p = s.solve_async(bd, tol=1e-10, max_cycles=60, history=True)
+        r = p.result()
+        assert r.status == sync.status and r.cycles == sync.cycles and r.relres == sync.relres
+        assert np.array_equal(r.hist, sync.hist)
+        assert np.array_equal(host(p.u), us)
+        # the outcome of a limit that runs out
+        r = s.solve_async(bd, tol=0.0, max_cycles=3).result()
+        assert r.status == MG_ENOCONV and r.cycles == 3
