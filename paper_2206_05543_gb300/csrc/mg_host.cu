@@ -127,9 +127,9 @@ cudaError_t launch_copy_words(void *dst, const void *src, size_t bytes, cudaStre
 
 // The same sum, and the kNormBytes that start at out (the sum and the error
 // word after it) stored into mapped pinned host memory as well. The host
-// reads them after the stream synchronises. A device-to-host copy would do
-// the same but can queue behind a caller's large copy on a copy engine, and
-// the solve waits for this value every cycle.
+// reads them after the stream synchronises (mg_residual_norm). A
+// device-to-host copy would do the same but can queue behind a caller's
+// large copy on a copy engine.
 __global__ void sum_partials_host_kernel(const double *__restrict__ p, int np, double *__restrict__ out,
                                          unsigned long long *__restrict__ host)
 {
