@@ -426,9 +426,10 @@ def run_ours(args):
     # memory to the device, the solve, its u back to pinned host memory, its
     # outcome (mg_solve_info) written by the device into pinned host memory.
     # Two device slots of (b, u) alternate: step k+1's input is copied in and
-    # step k-1's result copied out on a copy stream while step k solves
-    # (mg_solve_async: the solve, stop test included, is queued without
-    # synchronising; the context keeps the graphs of both slots).
+    # step k-1's result copied out, each direction on its own copy stream,
+    # while step k solves (mg_solve_async: the solve, stop test included, is
+    # queued without synchronising; the context keeps the graphs of both
+    # slots).
     u_host = torch.empty_like(b_host).pin_memory()
     slots_b = [torch.empty_like(b) for _ in range(2)]
     slots_u = [torch.empty_like(b) for _ in range(2)]
@@ -436,37 +437,49 @@ def run_ours(args):
     for sb, su in zip(slots_b, slots_u):  # record both slots' graphs before timing
         sb.copy_(b)
         solver.solve_async(sb, su, tol=TOL, max_cycles=100, zero_start=True, info_buf=infos[0]).result()
-    cs = torch.cuda.Stream()
+    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def copy_gbs(dst, src, cs):  # one copy alone, for the record (host links differ between machines)
+        with torch.cuda.stream(cs):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(cs)
+            dst.copy_(src, non_blocking=True)
+            z.record(cs)
+        z.synchronize()
+        return src.numel() * src.element_size() / (a.elapsed_time(z) * 1e-3) / 1e9
+
+    h2d_gbs, d2h_gbs = copy_gbs(slots_b[0], b_host, cs_in), copy_gbs(u_host, slots_u[0], cs_out)
     in_ready = [torch.cuda.Event() for _ in range(2)]
     solved = [torch.cuda.Event() for _ in range(2)]
     out_done = [torch.cuda.Event() for _ in range(2)]
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    with torch.cuda.stream(cs):  # step 0's input
-        cs.wait_event(f0)
+    with torch.cuda.stream(cs_in):  # step 0's input
+        cs_in.wait_event(f0)
         slots_b[0].copy_(b_host, non_blocking=True)
-        in_ready[0].record(cs)
+        in_ready[0].record(cs_in)
     pending = []
     for k in range(args.steps):
         sl = k % 2
         if k + 1 < args.steps:
-            with torch.cuda.stream(cs):  # the next step's input, once step k-1 stopped reading its slot
+            with torch.cuda.stream(cs_in):  # the next step's input, once step k-1 stopped reading its slot
                 if k >= 1:
-                    cs.wait_event(solved[1 - sl])
+                    cs_in.wait_event(solved[1 - sl])
                 slots_b[1 - sl].copy_(b_host, non_blocking=True)
-                in_ready[1 - sl].record(cs)
+                in_ready[1 - sl].record(cs_in)
         stream.wait_event(in_ready[sl])
         if k >= 2:
             stream.wait_event(out_done[sl])  # step k-2's result has left this slot
         pending.append(solver.solve_async(slots_b[sl], slots_u[sl], tol=TOL, max_cycles=100, zero_start=True,
                                           info_buf=infos[k]))
         solved[sl].record(stream)
-        with torch.cuda.stream(cs):  # this step's result, during the next solve
-            cs.wait_event(solved[sl])
+        with torch.cuda.stream(cs_out):  # this step's result, during the next solve
+            cs_out.wait_event(solved[sl])
             u_host.copy_(slots_u[sl], non_blocking=True)
-            out_done[sl].record(cs)
-    stream.wait_stream(cs)
+            out_done[sl].record(cs_out)
+    stream.wait_stream(cs_in)
+    stream.wait_stream(cs_out)
     f1.record(stream)
     barrier()
     clocks.stop()
@@ -581,7 +594,7 @@ def run_ours(args):
                 "frac_measured_hbm": eff_lo / peaks["hbm_gbs"], "frac_nominal_7900": eff_lo / NOMINAL_HBM_GBS,
                 "note": "FP64 ALU-bound: the cycle's bytes are not its limit"},
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": b.numel() * 8,
-                    "d2h_bytes_per_step": u.numel() * 8 + 24},
+                    "d2h_bytes_per_step": u.numel() * 8 + 24, "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "rows": rows,
