@@ -430,3 +430,60 @@ def test_async_equals_sync(d, N, prec, nu):
         # the outcome of a limit that runs out
         r = s.solve_async(bd, tol=0.0, max_cycles=3).result()
         assert r.status == MG_ENOCONV and r.cycles == 3
+
+
+def test_kept_graphs_follow_coefficient_and_refinement_changes():
+    """The context keeps the graphs of several (u, b) pairs; a change of the
+    smoother weights (or of the FP32 cycles per refinement iteration) must
+    reach every kept pair, not only the last one."""
+    bA, bB = inputs.uniform(2, 64, 60), inputs.uniform(2, 64, 61)
+    w9, w5 = coeffs.default(2), coeffs.weights(2, "m5")
+    with Solver(2, 64) as s:
+        dA, dB = dev(bA), dev(bB)
+        uA, uB = torch.empty_like(dA), torch.empty_like(dB)
+        for d, u in ((dA, uA), (dB, uB)):
+            s.solve(d, u, tol=1e-10, max_cycles=60, zero_start=True)
+        s.set_coeffs(w5)
+        for b, d, u in ((bA, dA, uA), (bB, dB, uB)):
+            got = s.solve(d, u, tol=1e-10, max_cycles=60, zero_start=True)
+            ref = oracle.solve(b, w5, tol=1e-10, max_cycles=60)
+            assert got.cycles == ref.cycles and np.array_equal(host(u), ref.u)
+    with Solver(2, 128, precision="fp32_ir") as s:
+        bA, bB = inputs.uniform(2, 128, 62), inputs.uniform(2, 128, 63)
+        dA, dB = dev(bA), dev(bB)
+        uA, uB = torch.empty_like(dA), torch.empty_like(dB)
+        first = []
+        for d, u in ((dA, uA), (dB, uB)):
+            f = s.solve(d, u, tol=1e-10, max_cycles=60, zero_start=True)
+            first.append((f.cycles, host(u)))
+        s.set_refinement_cycles(2)
+        for b, d, u, (fc, fu) in zip((bA, bB), (dA, dB), (uA, uB), first):
+            got = s.solve(d, u, tol=1e-10, max_cycles=60, zero_start=True)
+            assert got.converged and got.cycles <= fc
+            # two FP32 cycles per iteration give other iterates than one
+            assert not np.array_equal(host(u), fu)
+            r = oracle.residual_norm(host(u), b)
+            assert r <= 1e-10 * oracle.residual_norm(np.zeros_like(b), b) * (1 + 1e-6)
+
+
+def test_solve_async_rejects_bad_arguments():
+    b = torch.zeros((63, 63), dtype=torch.float64, device="cuda")
+    info = torch.zeros(24, dtype=torch.uint8, pin_memory=True)
+    lib = binding.lib()
+    with Solver(2, 64) as s:
+        P = ctypes.c_void_p
+        assert lib.mg_solve_async(s._ctx, P(b.data_ptr()), P(b.data_ptr()), 1e-10, 10, 0, None, None) == binding.MG_EINVAL
+        assert lib.mg_solve_async(s._ctx, P(b.data_ptr()), P(b.data_ptr()), 1e-10, 10, 4, P(info.data_ptr()),
+                                  None) == binding.MG_EINVAL
+        assert lib.mg_solve_async(s._ctx, P(b.data_ptr()), P(b.data_ptr()), -1.0, 10, 0, P(info.data_ptr()),
+                                  None) == binding.MG_EINVAL
+        hist = torch.zeros(8, dtype=torch.float64, device="cuda")
+        assert lib.mg_solve_async(s._ctx, P(b.data_ptr()), P(b.data_ptr()), 1e-10, (1 << 20) + 1, 0,
+                                  P(info.data_ptr()), P(hist.data_ptr())) == binding.MG_EINVAL
+        # a zero right-hand side: no cycle, status OK, written by the device
+        p = s.solve_async(b, tol=1e-10, max_cycles=10, info_buf=info)
+        r = p.result()
+        assert r.status == MG_OK and r.cycles == 0 and not host(p.u).any()
+    with pytest.raises(ValueError):
+        with Solver(2, 64) as s:
+            s.solve_async(b, info_buf=torch.zeros(24, dtype=torch.uint8))  # not page-locked
