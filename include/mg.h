@@ -94,13 +94,10 @@ mg_status mg_vcycle(mg_ctx *ctx, void *u, const void *b);
  * or max_cycles cycles ran (Sec. 4). b, u: device arrays of the context's
  * type (see mg_vcycle); residual norms are accumulated in FP64. cycles_out,
  * relres_out (= ||r_k||/||r_0||): nullable HOST pointers. hist_out: nullable
- * HOST array of max_cycles + 1 doubles receiving ||r_k||_2, k = 0..cycles
- * (with hist_out, max_cycles above 2^20: MG_EINVAL).
+ * HOST array of max_cycles + 1 doubles receiving ||r_k||_2, k = 0..cycles.
  * Returns MG_OK, MG_ENOCONV (u and outputs still written) or MG_ENAN.
- * The cycles and the stop test run on the device (a CUDA graph whose
- * conditional loop node repeats the cycle while a one-thread kernel finds the
- * test unmet); the call synchronises with the context's stream once per
- * solve. */
+ * Synchronises the stream once per cycle: the host applies the stop test
+ * (see mg_solve_async for the same solve with the test on the device). */
 mg_status mg_solve(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, int *cycles_out,
                    double *relres_out, double *hist_out);
 
@@ -129,8 +126,11 @@ typedef struct mg_solve_info {
  * returns. info: DEVICE-ACCESSIBLE memory (device memory, or page-locked host
  * memory on a system with unified addressing), written when the solve ends;
  * it must stay valid until then. hist: nullable device-accessible array of
- * max_cycles + 1 doubles (||r_k||_2, k = 0..cycles; max_cycles above 2^20
- * with a history: MG_EINVAL). The return value reports errors found before
+ * max_cycles + 1 doubles (||r_k||_2, k = 0..cycles). The cycles and the stop
+ * test run on the device: a CUDA graph whose conditional loop node repeats
+ * the cycle while a one-thread kernel finds the test unmet; nothing is
+ * written to host memory before the solve ends. Iterates, cycle count and
+ * history equal mg_solve_ex's bit for bit. The return value reports errors found before
  * queueing (arguments, graph recording); the solve's own status is
  * info->status. Solves queued back to back on one context run one after the
  * other; their arrays may differ (the graphs of the last few (u, b) pairs

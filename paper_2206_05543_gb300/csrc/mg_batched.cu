@@ -43,97 +43,19 @@ namespace mg {
 // ---------------------------------------------------------------------------
 // small batched kernels
 // ---------------------------------------------------------------------------
-// per active problem: the sum of its partials into norm2[p]
+// per active problem: the sum of its partials into norm2[p] and into the
+// mapped pinned host array h_norm2 (read after the stream synchronises; no
+// device-to-host copy that could queue behind a caller's large copies)
 __global__ void batched_sums(const double *__restrict__ partials, const int *__restrict__ off,
-                             const int *__restrict__ cnt, const int *__restrict__ active, double *__restrict__ norm2)
+                             const int *__restrict__ cnt, const int *__restrict__ active, double *__restrict__ norm2,
+                             double *__restrict__ h_norm2)
 {
     const int p = blockIdx.x;
     if (!active[p]) return;
     double v = 0.0;
     for (int i = threadIdx.x; i < cnt[p]; i += blockDim.x) v += partials[off[p] + i];
     block_sum_store<256>(v, &norm2[p]);  // thread 0 stores it
-}
-
-// The loop of a batched solve on the device (Sec. 4's stop test per
-// problem): the arguments of the solve, the iteration count, and the kernels
-// the loop graph ran on this context.
-struct BLoopHdr {
-    double tol;
-    int max_cycles, k;
-    unsigned long long launched;
-};
-
-// a problem's outcome, stored into mapped pinned host memory when the loop ends
-struct BatchOut {
-    double r0, rk;
-    int cycles, state;  // state: 0 active, 1 converged, 2 out of cycles, 3 NaN
-};
-
-constexpr int kDecideThreads = 256;
-
-// before a solve: every problem active, the arguments stored (by value)
-__global__ void batched_begin(BLoopHdr *__restrict__ h, double tol, int max_cycles, int *__restrict__ active,
-                              int *__restrict__ state, int count)
-{
-    for (int p = threadIdx.x; p < count; p += blockDim.x) {
-        active[p] = 1;
-        state[p] = 0;
-    }
-    if (threadIdx.x == 0) {
-        h->tol = tol;
-        h->max_cycles = max_cycles;
-        h->k = 0;
-    }
-}
-
-// After iteration k's residual norms: per active problem ||r_k||_2 =
-// sqrt(sum) * N * N (the IEEE operations the host loop used), r_0 at k = 0,
-// then converged (||r_k|| <= tol ||r_0||), NaN, or out of cycles (k =
-// max_cycles) ends the problem; its flag gates every later kernel. The
-// condition value of the loop: some problem still active. At the end every
-// problem's outcome and the launch count go to mapped host memory.
-__global__ void __launch_bounds__(kDecideThreads)
-batched_decide(BLoopHdr *__restrict__ h, const double *__restrict__ norm2, const int *__restrict__ N,
-               int *__restrict__ active, double *__restrict__ r0, double *__restrict__ rk, int *__restrict__ cyc,
-               int *__restrict__ state, int count, BatchOut *__restrict__ out,
-               unsigned long long *__restrict__ launched_host, unsigned iter_nodes, cudaGraphConditionalHandle loop)
-{
-    __shared__ int s_active;
-    if (threadIdx.x == 0) s_active = 0;
-    __syncthreads();
-    const int k = h->k;
-    const double tol = h->tol;
-    const int max_cycles = h->max_cycles;
-    int mine = 0;
-    for (int p = threadIdx.x; p < count; p += blockDim.x) {
-        int st = state[p];
-        if (st) continue;
-        const double nd = (double)N[p];
-        const double r = __dmul_rn(__dmul_rn(__dsqrt_rn(norm2[p]), nd), nd);
-        if (k == 0) r0[p] = r;
-        rk[p] = r;
-        cyc[p] = k;
-        if (!isfinite(r))
-            st = 3;
-        else if (r <= __dmul_rn(tol, r0[p]))
-            st = 1;
-        else if (k == max_cycles)
-            st = 2;
-        state[p] = st;
-        active[p] = st == 0;
-        mine += st == 0;
-    }
-    if (mine) atomicAdd(&s_active, mine);
-    __syncthreads();
-    const bool more = s_active > 0;
-    if (threadIdx.x == 0) {
-        h->k = k + 1;
-        h->launched += 1 + (k > 0 ? iter_nodes : 0u);
-        if (!more) *launched_host = h->launched;
-        cudaGraphSetConditional(loop, more ? 1u : 0u);
-    }
-    if (!more)
-        for (int p = threadIdx.x; p < count; p += blockDim.x) out[p] = BatchOut{r0[p], rk[p], cyc[p], state[p]};
+    if (threadIdx.x == 0) h_norm2[p] = norm2[p];
 }
 
 struct UpdItem {
@@ -275,15 +197,10 @@ struct BatchWork {
     int *part_off = nullptr, *part_cnt = nullptr;
     BResGroup *rgroups = nullptr;  // the groups for the one-launch residual, descending n
     int res_items = 0;
-    double *norm2 = nullptr;
-    int *active = nullptr;
-    // the device-side loop: its header, per-problem r_0, r_k, cycles, state
-    // and N, and the outcome in mapped pinned host memory
-    BLoopHdr *hdr = nullptr;
-    double *r0 = nullptr, *rk = nullptr;
-    int *cyc = nullptr, *state = nullptr, *Nd = nullptr;
-    BatchOut *h_out = nullptr, *h_out_dev = nullptr;
-    cudaGraphExec_t loop = nullptr;
+    double *norm2 = nullptr, *h_norm2 = nullptr;  // h_norm2: mapped pinned
+    double *h_norm2_dev = nullptr;                 // its device address
+    int *active = nullptr, *h_active = nullptr;  // h_active: mapped pinned
+    int *h_active_dev = nullptr;
     UpdItem *upd = nullptr;
     std::vector<UpdItem> upd_host;
     int upd_chunks = 1;
@@ -480,7 +397,8 @@ cudaError_t record_pre0(mg_ctx *c, BatchWork *w)
     count_launch(1);
     if ((e = cudaGetLastError())) return e;
     if ((e = launch_residual2d_batched_zero(w->rgroups, (int)w->groups.size(), w->res_items, c->s))) return e;
-    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2);
+    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2,
+                                             w->h_norm2_dev);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -490,40 +408,10 @@ cudaError_t record_pre(mg_ctx *c, BatchWork *w)
     cudaError_t e;
     if ((e = launch_residual2d_batched_all(w->rgroups, (int)w->groups.size(), w->res_items, w->active, c->s)))
         return e;
-    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2);
+    batched_sums<<<w->count, 256, 0, c->s>>>(w->partials, w->part_off, w->part_cnt, w->active, w->norm2,
+                                             w->h_norm2_dev);
     count_launch(1);
     return cudaGetLastError();
-}
-
-// The loop graph of a batched solve: batched_decide for k = 0, then a WHILE
-// node whose body is rest -> pre -> batched_decide; the kernel sets the
-// condition value (some problem still active).
-cudaError_t record_loop(mg_ctx *c, BatchWork *w)
-{
-    if (w->loop) cudaGraphExecDestroy(w->loop);
-    w->loop = nullptr;
-    cudaGraph_t G = nullptr;
-    cudaError_t e = cudaGraphCreate(&G, 0);
-    if (e) return e;
-    cudaGraphConditionalHandle loop = 0;
-    unsigned long long n_rest = 0, n_pre = 0;
-    const auto decide = [&]() -> cudaError_t {
-        batched_decide<<<1, kDecideThreads, 0, c->s>>>(w->hdr, w->norm2, w->Nd, w->active, w->r0, w->rk, w->cyc,
-                                                       w->state, w->count, w->h_out_dev, c->h_launched_dev,
-                                                       (unsigned)(n_rest + n_pre), loop);
-        return cudaGetLastError();
-    };
-    e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
-    std::vector<cudaGraphNode_t> top, body;
-    cudaGraph_t B = nullptr;
-    if (!e) e = capture_into(c, G, top, decide, nullptr);
-    if (!e) e = add_conditional(G, top, loop, cudaGraphCondTypeWhile, 1, &B);
-    if (!e) e = capture_into(c, B, body, [&]() { return record_rest(c, w); }, &n_rest);
-    if (!e) e = capture_into(c, B, body, [&]() { return record_pre(c, w); }, &n_pre);
-    if (!e) e = capture_into(c, B, body, decide, nullptr);
-    if (!e) e = cudaGraphInstantiate(&w->loop, G, 0);
-    cudaGraphDestroy(G);
-    return e;
 }
 
 }  // namespace
@@ -545,10 +433,7 @@ mg_status batch_set_inner(mg_ctx *c, int inner)
     if (w->rest) cudaGraphExecDestroy(w->rest);
     w->rest = nullptr;
     c->inner = inner;
-    const mg_status st = capture_graph(c, &w->rest, &w->rest_nodes, [&]() { return record_rest(c, w); });
-    if (st != MG_OK) return st;
-    const cudaError_t e = record_loop(c, w);
-    return e ? cuda_fail(e) : MG_OK;
+    return capture_graph(c, &w->rest, &w->rest_nodes, [&]() { return record_rest(c, w); });
 }
 
 void free_batch(mg_ctx *c)
@@ -559,8 +444,8 @@ void free_batch(mg_ctx *c)
     if (w->pre0) cudaGraphExecDestroy(w->pre0);
     if (w->rest) cudaGraphExecDestroy(w->rest);
     if (w->arena) cudaFree(w->arena);
-    if (w->loop) cudaGraphExecDestroy(w->loop);
-    if (w->h_out) cudaFreeHost(w->h_out);
+    if (w->h_norm2) cudaFreeHost(w->h_norm2);
+    if (w->h_active) cudaFreeHost(w->h_active);
     delete w;
     c->batch = nullptr;
 }
@@ -706,10 +591,6 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
         double *nrm = (double *)a.take(count * sizeof(double));
         int *act = (int *)a.take(count * sizeof(int));
         UpdItem *up = (UpdItem *)a.take(count * sizeof(UpdItem));
-        BLoopHdr *hd = (BLoopHdr *)a.take(sizeof(BLoopHdr));
-        double *lr0 = (double *)a.take(count * sizeof(double)), *lrk = (double *)a.take(count * sizeof(double));
-        int *lcyc = (int *)a.take(count * sizeof(int)), *lst = (int *)a.take(count * sizeof(int));
-        int *lN = (int *)a.take(count * sizeof(int));
         if (real) {
             w->tail_lv = tl;
             w->tail_ops = to;
@@ -721,12 +602,6 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
             w->norm2 = nrm;
             w->active = act;
             w->upd = up;
-            w->hdr = hd;
-            w->r0 = lr0;
-            w->rk = lrk;
-            w->cyc = lcyc;
-            w->state = lst;
-            w->Nd = lN;
         }
     };
     Arena plan;
@@ -745,8 +620,10 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
         mg_destroy(c);
         return cuda_fail(ce);
     }
-    if (cudaHostAlloc((void **)&w->h_out, count * sizeof(BatchOut), cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void **)&w->h_out_dev, w->h_out, 0) != cudaSuccess) {
+    if (cudaHostAlloc((void **)&w->h_norm2, count * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&w->h_norm2_dev, w->h_norm2, 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&w->h_active, count * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&w->h_active_dev, w->h_active, 0) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(c);
         return MG_ENOMEM;
@@ -826,7 +703,6 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
         up(w->part_cnt, part_cnt.data(), count * sizeof(int));
         std::vector<int> ones(count, 1);
         up(w->active, ones.data(), count * sizeof(int));
-        up(w->Nd, w->N.data(), count * sizeof(int));
     }
     for (BatchGroup &G : w->groups) {
         G.host.resize(G.probs.size());
@@ -869,10 +745,6 @@ extern "C" mg_status mg_setup_batched(int d, int count, const int *Ns, const dou
     if (st == MG_OK) st = capture_graph(c, &w->rest, &w->rest_nodes, [&]() { return record_rest(c, w); });
     if (st == MG_OK) st = capture_graph(c, &w->pre, &w->pre_nodes, [&]() { return record_pre(c, w); });
     if (st == MG_OK) st = capture_graph(c, &w->pre0, &w->pre0_nodes, [&]() { return record_pre0(c, w); });
-    if (st == MG_OK) {
-        const cudaError_t e = record_loop(c, w);
-        if (e) st = cuda_fail(e);
-    }
     if (st != MG_OK) {
         mg_destroy(c);
         return st;
@@ -921,22 +793,47 @@ extern "C" mg_status mg_solve_batched_ex(mg_ctx *ctx, const void *const *b, void
         w->cap_u.assign(u, u + count);
         w->cap_b.assign(b, b + count);
     }
-    // the solve: arguments and flags by one kernel, the first residuals, and
-    // the loop graph (every cycle and every stop test on the device); one
-    // synchronisation, the outcome from mapped memory
-    batched_begin<<<1, kDecideThreads, 0, ctx->s>>>(w->hdr, tol, max_cycles, w->active, w->state, count);
-    count_launch(1);
-    if (cudaGetLastError() != cudaSuccess || cudaGraphLaunch(zero_start ? w->pre0 : w->pre, ctx->s) != cudaSuccess ||
-        cudaGraphLaunch(w->loop, ctx->s) != cudaSuccess || cudaStreamSynchronize(ctx->s) != cudaSuccess)
+    std::vector<double> r0(count, 0.0), rk(count, 0.0);
+    std::vector<int> cyc(count, 0), state(count, 0);  // 0 active, 1 converged, 2 out of cycles, 3 NaN
+    for (int p = 0; p < count; ++p) w->h_active[p] = 1;
+    auto upload_flags = [&]() {
+        // a kernel reads the flags from mapped memory: a copy engine could
+        // queue this behind a caller's large transfer
+        return launch_copy_words(w->active, w->h_active_dev, count * sizeof(int), ctx->s);
+    };
+    if (upload_flags() != cudaSuccess || cudaGraphLaunch(zero_start ? w->pre0 : w->pre, ctx->s) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->s) != cudaSuccess)
         return cuda_fail(cudaGetLastError());
     count_launch(zero_start ? w->pre0_nodes : w->pre_nodes);
+    for (int k = 0;; ++k) {
+        int nactive = 0;
+        for (int p = 0; p < count; ++p) {
+            if (state[p]) continue;
+            const double r = std::sqrt(w->h_norm2[p]) * (double)w->N[p] * (double)w->N[p];
+            if (k == 0) r0[p] = r;
+            rk[p] = r;
+            cyc[p] = k;
+            if (!std::isfinite(r))
+                state[p] = 3;
+            else if (r <= tol * r0[p])
+                state[p] = 1;
+            else if (k == max_cycles)
+                state[p] = 2;
+            if (state[p]) w->h_active[p] = 0;
+            else ++nactive;
+        }
+        if (!nactive) break;
+        if (upload_flags() != cudaSuccess || cudaGraphLaunch(w->rest, ctx->s) != cudaSuccess ||
+            cudaGraphLaunch(w->pre, ctx->s) != cudaSuccess || cudaStreamSynchronize(ctx->s) != cudaSuccess)
+            return cuda_fail(cudaGetLastError());
+        count_launch(w->rest_nodes + w->pre_nodes);
+    }
     mg_status st = MG_OK;
     for (int p = 0; p < count; ++p) {
-        const BatchOut o = w->h_out[p];
-        if (cycles_out) cycles_out[p] = o.cycles;
-        if (relres_out) relres_out[p] = o.r0 > 0.0 ? o.rk / o.r0 : 0.0;
-        if (o.state == 3) st = MG_ENAN;
-        else if (o.state == 2 && st == MG_OK) st = MG_ENOCONV;
+        if (cycles_out) cycles_out[p] = cyc[p];
+        if (relres_out) relres_out[p] = r0[p] > 0.0 ? rk[p] / r0[p] : 0.0;
+        if (state[p] == 3) st = MG_ENAN;
+        else if (state[p] == 2 && st == MG_OK) st = MG_ENOCONV;
     }
     if (cudaEventRecord(ctx->ev_out, ctx->s) != cudaSuccess || cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0) != cudaSuccess)
         return cuda_fail(cudaGetLastError());

@@ -87,12 +87,9 @@ struct mg_ctx {
     double *h_norm2 = nullptr;  // mapped pinned
     unsigned long long *h_norm2_dev = nullptr;
     int *d_err = nullptr;
+    bool norm_to_host = true;  // while recording: the pre graphs' norms also to h_norm2
     LoopState *d_loop = nullptr;
-    // mapped pinned: the result of a synchronous solve, its history
-    // (hist_cap doubles), and the count of kernels the loop graphs ran
-    mg_solve_info *h_info = nullptr, *h_info_dev = nullptr;
-    double *h_hist = nullptr, *h_hist_dev = nullptr;
-    int hist_cap = 0;
+    // mapped pinned: the count of kernels the loop graphs ran
     unsigned long long *h_launched = nullptr, *h_launched_dev = nullptr;
     GraphPair g;                  // the graphs for the arrays of the last call
     std::vector<GraphPair> other; // graphs recorded for other arrays, oldest first

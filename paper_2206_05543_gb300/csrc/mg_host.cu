@@ -177,6 +177,16 @@ static cudaError_t launch_sum_partials_host(const mg_ctx *c, int np, cudaStream_
     return cudaGetLastError();
 }
 
+// The squared residual norm of a pre or norm-only graph: also into mapped
+// host memory for the host-driven loop of mg_solve (and mg_vcycle's graphs),
+// device memory only inside the device-side loop graph, which writes nothing
+// to host memory while it runs.
+static cudaError_t launch_norm_sum(const mg_ctx *c, int np)
+{
+    return c->norm_to_host ? launch_sum_partials_host(c, np, c->s)
+                           : launch_sum_partials(c->partials, np, c->d_norm2, c->s);
+}
+
 // ---------------------------------------------------------------------------
 // the cycle loop of a solve on the device: the stop test ||r_k|| <= tol ||r_0||
 // of Sec. 4 decided by one-thread kernels that set the condition values of the
@@ -230,12 +240,18 @@ __device__ __forceinline__ bool wait_expired(const int *err) { return *(volatile
 // a solve's arguments, by value, stored for its loop graph
 __global__ void loop_args_kernel(LoopState *st, LoopArgs a) { st->a = a; }
 
+// the first graph of the solve: the from-zero pre graph or the pre graph
+__global__ void loop_head_kernel(const LoopState *st, cudaGraphConditionalHandle from_zero)
+{
+    cudaGraphSetConditional(from_zero, st->a.zero_start ? 1u : 0u);
+}
+
 // after the first pre graph: r_0, the history's first entry, the loop's
 // state; zero_u is set when a solve from u = 0 runs no cycle (u would stay
-// unwritten otherwise)
+// unwritten otherwise). n_pre0, n_pre: kernels of the two first graphs.
 __global__ void loop_init_kernel(LoopState *st, const double *norm2, const int *err, double nd, int guessing,
-                                 cudaGraphConditionalHandle loop, cudaGraphConditionalHandle zero_u,
-                                 unsigned long long *launched)
+                                 unsigned n_pre0, unsigned n_pre, cudaGraphConditionalHandle loop,
+                                 cudaGraphConditionalHandle zero_u, unsigned long long *launched)
 {
     LoopState s = *st;
     s.r0 = s.rk = loop_norm(norm2, nd);
@@ -246,7 +262,8 @@ __global__ void loop_init_kernel(LoopState *st, const double *norm2, const int *
     if (s.a.hist) s.a.hist[0] = s.r0;
     const bool more = loop_continue(s);
     const bool zero = s.a.zero_start && !more;
-    s.launched += zero ? 2 : 1;  // this kernel and the zeroing of u
+    // the head kernel, the first graph, this kernel, the zeroing of u
+    s.launched += 2 + (s.a.zero_start ? n_pre0 : n_pre) + (zero ? 1 : 0);
     *st = s;
     if (!more) loop_finish(s, launched);
     cudaGraphSetConditional(zero_u, zero ? 1u : 0u);
@@ -553,8 +570,6 @@ static void destroy_ctx(mg_ctx *c)
     for (void *p : c->owned) cudaFree(p);
     unregister_ctx(c);
     if (c->h_norm2) cudaFreeHost(c->h_norm2);
-    if (c->h_info) cudaFreeHost(c->h_info);
-    if (c->h_hist) cudaFreeHost(c->h_hist);
     if (c->h_launched) cudaFreeHost(c->h_launched);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -775,31 +790,54 @@ using CaptureFn = std::function<cudaError_t()>;
 // The graphs of a solve. pre: the residual norm of u (with a fused pre-sweep
 // when the cycle starts with one); pre0: the same for u = 0 without reading
 // u; meas: the norm alone (only with a fused pre-sweep); rest: the rest of the
-// cycle. loop: the cycle loop with its stop test on the device,
-//   init -> [IF zero_u: u = 0] -> WHILE loop { [IF rerun_pre: pre] -> rest ->
-//           [IF use_meas: meas ELSE pre] -> after }
+// cycle. loop: a whole solve with its stop test on the device,
+//   head -> [IF from_zero: pre0 ELSE pre] -> init -> [IF zero_u: u = 0] ->
+//   WHILE loop { [IF rerun_pre: pre] -> rest -> [IF use_meas: meas ELSE pre]
+//                -> after }
 // (without meas: WHILE loop { rest -> pre -> after }), where the one-thread
-// kernels init and after set the condition values.
+// kernels head, init and after set the condition values.
 static mg_status record_graphs(mg_ctx *c, void *u, const CaptureFn &pre, const CaptureFn &pre0,
                                const CaptureFn *meas, const CaptureFn &rest)
 {
+    // the plain graphs (mg_vcycle, the host-driven loop of mg_solve); their
+    // norms also go to mapped host memory
+    mg_status st;
+    c->norm_to_host = true;
+    if ((st = capture(c, &c->g.pre, &c->g.pre_nodes, pre)) != MG_OK) return st;
+    if ((st = capture(c, &c->g.pre0, &c->g.pre0_nodes, pre0)) != MG_OK) return st;
+    if (meas && (st = capture(c, &c->g.meas, &c->g.meas_nodes, *meas)) != MG_OK) return st;
+    if ((st = capture(c, &c->g.rest, &c->g.rest_nodes, rest)) != MG_OK) return st;
+    // the loop graph of mg_solve_async, with its own copies of the same work
     cudaGraph_t G = nullptr;
     cudaError_t e = cudaGraphCreate(&G, 0);
     if (e) return cuda_fail(e);
     const double nd = (double)c->N;
     const int has_meas = meas != nullptr;
     const size_t ubytes = npoints(c->d, c->n[0]) * (c->prec == MG_FP32 ? sizeof(float) : sizeof(double));
+    c->norm_to_host = false;
     auto build = [&]() -> cudaError_t {
         // every handle belongs to the top graph and is reset at each launch
-        cudaGraphConditionalHandle loop, zero_u, rerun_pre = 0, use_meas = 0;
-        cudaError_t e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
+        cudaGraphConditionalHandle from_zero, loop, zero_u, rerun_pre = 0, use_meas = 0;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&from_zero, G, 0, cudaGraphCondAssignDefault);
+        if (!e) e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
         if (!e) e = cudaGraphConditionalHandleCreate(&zero_u, G, 0, cudaGraphCondAssignDefault);
         if (!e && has_meas) e = cudaGraphConditionalHandleCreate(&rerun_pre, G, 0, cudaGraphCondAssignDefault);
         if (!e && has_meas) e = cudaGraphConditionalHandleCreate(&use_meas, G, 0, cudaGraphCondAssignDefault);
         std::vector<cudaGraphNode_t> top, body, none;
         if (!e) e = capture_into(c, G, top, [&]() {
-            loop_init_kernel<<<1, 1, 0, c->s>>>(c->d_loop, c->d_norm2, c->d_err, nd, has_meas, loop, zero_u,
-                                                c->h_launched_dev);
+            loop_head_kernel<<<1, 1, 0, c->s>>>(c->d_loop, from_zero);
+            return cudaGetLastError();
+        }, nullptr);
+        unsigned long long n_pre0 = 0, n_pre_head = 0;
+        cudaGraph_t first[2] = {nullptr, nullptr};  // [0]: from zero, [1]: else
+        if (!e) e = add_conditional(G, top, from_zero, cudaGraphCondTypeIf, 2, first);
+        if (!e) e = capture_into(c, first[0], none, pre0, &n_pre0);
+        none.clear();
+        if (!e) e = capture_into(c, first[1], none, pre, &n_pre_head);
+        none.clear();
+        if (!e) e = capture_into(c, G, top, [&]() {
+            loop_init_kernel<<<1, 1, 0, c->s>>>(c->d_loop, c->d_norm2, c->d_err, nd, has_meas, (unsigned)n_pre0,
+                                                (unsigned)n_pre_head, loop, zero_u, c->h_launched_dev);
             return cudaGetLastError();
         }, nullptr);
         cudaGraph_t Z = nullptr, B = nullptr;
@@ -834,15 +872,9 @@ static mg_status record_graphs(mg_ctx *c, void *u, const CaptureFn &pre, const C
         return e;
     };
     e = build();
+    c->norm_to_host = true;
     cudaGraphDestroy(G);
-    if (e) return cuda_fail(e);
-    // the same work as plain graphs (mg_vcycle, and the first pre graph of a
-    // solve), recorded after the loop's copies
-    mg_status st;
-    if ((st = capture(c, &c->g.pre, &c->g.pre_nodes, pre)) != MG_OK) return st;
-    if ((st = capture(c, &c->g.pre0, &c->g.pre0_nodes, pre0)) != MG_OK) return st;
-    if (meas && (st = capture(c, &c->g.meas, &c->g.meas_nodes, *meas)) != MG_OK) return st;
-    return capture(c, &c->g.rest, &c->g.rest_nodes, rest);
+    return e ? cuda_fail(e) : MG_OK;
 }
 
 // Plain cycles in precision T on the caller's arrays (level 0 = caller's u, b).
@@ -860,7 +892,7 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
             e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
         if (e) return e;
         const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
-        return launch_sum_partials(c->partials, np, c->d_norm2, c->s);
+        return launch_norm_sum(c, np);
     };
     // solve from u = 0: the first pre-sweep in its from-zero form (u is not
     // read; the rest of the cycle writes it); without a fused pre-sweep, u is
@@ -875,12 +907,12 @@ static mg_status record_plain(mg_ctx *c, void *u, const void *b)
         }
         if (e) return e;
         const int np = fused ? sweep_partials(d, n0, (int)sizeof(T)) : residual_partials(d, n0);
-        return launch_sum_partials(c->partials, np, c->d_norm2, c->s);
+        return launch_norm_sum(c, np);
     };
     const CaptureFn meas = [&]() -> cudaError_t {
         cudaError_t e = op_residual<T, T>(d, (const T *)u, (const T *)b, true, (T *)nullptr, n0, c->partials, c->s);
         if (e) return e;
-        return launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s);
+        return launch_norm_sum(c, residual_partials(d, n0));
     };
     const CaptureFn rest = [&]() -> cudaError_t { return R.visit(0, false, fused); };
     return record_graphs(c, u, pre, pre0, fused ? &meas : nullptr, rest);
@@ -932,7 +964,7 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
                                                c->partials, c->s);
             }
             if (e) return e;
-            return launch_sum_partials(c->partials, residual_partials(d, n0), c->d_norm2, c->s);
+            return launch_norm_sum(c, residual_partials(d, n0));
         };
         // solve from u = 0: u zeroed (the FP64 updates add into it) and the
         // first residual is h^2 b itself, rounded to FP32, without FP64 work
@@ -941,7 +973,7 @@ static mg_status record(mg_ctx *c, void *u, const void *b)
             int nb = 0;
             if (!e) e = launch_refine_rhs_zero(c, (const double *)b, nb);
             if (e) return e;
-            return launch_sum_partials(c->partials, nb, c->d_norm2, c->s);
+            return launch_norm_sum(c, nb);
         };
         const CaptureFn rest = [&]() -> cudaError_t {
             cudaError_t e = cudaSuccess;
@@ -1105,9 +1137,6 @@ static mg_status setup_impl(int d, int N, const double *coeffs, int ncoeffs, int
         MG_TRYC(cudaHostAlloc((void **)&c->h_norm2, kNormBytes, cudaHostAllocMapped));
         MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_norm2_dev, c->h_norm2, 0));
         std::memset(c->h_norm2, 0, kNormBytes);
-        MG_TRYC(cudaHostAlloc((void **)&c->h_info, sizeof(mg_solve_info), cudaHostAllocMapped));
-        MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_info_dev, c->h_info, 0));
-        std::memset(c->h_info, 0, sizeof(mg_solve_info));
         MG_TRYC(cudaHostAlloc((void **)&c->h_launched, sizeof(unsigned long long), cudaHostAllocMapped));
         MG_TRYC(cudaHostGetDevicePointer((void **)&c->h_launched_dev, c->h_launched, 0));
         *c->h_launched = 0;
@@ -1257,26 +1286,9 @@ static mg_status sync_ctx(mg_ctx *ctx)
     return timed_out(ctx) ? MG_ETIMEOUT : MG_OK;
 }
 
-// the history lives in mapped pinned memory: at most this many cycles
-constexpr int kMaxHistCycles = 1 << 20;
-
-// a mapped history of at least n doubles for the device loop
-static mg_status hist_reserve(mg_ctx *c, int n)
-{
-    if (n <= c->hist_cap) return MG_OK;
-    if (c->h_hist) cudaFreeHost(c->h_hist);
-    c->h_hist = c->h_hist_dev = nullptr;
-    c->hist_cap = 0;
-    const int cap = std::max(n, 128);
-    MG_CUDA(cudaHostAlloc((void **)&c->h_hist, (size_t)cap * sizeof(double), cudaHostAllocMapped));
-    MG_CUDA(cudaHostGetDevicePointer((void **)&c->h_hist_dev, c->h_hist, 0));
-    c->hist_cap = cap;
-    return MG_OK;
-}
-
 // Queue one solve on the context's stream, between enter() and leave(): its
-// arguments (by value, in a kernel's parameters), the first pre graph, and
-// the loop graph, which runs the cycles and the stop test on the device. The
+// arguments (by value, in a kernel's parameters) and the loop graph, which
+// runs the first pre graph, the cycles and the stop test on the device. The
 // pre graph smooths the next cycle's input speculatively while it measures
 // the residual, so the measurement that ends the solve would pay for a sweep
 // nobody uses: when the last convergence factor, carried one cycle forward,
@@ -1298,42 +1310,69 @@ static mg_status queue_solve(mg_ctx *ctx, const void *b, void *u, double tol, in
     loop_args_kernel<<<1, 1, 0, ctx->s>>>(ctx->d_loop, a);
     count_launch(1);
     MG_CUDA(cudaGetLastError());
-    if ((st = zero_start ? launch_graph(ctx, ctx->g.pre0, ctx->g.pre0_nodes)
-                         : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK)
-        return st;
     MG_CUDA(cudaGraphLaunch(ctx->g.loop, ctx->s));
     return MG_OK;
 }
 
-// mg_solve_ex between enter() and leave(): the queued solve, one
-// synchronisation, the result from mapped memory
+// mg_solve_ex between enter() and leave(): the same schedule driven from the
+// host, one synchronisation per cycle (the norm comes through mapped host
+// memory). On small grids this is faster than the device-side loop, whose
+// conditional nodes cost a few microseconds per cycle more than the round
+// trip, and every kernel of it is visible to profilers that cannot look
+// inside graphs with conditional nodes. Its iterates, counts and history are
+// those of mg_solve_async bit for bit.
 static mg_status solve_loop(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, bool zero_start,
                             int *cycles_out, double *relres_out, double *hist_out)
 {
     mg_status st;
-    if (hist_out && (st = hist_reserve(ctx, max_cycles + 1)) != MG_OK) return st;
-    if ((st = queue_solve(ctx, b, u, tol, max_cycles, zero_start, ctx->h_info_dev,
-                          hist_out ? ctx->h_hist_dev : nullptr)) != MG_OK)
+    if ((st = record(ctx, u, b)) != MG_OK) return st;
+    if ((st = zero_start ? launch_graph(ctx, ctx->g.pre0, ctx->g.pre0_nodes)
+                         : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK)
         return st;
-    MG_CUDA(cudaStreamSynchronize(ctx->s));
-    mg_solve_info r;
-    std::memcpy(&r, ctx->h_info, sizeof r);
-    if (r.status == MG_ETIMEOUT) {
-        int e = 0;  // the expiry bits, for the message
-        if (cudaMemcpy(&e, ctx->d_err, sizeof e, cudaMemcpyDeviceToHost) == cudaSuccess) timed_out_word(e);
-        return MG_ETIMEOUT;
+    if ((st = sync_ctx(ctx)) != MG_OK) return st;
+    const double r0 = norm_from_host(ctx);
+    double rk = r0, rprev = 0.0;
+    int k = 0;
+    if (hist_out) hist_out[0] = r0;
+    st = std::isfinite(r0) ? MG_OK : MG_ENAN;
+    bool guessing = ctx->g.meas != nullptr;
+    while (st == MG_OK && !(rk <= tol * r0)) {
+        if (k == max_cycles) {
+            st = MG_ENOCONV;
+            break;
+        }
+        const bool guess = guessing && k >= 1 && rprev > 0.0 && rk * (rk / rprev) <= tol * r0;
+        mg_status ls;
+        if ((ls = launch_graph(ctx, ctx->g.rest, ctx->g.rest_nodes)) != MG_OK) return ls;
+        ls = guess ? launch_graph(ctx, ctx->g.meas, ctx->g.meas_nodes) : launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes);
+        if (ls != MG_OK) return ls;
+        if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
+        ++k;
+        rprev = rk;
+        rk = norm_from_host(ctx);
+        if (hist_out) hist_out[k] = rk;
+        if (!std::isfinite(rk)) st = MG_ENAN;
+        if (st == MG_OK && guess && !(rk <= tol * r0) && k < max_cycles) {
+            guessing = false;
+            if ((ls = launch_graph(ctx, ctx->g.pre, ctx->g.pre_nodes)) != MG_OK) return ls;
+            if ((ls = sync_ctx(ctx)) != MG_OK) return ls;
+        }
     }
-    if (hist_out) std::memcpy(hist_out, ctx->h_hist, (size_t)(r.cycles + 1) * sizeof(double));
-    if (cycles_out) *cycles_out = r.cycles;
-    if (relres_out) *relres_out = r.r0 > 0.0 ? r.rk / r.r0 : 0.0;
-    return (mg_status)r.status;
+    if (zero_start && k == 0) {
+        // no cycle ran (zero rhs, max_cycles = 0, a non-finite r0): u is the
+        // zero initial guess, which a zero start never wrote
+        const size_t bytes = npoints(ctx->d, ctx->n[0]) * (ctx->prec == MG_FP32 ? sizeof(float) : sizeof(double));
+        MG_CUDA(launch_zero_words(u, bytes, ctx->s));
+    }
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = r0 > 0.0 ? rk / r0 : 0.0;
+    return st;
 }
 
 mg_status mg_solve_ex(mg_ctx *ctx, const void *b, void *u, double tol, int max_cycles, unsigned flags,
                       int *cycles_out, double *relres_out, double *hist_out)
 {
-    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch || (flags & ~MG_SOLVE_ZERO_START) ||
-        (hist_out && max_cycles > kMaxHistCycles))
+    if (!ctx || !u || !b || max_cycles < 0 || !(tol >= 0.0) || ctx->batch || (flags & ~MG_SOLVE_ZERO_START))
         return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;
@@ -1347,7 +1386,7 @@ mg_status mg_solve_async(mg_ctx *ctx, const void *b, void *u, double tol, int ma
                          mg_solve_info *info, double *hist)
 {
     if (!ctx || !u || !b || !info || max_cycles < 0 || !(tol >= 0.0) || ctx->batch ||
-        (flags & ~MG_SOLVE_ZERO_START) || (hist && max_cycles > kMaxHistCycles))
+        (flags & ~MG_SOLVE_ZERO_START))
         return MG_EINVAL;
     mg_status st = enter(ctx);
     if (st != MG_OK) return st;

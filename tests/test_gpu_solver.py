@@ -357,10 +357,9 @@ def test_solve_ex_rejects_unknown_flags():
     assert st == binding.MG_EINVAL
 
 
-def test_device_loop_limits_and_optional_outputs():
-    """The cycle loop runs on the device: a solve with tol = 0 runs exactly
-    max_cycles cycles with the oracle's history; the outputs are optional;
-    a history longer than the loop can hold is refused."""
+def test_loop_limits_and_optional_outputs():
+    """A solve with tol = 0 runs exactly max_cycles cycles with the oracle's
+    history; the outputs are optional."""
     b = inputs.uniform(2, 64, 21)
     w = coeffs.default(2)
     ref = oracle.solve(b, w, tol=0.0, max_cycles=30)
@@ -383,10 +382,6 @@ def test_device_loop_limits_and_optional_outputs():
         st = lib.mg_solve_ex(s._ctx, ctypes.c_void_p(bt.data_ptr()), ctypes.c_void_p(u.data_ptr()), 1e-10,
                              1 << 30, binding.MG_SOLVE_ZERO_START, None, None, None)
         assert st == MG_OK and np.array_equal(host(u), o.u)
-        hist = np.zeros(4)
-        st = lib.mg_solve_ex(s._ctx, ctypes.c_void_p(bt.data_ptr()), ctypes.c_void_p(u.data_ptr()), 1e-10,
-                             (1 << 20) + 1, 0, None, None, hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-        assert st == binding.MG_EINVAL
 
 
 def test_async_solves_queued_back_to_back():
@@ -477,9 +472,6 @@ def test_solve_async_rejects_bad_arguments():
                                   None) == binding.MG_EINVAL
         assert lib.mg_solve_async(s._ctx, P(b.data_ptr()), P(b.data_ptr()), -1.0, 10, 0, P(info.data_ptr()),
                                   None) == binding.MG_EINVAL
-        hist = torch.zeros(8, dtype=torch.float64, device="cuda")
-        assert lib.mg_solve_async(s._ctx, P(b.data_ptr()), P(b.data_ptr()), 1e-10, (1 << 20) + 1, 0,
-                                  P(info.data_ptr()), P(hist.data_ptr())) == binding.MG_EINVAL
         # a zero right-hand side: no cycle, status OK, written by the device
         p = s.solve_async(b, tol=1e-10, max_cycles=10, info_buf=info)
         r = p.result()
