@@ -10,7 +10,11 @@ in HBM; every field (537 MB) is larger than L2, so no flush is needed.
 
 value = unknowns x V-cycles / second (DOF/s), summed over ranks; each rank
 solves its own replica of the problem (the single-problem path is not
-decomposed across GPUs). Printed as one JSON line by rank 0.
+decomposed across GPUs). Printed as one JSON line by rank 0. e2e is the same
+metric with every step's b copied in from pinned host memory and its u and
+outcome returned to pinned host memory, the solves queued with
+mg_solve_async on two alternating device slots so that the copies of one
+step overlap the solve of the next.
 
 --impl reference times the FP64 CPU oracle (the checker in oracle/) on this
 machine's host cores on the same workload; each step is a bounded sample,

@@ -86,3 +86,14 @@ def test_package_weights_equal_oracle_weights():
         ref = ref[: len(w)]
         assert np.array_equal(np.array(w), np.array(ref)), (d, name)
         assert all(r == 0.0 for r in coeffs.weights(d, name)[len(w):])
+
+
+def test_solve_info_layout_matches_the_header():
+    """mg_solve_info as declared in include/mg.h: two doubles, two ints."""
+    text = open(os.path.join(ROOT, "include", "mg.h")).read()
+    body = re.search(r"typedef struct mg_solve_info \{(.*?)\} mg_solve_info;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(double|int)\s+(\w+);", body)
+    assert fields == [("double", "r0"), ("double", "rk"), ("int", "cycles"), ("int", "status")]
+    assert [f[0] for f in binding.MGSolveInfo._fields_] == [f[1] for f in fields]
+    assert ctypes.sizeof(binding.MGSolveInfo) == 24
