@@ -479,3 +479,31 @@ def test_solve_async_rejects_bad_arguments():
     with pytest.raises(ValueError):
         with Solver(2, 64) as s:
             s.solve_async(b, info_buf=torch.zeros(24, dtype=torch.uint8))  # not page-locked
+
+
+@pytest.mark.parametrize("case", ["misses", "holds"])
+def test_async_final_measurement_guess(case):
+    """The device-side loop of mg_solve_async takes the same guesses as the
+    host loop: the norm-only graph for the predicted last cycle, and after a
+    guess that misses, the pre graph and no more guessing. Cycles, history
+    and u equal the oracle's (which never guesses)."""
+    if case == "misses":
+        d, N, seed, nu, j = 2, 64, 64, 1, 8
+        b = inputs.uniform(d, N, seed)
+        h = np.asarray(oracle.solve(b, coeffs.default(d), tol=0.0, max_cycles=10).hist)
+        guess = h[j - 1] ** 2 / h[j - 2]
+        assert guess < h[j] * (1 - 1e-3)
+        tol, cycles = float(np.sqrt(guess * h[j]) / h[0]), j + 1
+    else:
+        d, N, seed, nu, j = 3, 32, 5, 2, 7
+        b = inputs.uniform(d, N, seed)
+        h = np.asarray(oracle.solve(b, coeffs.default(d), tol=0.0, max_cycles=9, nu1=nu, nu2=nu).hist)
+        tol, cycles = float(h[j] * (1 + 1e-6) / h[0]), j
+    ref = oracle.solve(b, coeffs.default(d), tol=tol, max_cycles=60, nu1=nu, nu2=nu)
+    assert ref.cycles == cycles
+    with Solver(d, N, nu1=nu, nu2=nu) as s:
+        p = s.solve_async(dev(b), tol=tol, max_cycles=60, history=True)
+        r = p.result()
+    assert r.status == ref.status and r.cycles == ref.cycles
+    np.testing.assert_allclose(r.hist, ref.hist, rtol=1e-12, atol=0)
+    assert np.array_equal(host(p.u), ref.u)
