@@ -99,13 +99,19 @@ def f_ab_extremes(a: float, b: float):
 # two-grid analysis (Sec. 4, Table 1)
 # ---------------------------------------------------------------------------
 
-def two_grid_factor(d: int, wfold, nu: int, n: int = 256) -> float:
+def two_grid_factor(d: int, wfold, nu: int, n: int = 256, coarse: str = "rediscretised") -> float:
     """LFA two-grid factor rho_h(nu): the largest spectral radius of the
     2^d x 2^d symbol S^nu K over the low frequencies theta = 2 pi k / n in
-    T^L, theta != 0, where K = I - P~ (A~_H)^{-1} R~ A~_h uses the
-    rediscretised coarse operator (H = 2h), full weighting (symbol
-    prod (1 + cos theta_i)/2 per harmonic) and linear interpolation (the same
-    symbol). The harmonics of theta are theta + pi alpha, alpha in {0,1}^d."""
+    T^L, theta != 0, where K = I - P~ (A~_H)^{-1} R~ A~_h with full weighting
+    (symbol prod (1 + cos theta_i)/2 per harmonic) and linear interpolation
+    (the same symbol). The harmonics of theta are theta + pi alpha, alpha in
+    {0,1}^d. coarse: "rediscretised" (A_H the same stencil on H = 2h, as in
+    the cycle of Sec. 4) or "galerkin" (A_H = R A_h P, whose symbol is the sum
+    over the harmonics of R~ A~_h P~). Table 1 (Sec. 4) does not say which it
+    uses; its 2D M_5 and M_9 rows are the Galerkin values and its other rows
+    the rediscretised ones (both reproduced to the printed digits)."""
+    if coarse not in ("rediscretised", "galerkin"):
+        raise ValueError(coarse)
     ks = np.arange(-n // 4, n // 4)
     theta = np.stack(np.meshgrid(*([2.0 * np.pi * ks / n] * d), indexing="ij"), -1).reshape(-1, d)
     theta = theta[np.any(theta != 0.0, axis=1)]
@@ -118,7 +124,10 @@ def two_grid_factor(d: int, wfold, nu: int, n: int = 256) -> float:
         m = m + 4.0 * wfold[2] * cos[..., 0] * cos[..., 1]
     s = (1.0 - a_h * m) ** nu
     r = np.prod((1.0 + cos) / 2.0, axis=-1)  # (T, 2^d)
-    a_H = 2.0 * (d - np.cos(2.0 * theta).sum(axis=-1)) / 4.0  # H = 2h relative to h = 1
+    if coarse == "galerkin":
+        a_H = (r * a_h * r).sum(axis=-1)
+    else:
+        a_H = 2.0 * (d - np.cos(2.0 * theta).sum(axis=-1)) / 4.0  # H = 2h relative to h = 1
     K = np.eye(2 ** d)[None] - r[:, :, None] * (r * a_h)[:, None, :] / a_H[:, None, None]
     T = s[:, :, None] * K
     return float(np.max(np.abs(np.linalg.eigvals(T))))
